@@ -1,0 +1,364 @@
+"""Benchmark of the ETD2RK-DS step on GB300.
+
+Default workload (N = 1): 2D FitzHugh-Nagumo, n = 4096 interior points per axis,
+two fields, kappa_u = 1e-3, kappa_v = 5e-3, eps = 0.01, a = 0.5, b = 0.1,
+tau = 1e-2, Pade P_{0,2}, split-TF32 transforms, seeded U[-0.1, 0.1] fields.
+A "step" is one ETD2RK-DS time step (eq. (13)-(14)): two reaction kernels and
+eight transform passes over both fields.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--precision P]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Prints one JSON line (rank 0). With N > 1 (torchrun), every rank advances its
+own replica of the workload (the problem has no data-parallel exchange; see
+the design notes): value = all ranks' unknown-updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FHN = (1.0, 0.01, 0.5, 0.1)  # c3, eps, a, b
+
+WORKLOADS = {
+    # name: (d, n, kappa_u, kappa_v or None, q, tau, reaction, description)
+    "fhn2d_4096": (2, 4096, 1e-3, 5e-3, 0.0, 1e-2, "fhn",
+                   "2D FitzHugh-Nagumo n=4096 (2 fields), kappa_u=1e-3 kappa_v=5e-3 eps=0.01 a=0.5 b=0.1 tau=1e-2"),
+    "fhn2d_2048": (2, 2048, 1e-3, 5e-3, 0.0, 1e-2, "fhn",
+                   "2D FitzHugh-Nagumo n=2048 (2 fields), kappa_u=1e-3 kappa_v=5e-3 eps=0.01 a=0.5 b=0.1 tau=1e-2"),
+    "ac3d_256": (3, 256, 1e-3, None, 0.1, 5e-3, "allen_cahn", "3D Allen-Cahn n=256, kappa=1e-3 q=0.1 tau=5e-3"),
+    "ac3d_384": (3, 384, 1e-3, None, 0.1, 5e-3, "allen_cahn", "3D Allen-Cahn n=384, kappa=1e-3 q=0.1 tau=5e-3"),
+    "ac2d_64": (2, 64, 1e-2, None, 0.0, 1e-3, "allen_cahn", "2D Allen-Cahn n=64, kappa=1e-2 q=0 tau=1e-3"),
+}
+TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
+L2_BYTES = 129e6
+
+
+def initial_field(name):
+    from paper_2601_06849_gb300 import inputs
+
+    d, n, ku, kv, q, tau, rx, _ = WORKLOADS[name]
+    if rx == "fhn":
+        return inputs.fhn_uniform(n, d, workload=1)
+    if d == 3:
+        return inputs.gaussian_bump(n, 3)
+    return inputs.allen_cahn_2d(n, workload=0)
+
+
+def make_plan(name, precision, stream=None):
+    from paper_2601_06849_gb300 import etd
+
+    d, n, ku, kv, q, tau, rx, _ = WORKLOADS[name]
+    if rx == "fhn":
+        return etd.Plan(d, n, ku, q, tau, pade=2, precision=precision, reaction="fhn", rx_params=FHN, n_comp=2,
+                        kappa_comp=(ku, kv), stream=stream)
+    return etd.Plan(d, n, ku, q, tau, pade=2, precision=precision, reaction=rx, n_comp=1, stream=stream)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier_max(value, world):
+    """Barrier, then the max of `value` over ranks."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def cpu_baseline(name, steps=5):
+    """The FP64 CPU oracle as it stands, all host cores, `steps` time steps of the workload."""
+    from oracle import oracle as O
+
+    d, n, ku, kv, q, tau, rx, _ = WORKLOADS[name]
+    kap = (ku, kv) if rx == "fhn" else (ku,)
+    P = O.Problem(d=d, n=n, kappa=kap, q=q, tau=tau, pade=2, reaction=rx, rp=FHN if rx == "fhn" else ())
+    u0 = initial_field(name)
+    O.lib()  # build and load before timing
+    t0 = time.perf_counter()
+    O.run(P, u0, steps)
+    dt = time.perf_counter() - t0
+    unknowns = u0.size
+    return {"value": unknowns * steps / dt, "unit": "unknown-updates/s", "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"{steps} FP64 time step(s) of the full {name} workload ({unknowns} unknowns), "
+                      f"Thomas/LU oracle, OpenMP over 1D lines", "seconds": dt}
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the FP64 CPU oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    name = args.workload
+    d, n, ku, kv, q, tau, rx, desc = WORKLOADS[name]
+    kap = (ku, kv) if rx == "fhn" else (ku,)
+    u0 = initial_field(name)
+    # per-step sample: one full time step of the workload, unless the whole run
+    # would exceed ~150 s; then the same workload on a coarser grid.
+    P = O.Problem(d=d, n=n, kappa=kap, q=q, tau=tau, pade=2, reaction=rx, rp=FHN if rx == "fhn" else ())
+    t0 = time.perf_counter()
+    O.run(P, u0, 1)
+    one = time.perf_counter() - t0
+    sample_n = n
+    budget = 150.0
+    while (args.steps + args.warmup) * one > budget and sample_n > 256:
+        sample_n //= 2
+        one /= (2 ** (d + 1))
+    if sample_n != n:
+        P = O.Problem(d=d, n=sample_n, kappa=kap, q=q, tau=tau, pade=2, reaction=rx, rp=P.rp)
+        from paper_2601_06849_gb300 import inputs
+
+        u0 = inputs.fhn_uniform(sample_n, d, workload=1) if rx == "fhn" else (
+            inputs.gaussian_bump(sample_n, 3) if d == 3 else inputs.allen_cahn_2d(sample_n, workload=0))
+    u = O.run(P, u0, args.warmup)
+    t0 = time.perf_counter()
+    u = O.run(P, u, args.steps)
+    el = time.perf_counter() - t0
+    value = u.size * args.steps / el
+    sample = (f"each step: one FP64 oracle time step of {name}" +
+              (f" on the coarser n={sample_n} grid" if sample_n != n else " (full grid)"))
+    line = {"impl": "reference", "metric": "unknown-updates/s per ETD2RK-DS step", "value": value,
+            "unit": "unknown-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "n": sample_n, "d": d, "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": "unknown-updates/s", "cores": O.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "unknown-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="fhn2d_4096", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="tf32x3")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    import __graft_entry__
+    from paper_2601_06849_gb300 import etd
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    name = args.workload
+    d, n, ku, kv, q, tau, rx, desc = WORKLOADS[name]
+    stream = torch.cuda.Stream()
+    plan = make_plan(name, args.precision, stream=stream)
+    info = plan.info()
+    u0 = initial_field(name)
+    u = torch.tensor(u0, dtype=plan.dtype, device="cuda")
+    passes = info.gemms_per_step
+    launches_per_step = passes + 2
+
+    with torch.cuda.stream(stream):
+        plan.step(u, args.warmup)
+        plan.sync()
+        plan.set_timing(True)
+        plan.kernel_times(0)
+        plan.kernel_times(1)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clocks:
+            ev0.record(stream)
+            plan.step(u, args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        barrier(world)
+        el_ms = ev0.elapsed_time(ev1)
+        plan.sync()
+        gemm_ms, gemm_n = plan.kernel_times(0)
+        rx_ms, rx_n = plan.kernel_times(1)
+        plan.set_timing(False)
+    el_max = barrier_max(el_ms, world)
+    m, bad = plan.stats(u)
+    unknowns = info.unknowns
+    value = world * unknowns * args.steps / (el_max / 1e3)
+
+    # end to end through the public host entry point: H2D + step + D2H each step
+    e2e_steps = args.e2e_steps or max(3, min(args.steps, 10))
+    host = torch.tensor(u0, dtype=plan.dtype).pin_memory()
+    plan.step_host(host, 1)  # warm the host path
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        plan.step_host(host, 1)
+    e2e_s = barrier_max(time.perf_counter() - t0, world)
+    bytes_field = unknowns * (8 if plan.dtype == torch.float64 else 4)
+
+    peaks, src = measured_peaks()
+    avg_gemm_ms = gemm_ms / max(gemm_n, 1)
+    if info.products > 0:
+        flops = info.gemm_flops * info.products
+        peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+        achieved = flops / (avg_gemm_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "gemm_tf32_tc_kernel (transform pass)",
+                "peak_source": f"{src}: bf16_tflops_sustained x 1.1/2.25 (TF32/BF16 nominal)",
+                "flops_per_launch": flops, "avg_launch_ms": avg_gemm_ms}
+    else:
+        flops = info.gemm_flops
+        lanes = 128 if plan.dtype == torch.float32 else 2  # FP32 lanes / FP64 units per SM
+        clk = 2.07e9
+        peak = 152 * lanes * 2 * clk / 1e12
+        achieved = flops / (avg_gemm_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "gemm_simt_kernel (transform pass)",
+                "peak_source": "152 SMs x FMA lanes x 2 x 2.07 GHz", "flops_per_launch": flops,
+                "avg_launch_ms": avg_gemm_ms}
+
+    line = {
+        "metric": "unknown-updates/s per ETD2RK-DS step",
+        "value": value,
+        "unit": "unknown-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": el_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"tf32x3": "tf32x3 (f32 state)", "tf32": "tf32 (f32 state)", "fp32": "f32",
+                  "fp64": "f64"}.get(args.precision, args.precision),
+        "data": "synthetic",
+        "config": {"workload": desc, "d": d, "n": n, "n_comp": info.n_comp, "precision": args.precision,
+                   "pade": "P02", "unknowns": unknowns,
+                   "l2": f"working set {info.workspace_bytes / 1e9:.2f} GB > 129 MB L2: inputs larger than L2, no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof,
+        "gpu_launches": launches_per_step * args.steps,
+        "kernel_ms": {"transform_passes": gemm_ms, "transform_launches": gemm_n, "reaction_ms": rx_ms,
+                      "reaction_launches": rx_n},
+        "e2e": {"value": world * unknowns * e2e_steps / e2e_s, "unit": "unknown-updates/s",
+                "h2d_bytes_per_step": bytes_field, "d2h_bytes_per_step": bytes_field,
+                "steps": e2e_steps, "api": "etd_step_host (pinned host field, 1 step per call)"},
+        "field_max_abs": m,
+        "nonfinite": bad,
+    }
+    cs = clocks.summary()
+    if cs:
+        line["clocks"] = cs
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(name)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * etd.h -- C ABI of the GB300 (sm_103a) ETD2RK-DS library.
+ *
+ * The library advances the semi-discrete reaction-diffusion system
+ *     u_t + A_h u = f(t, u)   on (0,1)^d, d = 2 or 3, homogeneous Dirichlet,
+ * A_h = -kappa Laplace_h + q (Section 2.1: second-order centred differences,
+ * n interior points per axis, h = 1/(n+1)), with the Pade-based
+ * dimension-split ETD2RK scheme of Section 3.1, eq. (13)-(14) in 2D and
+ * eq. (15)-(16) in 3D, by the Sylvester (diagonalisation) route of Section 3.3.2:
+ * every shifted 1D solve becomes a product with the eigenvector matrix P of the
+ * 1D operator, a Hadamard scaling by precomputed rational-factor grids, and a
+ * product with P again (Algorithms 1-2, in matrix-matrix form per Remark 2 of
+ * Section 3.4).
+ *
+ * Conventions shared by every call:
+ *   - Field layout: [comp][z][y][x], x fastest, contiguous, no boundary values
+ *     (the Dirichlet zeros are implicit; Section 2.1 vectorisation order).
+ *     Element type: double for ETD_PREC_FP64, float for every other precision.
+ *   - Device pointers must be 16-byte aligned device memory of at least
+ *     n_comp * n^d elements; host pointers any host memory of that size.
+ *   - The caller owns every field pointer. The plan owns P, the grids, all
+ *     workspaces and the carried spectral state; etd_plan_destroy frees them.
+ *   - Every call returns an etd_status; none aborts or throws. Kernel-side
+ *     errors (a bounded wait that gave up, a non-finite field) are reported by
+ *     the next etd_sync (or etd_step_host, which synchronises).
+ *   - Calls on one plan must come from one host thread at a time.
+ */
+#ifndef ETD_H
+#define ETD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct etd_plan etd_plan; /* opaque, library-owned */
+
+typedef enum {
+    ETD_OK = 0,
+    ETD_ERR_INVALID_ARG = 1, /* bad size, pointer, alignment or option */
+    ETD_ERR_OOM = 2,         /* a device allocation failed */
+    ETD_ERR_CUDA = 3,        /* a CUDA runtime or driver call failed */
+    ETD_ERR_UNSUPPORTED = 4, /* valid request this build or GPU cannot run */
+    ETD_ERR_DIVERGED = 5,    /* non-finite values found by etd_field_stats */
+    ETD_ERR_TIMEOUT = 6      /* a device-side wait exceeded its time limit */
+} etd_status;
+
+/* Arithmetic of the eigen-transforms (the dense products with P). */
+enum {
+    ETD_PREC_FP64 = 0,   /* double state, FP64 CUDA-core products */
+    ETD_PREC_FP32 = 1,   /* float state, FP32 CUDA-core products */
+    ETD_PREC_TF32 = 2,   /* float state, one TF32 tensor-core product */
+    ETD_PREC_TF32X3 = 3, /* float state, split TF32: hi*hi + hi*lo + lo*hi (default) */
+    ETD_PREC_BF16X3 = 4, /* float state, BF16 hi/lo split, three products */
+    ETD_PREC_BF16X6 = 5  /* float state, BF16 hi/mid/lo split, six products */
+};
+
+/* Reaction f(t, u), evaluated pointwise (autonomous kinds). */
+enum {
+    ETD_RX_NONE = 0,       /* f = 0 */
+    ETD_RX_LINEAR = 1,     /* f = c u; rx_params[0] = c; any n_comp */
+    ETD_RX_ALLEN_CAHN = 2, /* f = u - u^3; n_comp = 1 (Example 5.1 without forcing) */
+    ETD_RX_FHN = 3         /* FitzHugh-Nagumo (Example 5.3), n_comp = 2:
+                              f_u = u - c3 u^3 - v, f_v = eps (u - a v - b);
+                              rx_params = {c3, eps, a, b} */
+};
+
+/* Time-integration factor family, the pade_order argument. */
+enum {
+    ETD_EXACT_EXP = 0, /* exact exponentials of eq. (9)-(10): e^{-x}, phi_1, phi_2 */
+    ETD_PADE_02 = 2,   /* P_{0,2}: Q_1, Q_2, Q_3 of Section 3.1 */
+    ETD_PADE_04 = 4    /* P_{0,4}: R_1, R_2, R_3 of Section 5 */
+};
+
+typedef struct {
+    int precision;         /* ETD_PREC_*, default ETD_PREC_TF32X3 */
+    int reaction;          /* ETD_RX_*, default ETD_RX_ALLEN_CAHN */
+    double rx_params[8];   /* reaction parameters, see ETD_RX_* */
+    int n_comp;            /* 1 or 2; default 1 */
+    double kappa_comp[2];  /* per-component diffusivity; <= 0 means "use kappa" */
+    void* stream;          /* cudaStream_t the plan launches on; NULL = legacy default */
+    int flags;             /* reserved, must be 0 */
+} etd_options;
+
+/* Performance-relevant facts of a plan (for benchmarks and roofline figures). */
+typedef struct {
+    int d, n, n_comp, precision;
+    int products;                /* tensor-core products per MMA tile (1, 3 or 6; 0 for CUDA cores) */
+    int gemms_per_step;          /* transform passes per time step (8 in 2D, 12 in 3D) */
+    long long unknowns;          /* n_comp * n^d */
+    double gemm_flops;           /* algorithmic flops of one pass, all components: 2 n^(d+1) n_comp */
+    double step_flops;           /* algorithmic flops of one time step (16 n or 24 n per unknown) */
+    long long workspace_bytes;   /* device memory the plan holds */
+} etd_plan_info;
+
+/* Fill *opt with the defaults listed above. */
+etd_status etd_options_default(etd_options* opt);
+
+/*
+ * Create a plan for one problem (Section 2.1 operator, Section 3.1 scheme).
+ *   d          2 or 3
+ *   m          interior points per axis (n), 2 <= m <= 16384 (2D), 2 <= m <= 1024 (3D)
+ *   kappa      diffusivity > 0 (component 0 unless kappa_comp overrides)
+ *   q          potential >= 0, split q/d per axis
+ *   dt         time step tau > 0
+ *   pade_order ETD_PADE_02, ETD_PADE_04 or ETD_EXACT_EXP
+ *   opt        NULL for defaults
+ * Precomputes (FP64 on the host) the eigenvectors P (closed-form sine basis)
+ * and the factor grids E_l(tau lambda_k), allocates every workspace, and
+ * returns the plan in *out (NULL on error).
+ */
+etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q, double dt, int pade_order,
+                           const etd_options* opt);
+
+/*
+ * Advance u_dev (device, layout above) in place by n_steps time steps
+ * (eq. (13)-(16)); the plan's time advances by n_steps * dt. Asynchronous on
+ * the plan stream. The plan carries the spectral coefficients of u between
+ * calls; call etd_plan_invalidate after writing u_dev yourself, or pass a
+ * different pointer (the plan then re-derives them).
+ */
+etd_status etd_step(etd_plan* p, void* u_dev, int n_steps);
+
+/*
+ * Same as etd_step for a HOST array u_host: copies it to a plan-owned device
+ * field, advances n_steps, copies the result back and synchronises. Page-locked
+ * host memory gives asynchronous copies; pageable memory works but is slower.
+ */
+etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps);
+
+/*
+ * Spectral transform of one field (step a2 alone): out = T(in) per component,
+ * T(X) = P_x^T X P_y in 2D and the three mode products in 3D. in and out are
+ * device fields in the layout above ([comp][l][k] / [comp][p][l][k] for the
+ * spectral side). T is its own inverse because P is symmetric and orthogonal.
+ */
+etd_status etd_transform(etd_plan* p, const void* in_dev, void* out_dev);
+
+/* Forget the carried spectral state (after the caller changed u_dev). */
+etd_status etd_plan_invalidate(etd_plan* p);
+
+/* Set the plan time t (used by time-dependent reactions; default 0). */
+etd_status etd_set_time(etd_plan* p, double t);
+
+/* Wait for the plan stream; report device-side errors raised since the last sync. */
+etd_status etd_sync(etd_plan* p);
+
+/*
+ * FP64 diagnostics of a device field (step a8): *max_abs = max |u| and
+ * *n_nonfinite = number of NaN/Inf entries over all components. Synchronises.
+ * Returns ETD_ERR_DIVERGED when n_nonfinite > 0 (outputs still written).
+ */
+etd_status etd_field_stats(etd_plan* p, const void* u_dev, double* max_abs, long long* n_nonfinite);
+
+/* Copy the plan's facts into *info. */
+etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info);
+
+/*
+ * Kernel timing: when enabled, every launch of the plan is bracketed by CUDA
+ * events on the plan stream. etd_kernel_times (after etd_sync) returns, for
+ * kind 0 = transform GEMM passes, 1 = pointwise reaction/split kernels, the
+ * summed milliseconds and launch count since the last reset.
+ */
+etd_status etd_set_timing(etd_plan* p, int enable);
+etd_status etd_kernel_times(etd_plan* p, int kind, double* total_ms, long long* launches);
+
+/* Release every resource of the plan. NULL-safe. */
+etd_status etd_plan_destroy(etd_plan* p);
+
+/* Static description of a status code. */
+const char* etd_status_string(etd_status s);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* etd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ETD_H */

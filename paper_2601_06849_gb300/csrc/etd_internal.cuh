@@ -1,0 +1,161 @@
+// Internal declarations of the ETD2RK-DS CUDA library (not part of the C ABI).
+//
+// Data layout of every internal field buffer: [comp][slow][mid][fast] with the
+// fast axis padded to `ld` elements (a multiple of 4 so that every row starts on
+// a 16-byte boundary, as TMA requires). One transform pass is the product
+//     out(b, mm, nn) = sum_k A[b][mm][k] * P[nn][k]
+// over the fast axis k of A (rows mm = the n^(d-1) other indices), written
+// TRANSPOSED so that the contracted axis becomes the slowest one:
+//     out offset = (nn * n^(d-2) + mm / n) * ld + mm % n.
+// P is the symmetric orthogonal sine basis, so two passes give P X P (2D) and
+// three passes the three mode products (3D), and the same passes invert them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace etd {
+
+enum EpiMode : int {
+    EPI_SPLIT = 0,   // write the value as the next pass's operand
+    EPI_CARRY = 1,   // store the carried spectral state  U^ = value
+    EPI_STAGE1 = 2,  // eq. (13) in the spectral basis -> W^, F^q, operand(W^)
+    EPI_STAGE2 = 3,  // eq. (14) in the spectral basis -> U^+, operand(U^+)
+    EPI_PLAIN = 4    // store the physical field (rows of length n, own pitch)
+};
+
+// How an operand is written for the tensor-core products.
+enum SplitKind : int {
+    SPLIT_NONE = 0,  // one plane, the value itself (CUDA-core products)
+    SPLIT_TF32 = 1,  // hi = rna_tf32(v), lo = rna_tf32(v - hi)
+    SPLIT_TF32_HI = 2  // hi only, rna_tf32(v) (single TF32 product)
+};
+
+enum ErrBits : unsigned { ERR_TIMEOUT = 1u, ERR_BAD_CONFIG = 2u };
+
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <typename T>
+struct Epi {
+    int mode;        // EpiMode
+    int split;       // SplitKind (float only)
+    int d, n, M;     // M = n^(d-1) rows per component
+    int mq;          // M / n = n^(d-2)
+    int ld;          // padded row length of internal buffers
+    long long bs;    // component stride of internal buffers (elements)
+    T* op_hi;        // operand output planes (layout of the next pass)
+    T* op_lo;
+    T* dst;          // EPI_PLAIN destination
+    int ld_dst;
+    long long bs_dst;
+    T* uhat;         // carried spectral state U^   (internal layout)
+    T* what;         // W^ of the current step
+    T* fq;           // E_1(tau A_2) F^ of the current step
+    const T* grid;   // [comp][3][n]: E_1, E_2, E_3 at tau * lambda_k
+    T tau;
+
+    __device__ __forceinline__ void write_operand(long long o, T v) const {
+        if constexpr (sizeof(T) == 4) {
+            if (split == SPLIT_TF32) {
+                float h = tf32_rna(v);
+                op_hi[o] = h;
+                op_lo[o] = tf32_rna(v - h);
+                return;
+            }
+            if (split == SPLIT_TF32_HI) {
+                op_hi[o] = tf32_rna(v);
+                return;
+            }
+        }
+        op_hi[o] = v;
+    }
+
+    // Value v = out(b, mm, nn) with mm = mh * n + ml.
+    __device__ __forceinline__ void apply(int b, int mh, int ml, int nn, T v) const {
+        if (mode == EPI_PLAIN) {
+            dst[b * bs_dst + ((long long)nn * mq + mh) * ld_dst + ml] = v;
+            return;
+        }
+        const long long o = b * bs + ((long long)nn * mq + mh) * ld + ml;
+        switch (mode) {
+            case EPI_SPLIT:
+                write_operand(o, v);
+                break;
+            case EPI_CARRY:
+                uhat[o] = v;
+                break;
+            case EPI_STAGE1: {
+                // spectral indices: k = ml (x mode); 2D l = nn; 3D l = mh, p = nn
+                const T* g = grid + (long long)b * 3 * n;
+                T s = (d == 2) ? g[nn] : g[mh] * g[nn];  // E_1(tau A_2) [E_1(tau A_2^z)]
+                T w = g[ml] * s * uhat[o] + tau * g[n + ml] * s * v;
+                what[o] = w;
+                fq[o] = s * v;
+                write_operand(o, w);
+                break;
+            }
+            case EPI_STAGE2: {
+                const T* g = grid + (long long)b * 3 * n;
+                T u = what[o] + tau * g[2 * n + ml] * (v - fq[o]);
+                uhat[o] = u;
+                write_operand(o, u);
+                break;
+            }
+            default:
+                break;
+        }
+    }
+};
+
+// Reaction / split kernel arguments (steps a1 and a5).
+template <typename T>
+struct Rx {
+    int kind;        // ETD_RX_*, or -1 for "identity" (split u itself)
+    int ncomp, n;
+    long long npts;  // n^d
+    const T* in;
+    int ld_in;
+    long long bs_in;
+    T* out_hi;
+    T* out_lo;
+    int ld_out;
+    long long bs_out;
+    int split;
+    T rp[4];
+};
+
+// ---- launchers (defined in the .cu files) ----
+void launch_gemm_simt_f32(const float* A, const float* P, int M, int n, int nbatch, const Epi<float>& e,
+                          cudaStream_t st);
+void launch_gemm_simt_f64(const double* A, const double* P, int M, int n, int nbatch, const Epi<double>& e,
+                          cudaStream_t st);
+void launch_react_f32(const Rx<float>& r, cudaStream_t st);
+void launch_react_f64(const Rx<double>& r, cudaStream_t st);
+void launch_stats_f32(const float* u, long long count, double* acc, cudaStream_t st);
+void launch_stats_f64(const double* u, long long count, double* acc, cudaStream_t st);
+
+// tcgen05 transform pass (gemm_tc.cu)
+struct TcConfig {
+    int bn;          // tile width along nn (multiple of 16, <= 256)
+    int stages;      // shared-memory pipeline depth
+    int products;    // 1 (TF32) or 3 (split TF32)
+    int tiles_m, tiles_n;
+    int tmem_cols;
+    int smem_bytes;
+    unsigned stage_bytes;
+};
+struct TcMaps;  // opaque holder of CUtensorMap objects (gemm_tc.cu)
+TcConfig tc_choose(int M, int n, int products);
+cudaError_t tc_maps_create(TcMaps** out, const TcConfig& cfg, int M, int n, int nbatch, int ld,
+                           const float* const* a_hi, const float* const* a_lo, int n_a, const float* p_hi,
+                           const float* p_lo);
+void tc_maps_destroy(TcMaps* m);
+cudaError_t launch_gemm_tc(const TcConfig& cfg, const TcMaps* maps, int a_index, int M, int n, int nbatch,
+                           const Epi<float>& e, unsigned* err, cudaStream_t st);
+const char* tc_last_driver_error();
+
+}  // namespace etd

@@ -1,0 +1,651 @@
+// Host side of the ETD2RK-DS library: plan precompute, step orchestration and
+// the C ABI declared in include/etd.h.
+//
+// Plan (Algorithm 1/2, steps 1-2, done once in FP64 on the host):
+//   - A_x = (1/h^2) tridiag(-kappa, 2 kappa + (q/d) h^2, -kappa) has the
+//     orthonormal sine eigenvectors P[j][k] = sqrt(2/(n+1)) sin(pi (j+1)(k+1)/(n+1))
+//     and eigenvalues lambda_k = (4 kappa/h^2) sin^2(pi (k+1)/(2(n+1))) + q/d
+//     (Section 3.3.2 uses A_x = P_x D_x P_x^T; with equal spacing on every axis
+//     P_x = P_y = P_z and only lambda depends on the component's kappa);
+//   - the factor grids E_l(tau lambda_k), l = 1, 2, 3, of the chosen family:
+//     Q_l of Section 3.1 (P_{0,2}), R_l of Section 5 (P_{0,4}), or the exact
+//     exponential functions of eq. (9)-(10). Algorithm 1 stores
+//     d^(l) = Re(r_l / (tau lambda - s)); the real rational E_l = 2 d^(l) is
+//     evaluated directly instead.
+//
+// Step (eq. (13)-(16) in the eigenbasis, where every operator is diagonal; the
+// spectral coefficients U^ of u are carried from step to step):
+//   F = f(t_n, U)                                      reaction kernel
+//   F^ = T(F);  W^ = E1x E1y.. U^ + tau E2x E1y.. F^   d passes, last one fused
+//   W = T(W^)                                          d passes
+//   F_W = f(t_{n+1}, W)                                reaction kernel
+//   F_W^ = T(F_W); U^+ = W^ + tau E3x (F_W^ - E1y.. F^) d passes, last one fused
+//   U+ = T(U^+)                                        d passes
+// T is its own inverse (P symmetric orthogonal), so every pass is the same
+// product with P. 4d passes of 2 n^(d+1) flops: 16 n flops per unknown in 2D,
+// 24 n in 3D.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/etd.h"
+#include "etd_internal.cuh"
+
+using namespace etd;
+
+struct TimedLaunch {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+struct etd_plan {
+    int d = 0, n = 0, ncomp = 1, precision = ETD_PREC_TF32X3, pade = 2, reaction = ETD_RX_ALLEN_CAHN;
+    double rp[8] = {0};
+    double kappa[2] = {0, 0};
+    double q = 0, tau = 0, t = 0;
+    cudaStream_t stream = nullptr;
+    int M = 0, mq = 0, ld = 0;
+    long long bs = 0, npts = 0;
+    size_t elem = 4;
+    int split = SPLIT_NONE;
+    bool use_tc = false;
+    // device memory
+    void* P_hi = nullptr;
+    void* P_lo = nullptr;
+    void* grid = nullptr;
+    void* uhat = nullptr;
+    void* what = nullptr;
+    void* fq = nullptr;
+    void* wphys = nullptr;
+    void* op_hi[2] = {nullptr, nullptr};
+    void* op_lo[2] = {nullptr, nullptr};
+    unsigned* err = nullptr;
+    double* stats = nullptr;
+    void* host_field = nullptr;
+    long long workspace = 0;
+    // carried spectral state
+    bool uhat_valid = false;
+    const void* uhat_src = nullptr;
+    // tensor-core pass
+    TcConfig tc{};
+    TcMaps* maps = nullptr;
+    // timing
+    bool timing = false;
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+etd_status fail(etd_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define ETD_CUDA(call)                                                                              \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess) return fail(ETD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// E_1, E_2, E_3 at x = tau * lambda >= 0 in FP64.
+void factor_grids(int family, double x, double* e) {
+    if (family == ETD_PADE_02) {
+        const double den = x * x + 2 * x + 2;
+        e[0] = 2 / den;
+        e[1] = (x + 2) / den;
+        e[2] = (x + 1) / den;
+    } else if (family == ETD_PADE_04) {
+        const double den = (((x + 4) * x + 12) * x + 24) * x + 24;
+        e[0] = 24 / den;
+        e[1] = (((x + 4) * x + 12) * x + 24) / den;
+        e[2] = (((x + 3) * x + 8) * x + 12) / den;
+    } else {
+        // e^{-x}, (1 - e^{-x})/x, (x - 1 + e^{-x})/x^2; series where x - 1 + e^{-x} cancels
+        e[0] = std::exp(-x);
+        e[1] = (x > 0) ? -std::expm1(-x) / x : 1.0;
+        if (x < 0.05) {
+            double term = 0.5, sum = 0.0;  // sum_{j>=0} (-x)^j / (j+2)!
+            for (int j = 0; j < 10; ++j) {
+                sum += term;
+                term *= -x / (double)(j + 3);
+            }
+            e[2] = sum;
+        } else {
+            e[2] = (x + std::expm1(-x)) / (x * x);
+        }
+    }
+}
+
+// Round to TF32 (10 stored mantissa bits), nearest with ties away from zero.
+float tf32_round_host(float v) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return v;
+    u = (u + 0x1000u) & 0xffffe000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
+etd_status dalloc(etd_plan* p, void** ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? ETD_ERR_OOM : ETD_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    p->workspace += (long long)bytes;
+    return ETD_OK;
+}
+
+void free_plan(etd_plan* p) {
+    void* bufs[] = {p->P_hi, p->P_lo, p->grid, p->uhat, p->what, p->fq, p->wphys, p->op_hi[0], p->op_hi[1],
+                    p->op_lo[0], p->op_lo[1], p->err, p->stats, p->host_field};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (p->maps) tc_maps_destroy(p->maps);
+    for (auto& tl : p->timed) {
+        cudaEventDestroy(tl.a);
+        cudaEventDestroy(tl.b);
+    }
+    for (auto ev : p->pool) cudaEventDestroy(ev);
+    delete p;
+}
+
+cudaEvent_t take_event(etd_plan* p) {
+    if (!p->pool.empty()) {
+        cudaEvent_t e = p->pool.back();
+        p->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct TimerScope {
+    etd_plan* p;
+    int kind;
+    cudaEvent_t a = nullptr;
+    TimerScope(etd_plan* pp, int k) : p(pp), kind(k) {
+        if (p->timing) {
+            a = take_event(p);
+            cudaEventRecord(a, p->stream);
+        }
+    }
+    ~TimerScope() {
+        if (p->timing) {
+            cudaEvent_t b = take_event(p);
+            cudaEventRecord(b, p->stream);
+            p->timed.push_back({kind, a, b});
+        }
+    }
+};
+
+template <typename T>
+Epi<T> base_epi(const etd_plan* p) {
+    Epi<T> e{};
+    e.split = p->split;
+    e.d = p->d;
+    e.n = p->n;
+    e.M = p->M;
+    e.mq = p->mq;
+    e.ld = p->ld;
+    e.bs = p->bs;
+    e.uhat = (T*)p->uhat;
+    e.what = (T*)p->what;
+    e.fq = (T*)p->fq;
+    e.grid = (const T*)p->grid;
+    e.tau = (T)p->tau;
+    return e;
+}
+
+// One pass reading operand buffer `cur`; the epilogue's operand output (if any)
+// goes to buffer 1 - cur.
+template <typename T>
+etd_status run_pass(etd_plan* p, int cur, int mode, void* dst, int ld_dst, long long bs_dst) {
+    Epi<T> e = base_epi<T>(p);
+    e.mode = mode;
+    e.op_hi = (T*)p->op_hi[1 - cur];
+    e.op_lo = (T*)p->op_lo[1 - cur];
+    e.dst = (T*)dst;
+    e.ld_dst = ld_dst;
+    e.bs_dst = bs_dst;
+    TimerScope ts(p, 0);
+    if constexpr (sizeof(T) == 8) {
+        launch_gemm_simt_f64((const double*)p->op_hi[cur], (const double*)p->P_hi, p->M, p->n, p->ncomp, e,
+                             p->stream);
+    } else {
+        if (p->use_tc) {
+            cudaError_t ce = launch_gemm_tc(p->tc, p->maps, cur, p->M, p->n, p->ncomp, e, p->err, p->stream);
+            if (ce != cudaSuccess) return fail(ETD_ERR_CUDA, "tensor-core pass launch: %s", cudaGetErrorString(ce));
+            return ETD_OK;
+        }
+        launch_gemm_simt_f32((const float*)p->op_hi[cur], (const float*)p->P_hi, p->M, p->n, p->ncomp, e,
+                             p->stream);
+    }
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return fail(ETD_ERR_CUDA, "transform pass launch: %s", cudaGetErrorString(ce));
+    return ETD_OK;
+}
+
+// d passes starting from operand buffer `cur`; the last pass uses final_mode.
+template <typename T>
+etd_status run_chain(etd_plan* p, int& cur, int final_mode, void* dst, int ld_dst, long long bs_dst) {
+    for (int pass = 0; pass < p->d; ++pass) {
+        const bool last = pass == p->d - 1;
+        etd_status s = run_pass<T>(p, cur, last ? final_mode : EPI_SPLIT, dst, ld_dst, bs_dst);
+        if (s != ETD_OK) return s;
+        cur = 1 - cur;
+    }
+    return ETD_OK;
+}
+
+// Reaction (kind >= 0) or plain split (kind = -1) of a physical field into operand buffer 0.
+template <typename T>
+etd_status run_react(etd_plan* p, int kind, const void* in, int ld_in, long long bs_in, double t) {
+    (void)t;  // the supported reactions are autonomous
+    Rx<T> r{};
+    r.kind = kind;
+    r.ncomp = p->ncomp;
+    r.n = p->n;
+    r.npts = p->npts;
+    r.in = (const T*)in;
+    r.ld_in = ld_in;
+    r.bs_in = bs_in;
+    r.out_hi = (T*)p->op_hi[0];
+    r.out_lo = (T*)p->op_lo[0];
+    r.ld_out = p->ld;
+    r.bs_out = p->bs;
+    r.split = p->split;
+    for (int i = 0; i < 4; ++i) r.rp[i] = (T)p->rp[i];
+    TimerScope ts(p, 1);
+    if constexpr (sizeof(T) == 8)
+        launch_react_f64(r, p->stream);
+    else
+        launch_react_f32(r, p->stream);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) return fail(ETD_ERR_CUDA, "reaction launch: %s", cudaGetErrorString(ce));
+    return ETD_OK;
+}
+
+template <typename T>
+etd_status step_impl(etd_plan* p, void* u, int n_steps) {
+    const int n = p->n;
+    const long long N = p->npts;
+    etd_status s;
+    int cur = 0;
+    if (!p->uhat_valid || p->uhat_src != u) {
+        if ((s = run_react<T>(p, -1, u, n, N, p->t)) != ETD_OK) return s;
+        cur = 0;
+        if ((s = run_chain<T>(p, cur, EPI_CARRY, nullptr, 0, 0)) != ETD_OK) return s;
+        p->uhat_valid = true;
+        p->uhat_src = u;
+    }
+    for (int it = 0; it < n_steps; ++it) {
+        if ((s = run_react<T>(p, p->reaction, u, n, N, p->t)) != ETD_OK) return s;
+        cur = 0;
+        if ((s = run_chain<T>(p, cur, EPI_STAGE1, nullptr, 0, 0)) != ETD_OK) return s;
+        if ((s = run_chain<T>(p, cur, EPI_PLAIN, p->wphys, p->ld, p->bs)) != ETD_OK) return s;
+        if ((s = run_react<T>(p, p->reaction, p->wphys, p->ld, p->bs, p->t + p->tau)) != ETD_OK) return s;
+        cur = 0;
+        if ((s = run_chain<T>(p, cur, EPI_STAGE2, nullptr, 0, 0)) != ETD_OK) return s;
+        if ((s = run_chain<T>(p, cur, EPI_PLAIN, u, n, N)) != ETD_OK) return s;
+        p->t += p->tau;
+    }
+    return ETD_OK;
+}
+
+etd_status check_device_ptr(const void* ptr, const char* what) {
+    if (!ptr) return fail(ETD_ERR_INVALID_ARG, "%s is NULL", what);
+    if (reinterpret_cast<uintptr_t>(ptr) % 16 != 0) return fail(ETD_ERR_INVALID_ARG, "%s is not 16-byte aligned", what);
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ETD_ERR_INVALID_ARG, "%s: %s", what, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(ETD_ERR_INVALID_ARG, "%s is not device memory", what);
+    return ETD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+etd_status etd_options_default(etd_options* opt) {
+    if (!opt) return fail(ETD_ERR_INVALID_ARG, "opt is NULL");
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = ETD_PREC_TF32X3;
+    opt->reaction = ETD_RX_ALLEN_CAHN;
+    opt->n_comp = 1;
+    return ETD_OK;
+}
+
+etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q, double dt, int pade_order,
+                           const etd_options* opt_in) {
+    if (!out) return fail(ETD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    etd_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        etd_options_default(&opt);
+    if (d != 2 && d != 3) return fail(ETD_ERR_INVALID_ARG, "d must be 2 or 3 (got %d)", d);
+    const int mmax = (d == 2) ? 16384 : 1024;
+    if (m < 2 || m > mmax) return fail(ETD_ERR_INVALID_ARG, "m must be in [2, %d] (got %d)", mmax, m);
+    if (!(kappa > 0) || !std::isfinite(kappa)) return fail(ETD_ERR_INVALID_ARG, "kappa must be > 0");
+    if (!(q >= 0) || !std::isfinite(q)) return fail(ETD_ERR_INVALID_ARG, "q must be >= 0");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(ETD_ERR_INVALID_ARG, "dt must be > 0");
+    if (pade_order != ETD_PADE_02 && pade_order != ETD_PADE_04 && pade_order != ETD_EXACT_EXP)
+        return fail(ETD_ERR_INVALID_ARG, "pade_order must be 2, 4 or 0 (exact exponential)");
+    if (opt.n_comp < 1 || opt.n_comp > 2) return fail(ETD_ERR_INVALID_ARG, "n_comp must be 1 or 2");
+    if (opt.flags != 0) return fail(ETD_ERR_INVALID_ARG, "flags must be 0");
+    if (opt.reaction < ETD_RX_NONE || opt.reaction > ETD_RX_FHN) return fail(ETD_ERR_INVALID_ARG, "unknown reaction");
+    if (opt.reaction == ETD_RX_FHN && opt.n_comp != 2)
+        return fail(ETD_ERR_INVALID_ARG, "FitzHugh-Nagumo needs n_comp = 2");
+    if (opt.reaction == ETD_RX_ALLEN_CAHN && opt.n_comp != 1)
+        return fail(ETD_ERR_INVALID_ARG, "Allen-Cahn needs n_comp = 1");
+    if (opt.precision < ETD_PREC_FP64 || opt.precision > ETD_PREC_BF16X6)
+        return fail(ETD_ERR_INVALID_ARG, "unknown precision");
+    if (opt.precision == ETD_PREC_BF16X3 || opt.precision == ETD_PREC_BF16X6)
+        return fail(ETD_ERR_UNSUPPORTED, "BF16 split precisions are not built yet");
+
+    etd_plan* p = new (std::nothrow) etd_plan();
+    if (!p) return fail(ETD_ERR_OOM, "host allocation failed");
+    p->d = d;
+    p->n = m;
+    p->ncomp = opt.n_comp;
+    p->precision = opt.precision;
+    p->pade = pade_order;
+    p->reaction = opt.reaction;
+    std::memcpy(p->rp, opt.rx_params, sizeof p->rp);
+    for (int c = 0; c < p->ncomp; ++c) p->kappa[c] = (opt.kappa_comp[c] > 0) ? opt.kappa_comp[c] : kappa;
+    p->q = q;
+    p->tau = dt;
+    p->stream = (cudaStream_t)opt.stream;
+    p->elem = (opt.precision == ETD_PREC_FP64) ? 8 : 4;
+    p->use_tc = (opt.precision == ETD_PREC_TF32 || opt.precision == ETD_PREC_TF32X3);
+    p->split = opt.precision == ETD_PREC_TF32X3 ? SPLIT_TF32 : (opt.precision == ETD_PREC_TF32 ? SPLIT_TF32_HI : SPLIT_NONE);
+    const int n = m;
+    p->M = (d == 2) ? n : n * n;
+    p->mq = (d == 2) ? 1 : n;
+    p->ld = (n + 3) / 4 * 4;
+    p->bs = (long long)p->M * p->ld;
+    p->npts = (long long)p->M * n;
+
+    // ---- FP64 precompute ----
+    const double h = 1.0 / (n + 1);
+    const double pi = 3.14159265358979323846;
+    std::vector<double> P((size_t)n * n);
+    const double scale = std::sqrt(2.0 / (n + 1));
+    const long long period = 2LL * (n + 1);
+    for (int j = 0; j < n; ++j)
+        for (int k = 0; k < n; ++k) {
+            const long long r = ((long long)(j + 1) * (k + 1)) % period;  // reduce before sin()
+            P[(size_t)j * n + k] = scale * std::sin(pi * (double)r / (double)(n + 1));
+        }
+    std::vector<double> grid((size_t)p->ncomp * 3 * n);
+    for (int c = 0; c < p->ncomp; ++c)
+        for (int k = 0; k < n; ++k) {
+            const double sk = std::sin(pi * (k + 1) / (2.0 * (n + 1)));
+            const double lam = 4.0 * p->kappa[c] / (h * h) * sk * sk + q / d;
+            double e[3];
+            factor_grids(pade_order, dt * lam, e);
+            for (int l = 0; l < 3; ++l) grid[((size_t)c * 3 + l) * n + k] = e[l];
+        }
+
+    // ---- device buffers ----
+    etd_status s = ETD_OK;
+    const size_t E = p->elem;
+    const size_t field_bytes = (size_t)p->ncomp * p->bs * E;
+    const size_t pbytes = (size_t)n * p->ld * E;
+    const bool two_planes = p->precision == ETD_PREC_TF32X3;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (s == ETD_OK) s = dalloc(p, &p->P_hi, pbytes);
+    if (s == ETD_OK && two_planes) s = dalloc(p, &p->P_lo, pbytes);
+    if (s == ETD_OK) s = dalloc(p, &p->grid, (size_t)p->ncomp * 3 * n * E);
+    if (s == ETD_OK) s = dalloc(p, &p->uhat, field_bytes);
+    if (s == ETD_OK) s = dalloc(p, &p->what, field_bytes);
+    if (s == ETD_OK) s = dalloc(p, &p->fq, field_bytes);
+    if (s == ETD_OK) s = dalloc(p, &p->wphys, field_bytes);
+    for (int i = 0; i < 2 && s == ETD_OK; ++i) {
+        s = dalloc(p, &p->op_hi[i], field_bytes);
+        if (s == ETD_OK && two_planes) s = dalloc(p, &p->op_lo[i], field_bytes);
+    }
+    if (s == ETD_OK) s = dalloc(p, (void**)&p->err, sizeof(unsigned) * 4);
+    if (s == ETD_OK) s = dalloc(p, (void**)&p->stats, sizeof(double) * 4);
+    if (s != ETD_OK) {
+        free_plan(p);
+        return s;
+    }
+    std::vector<char> hostbuf(pbytes, 0);
+    std::vector<char> hostbuf_lo(pbytes, 0);
+    for (int j = 0; j < n; ++j)
+        for (int k = 0; k < n; ++k) {
+            const double v = P[(size_t)j * n + k];
+            const size_t o = (size_t)j * p->ld + k;
+            if (E == 8) {
+                ((double*)hostbuf.data())[o] = v;
+            } else if (p->split == SPLIT_NONE) {
+                ((float*)hostbuf.data())[o] = (float)v;
+            } else {
+                const float hi = tf32_round_host((float)v);
+                ((float*)hostbuf.data())[o] = hi;
+                ((float*)hostbuf_lo.data())[o] = tf32_round_host((float)(v - (double)hi));
+            }
+        }
+    std::vector<char> gbuf((size_t)p->ncomp * 3 * n * E);
+    for (size_t i = 0; i < grid.size(); ++i) {
+        if (E == 8)
+            ((double*)gbuf.data())[i] = grid[i];
+        else
+            ((float*)gbuf.data())[i] = (float)grid[i];
+    }
+    cudaError_t ce = cudaMemcpy(p->P_hi, hostbuf.data(), pbytes, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess && two_planes) ce = cudaMemcpy(p->P_lo, hostbuf_lo.data(), pbytes, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->grid, gbuf.data(), gbuf.size(), cudaMemcpyHostToDevice);
+    // zero the padded operand columns once (they are never written by the passes)
+    for (int i = 0; i < 2 && ce == cudaSuccess; ++i) {
+        ce = cudaMemset(p->op_hi[i], 0, field_bytes);
+        if (ce == cudaSuccess && p->op_lo[i]) ce = cudaMemset(p->op_lo[i], 0, field_bytes);
+    }
+    if (ce == cudaSuccess) ce = cudaMemset(p->err, 0, sizeof(unsigned) * 4);
+    if (ce != cudaSuccess) {
+        free_plan(p);
+        return fail(ETD_ERR_CUDA, "plan upload: %s", cudaGetErrorString(ce));
+    }
+    if (p->use_tc) {
+        p->tc = tc_choose(p->M, n, two_planes ? 3 : 1);
+        const float* ahi[2] = {(const float*)p->op_hi[0], (const float*)p->op_hi[1]};
+        const float* alo[2] = {(const float*)p->op_lo[0], (const float*)p->op_lo[1]};
+        ce = tc_maps_create(&p->maps, p->tc, p->M, n, p->ncomp, p->ld, ahi, alo, 2, (const float*)p->P_hi,
+                            (const float*)p->P_lo);
+        if (ce != cudaSuccess) {
+            std::string why = tc_last_driver_error();
+            free_plan(p);
+            return fail(ETD_ERR_CUDA, "tensor maps: %s %s", cudaGetErrorString(ce), why.c_str());
+        }
+    }
+    *out = p;
+    return ETD_OK;
+}
+
+etd_status etd_step(etd_plan* p, void* u_dev, int n_steps) {
+    if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    if (n_steps < 0) return fail(ETD_ERR_INVALID_ARG, "n_steps must be >= 0");
+    etd_status s = check_device_ptr(u_dev, "u_dev");
+    if (s != ETD_OK) return s;
+    if (n_steps == 0) return ETD_OK;
+    return (p->elem == 8) ? step_impl<double>(p, u_dev, n_steps) : step_impl<float>(p, u_dev, n_steps);
+}
+
+etd_status etd_sync(etd_plan* p) {
+    if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    ETD_CUDA(cudaStreamSynchronize(p->stream));
+    unsigned flags = 0;
+    ETD_CUDA(cudaMemcpy(&flags, p->err, sizeof flags, cudaMemcpyDeviceToHost));
+    if (flags) {
+        ETD_CUDA(cudaMemset(p->err, 0, sizeof(unsigned)));
+        p->uhat_valid = false;
+        if (flags & ERR_TIMEOUT) return fail(ETD_ERR_TIMEOUT, "a device-side wait exceeded its time limit");
+        return fail(ETD_ERR_CUDA, "device error flags 0x%x", flags);
+    }
+    return ETD_OK;
+}
+
+etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps) {
+    if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    if (!u_host) return fail(ETD_ERR_INVALID_ARG, "u_host is NULL");
+    if (n_steps < 0) return fail(ETD_ERR_INVALID_ARG, "n_steps must be >= 0");
+    const size_t bytes = (size_t)p->ncomp * p->npts * p->elem;
+    if (!p->host_field) {
+        etd_status s = dalloc(p, &p->host_field, bytes);
+        if (s != ETD_OK) return s;
+    }
+    ETD_CUDA(cudaMemcpyAsync(p->host_field, u_host, bytes, cudaMemcpyHostToDevice, p->stream));
+    p->uhat_valid = false;  // the field was rewritten from the host
+    etd_status s = (p->elem == 8) ? step_impl<double>(p, p->host_field, n_steps)
+                                  : step_impl<float>(p, p->host_field, n_steps);
+    if (s != ETD_OK) return s;
+    ETD_CUDA(cudaMemcpyAsync(u_host, p->host_field, bytes, cudaMemcpyDeviceToHost, p->stream));
+    return etd_sync(p);
+}
+
+etd_status etd_transform(etd_plan* p, const void* in_dev, void* out_dev) {
+    if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    etd_status s = check_device_ptr(in_dev, "in_dev");
+    if (s == ETD_OK) s = check_device_ptr(out_dev, "out_dev");
+    if (s != ETD_OK) return s;
+    int cur = 0;
+    if (p->elem == 8) {
+        if ((s = run_react<double>(p, -1, in_dev, p->n, p->npts, p->t)) != ETD_OK) return s;
+        s = run_chain<double>(p, cur, EPI_PLAIN, out_dev, p->n, p->npts);
+    } else {
+        if ((s = run_react<float>(p, -1, in_dev, p->n, p->npts, p->t)) != ETD_OK) return s;
+        s = run_chain<float>(p, cur, EPI_PLAIN, out_dev, p->n, p->npts);
+    }
+    return s;
+}
+
+etd_status etd_plan_invalidate(etd_plan* p) {
+    if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    p->uhat_valid = false;
+    p->uhat_src = nullptr;
+    return ETD_OK;
+}
+
+etd_status etd_set_time(etd_plan* p, double t) {
+    if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    if (!std::isfinite(t)) return fail(ETD_ERR_INVALID_ARG, "t must be finite");
+    p->t = t;
+    return ETD_OK;
+}
+
+etd_status etd_field_stats(etd_plan* p, const void* u_dev, double* max_abs, long long* n_nonfinite) {
+    if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    if (!max_abs || !n_nonfinite) return fail(ETD_ERR_INVALID_ARG, "output pointer is NULL");
+    etd_status s = check_device_ptr(u_dev, "u_dev");
+    if (s != ETD_OK) return s;
+    ETD_CUDA(cudaMemsetAsync(p->stats, 0, sizeof(double) * 2, p->stream));
+    const long long count = (long long)p->ncomp * p->npts;
+    if (p->elem == 8)
+        launch_stats_f64((const double*)u_dev, count, p->stats, p->stream);
+    else
+        launch_stats_f32((const float*)u_dev, count, p->stats, p->stream);
+    ETD_CUDA(cudaGetLastError());
+    unsigned long long host[2];
+    ETD_CUDA(cudaMemcpyAsync(host, p->stats, sizeof host, cudaMemcpyDeviceToHost, p->stream));
+    ETD_CUDA(cudaStreamSynchronize(p->stream));
+    std::memcpy(max_abs, &host[0], sizeof(double));
+    *n_nonfinite = (long long)host[1];
+    if (host[1]) return fail(ETD_ERR_DIVERGED, "%llu non-finite values", host[1]);
+    return ETD_OK;
+}
+
+etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
+    if (!p || !info) return fail(ETD_ERR_INVALID_ARG, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->d = p->d;
+    info->n = p->n;
+    info->n_comp = p->ncomp;
+    info->precision = p->precision;
+    info->products = p->use_tc ? p->tc.products : 0;
+    info->gemms_per_step = 4 * p->d;
+    info->unknowns = (long long)p->ncomp * p->npts;
+    info->gemm_flops = 2.0 * (double)p->npts * (double)p->n * p->ncomp;
+    info->step_flops = info->gemm_flops * info->gemms_per_step;
+    info->workspace_bytes = p->workspace;
+    return ETD_OK;
+}
+
+etd_status etd_set_timing(etd_plan* p, int enable) {
+    if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    p->timing = enable != 0;
+    return ETD_OK;
+}
+
+etd_status etd_kernel_times(etd_plan* p, int kind, double* total_ms, long long* launches) {
+    if (!p || !total_ms || !launches) return fail(ETD_ERR_INVALID_ARG, "NULL argument");
+    ETD_CUDA(cudaStreamSynchronize(p->stream));
+    double ms = 0;
+    long long cnt = 0;
+    std::vector<TimedLaunch> keep;
+    for (auto& tl : p->timed) {
+        if (tl.kind == kind) {
+            float f = 0;
+            cudaEventElapsedTime(&f, tl.a, tl.b);
+            ms += f;
+            ++cnt;
+            p->pool.push_back(tl.a);
+            p->pool.push_back(tl.b);
+        } else {
+            keep.push_back(tl);
+        }
+    }
+    p->timed.swap(keep);
+    *total_ms = ms;
+    *launches = cnt;
+    return ETD_OK;
+}
+
+etd_status etd_plan_destroy(etd_plan* p) {
+    if (!p) return ETD_OK;
+    cudaStreamSynchronize(p->stream);
+    free_plan(p);
+    return ETD_OK;
+}
+
+const char* etd_status_string(etd_status s) {
+    switch (s) {
+        case ETD_OK: return "ok";
+        case ETD_ERR_INVALID_ARG: return "invalid argument";
+        case ETD_ERR_OOM: return "out of device memory";
+        case ETD_ERR_CUDA: return "CUDA error";
+        case ETD_ERR_UNSUPPORTED: return "unsupported";
+        case ETD_ERR_DIVERGED: return "non-finite values";
+        case ETD_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+const char* etd_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

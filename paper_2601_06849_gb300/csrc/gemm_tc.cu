@@ -1,0 +1,437 @@
+// Tensor-core transform pass for sm_103a (precisions ETD_PREC_TF32, ETD_PREC_TF32X3):
+//     out(b, mm, nn) = sum_k A[b][mm][k] P[nn][k]     + fused epilogue (etd_internal.cuh)
+//
+// Split TF32 (Section 3.3.2's products done on 5th-generation tensor cores):
+// every operand is stored as hi = rna_tf32(x), lo = rna_tf32(x - hi), and one
+// tile accumulates hi*hi + hi*lo + lo*hi in FP32 in tensor memory, which keeps
+// about 21 bits of each product instead of TF32's 11.
+//
+// One CTA computes a 128 x bn tile (bn <= 256) with 6 warps:
+//   warps 0-3  epilogue: tcgen05.ld of the accumulator lanes 32w..32w+31, the
+//              Hadamard stage of eq. (13)/(14) when this pass ends a transform,
+//              transposed (coalesced) stores;
+//   warp 4     TMA producer (one lane) and tensor-memory allocator (whole warp);
+//   warp 5     MMA issuer (one lane): tcgen05.mma.cta_group::1.kind::tf32.
+// Shared memory holds `stages` k-blocks of 32 FP32 values (128-byte rows,
+// 128-byte swizzle, the canonical K-major layout of the MMA descriptors) for
+// A hi/lo and P hi/lo. Producer and MMA meet on full/empty mbarriers; the
+// accumulator is handed to the epilogue through one more mbarrier signalled by
+// tcgen05.commit.
+//
+// Every wait has a time limit (%globaltimer, 2 s). When one expires the CTA
+// raises ERR_TIMEOUT in the plan's error word, stops issuing work, waits (with
+// a limit) for its own copies and products in flight, frees its tensor memory
+// and returns; later CTAs of the grid see the error word and return at once.
+#include <cuda.h>
+#include <stdio.h>
+
+#include "etd_internal.cuh"
+
+namespace etd {
+
+struct TcMaps {
+    CUtensorMap a_hi[4];
+    CUtensorMap a_lo[4];
+    CUtensorMap p_hi;
+    CUtensorMap p_lo;
+    int n_a;
+};
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BKF = 32;                  // FP32 elements per k-block = one 128-byte row
+constexpr int A_BYTES = BM * BKF * 4;    // 16 KiB per operand plane
+constexpr int NUM_THREADS = 192;
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
+constexpr int SMEM_LIMIT = 227 * 1024 - 1024;  // dynamic bytes; leaves room for the static barriers
+
+struct KParams {
+    int M, n, bn, stages, products, tiles_m, tiles_n, tmem_cols;
+    unsigned stage_bytes, b_bytes, tx_bytes;
+    unsigned* err;
+    Epi<float> e;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete; false on timeout/abort.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* err) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+            *abort_flag = 1;
+            atomicOr(err, ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major operand, 128-byte swizzle:
+// start address >> 4 (bits 0-13), leading byte offset (unused with this
+// swizzle, 16 B), stride byte offset 1024 B between 8-row groups (bits 32-45),
+// descriptor version 1 (bit 46), swizzle mode 2 = 128 B (bits 61-63).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor of kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
+// (bits 7-9 and 10-12 = 2), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    gemm_tf32_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
+                        const __grid_constant__ CUtensorMap mP_hi, const __grid_constant__ CUtensorMap mP_lo,
+                        const KParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ int s_skip;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    __shared__ int s_consumed;
+    __shared__ int s_issued;
+    __shared__ __align__(8) uint64_t s_bar[2 * 8 + 1];  // full[8], empty[8], accum
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) s_skip = (*(volatile unsigned*)p.err != 0u);
+    __syncthreads();
+    if (s_skip) return;
+
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int S = p.stages;
+    volatile int* abort_flag = &s_abort;
+    const uint32_t bar_full = smem_u32(&s_bar[0]);
+    const uint32_t bar_empty = smem_u32(&s_bar[8]);
+    const uint32_t bar_accum = smem_u32(&s_bar[16]);
+
+    int t = blockIdx.x;
+    const int tn = t % p.tiles_n;
+    t /= p.tiles_n;
+    const int tm = t % p.tiles_m;
+    const int b = t / p.tiles_m;
+    const int nk = (p.n + BKF - 1) / BKF;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(bar_full + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, 1);
+        }
+        mbar_init(bar_accum, 1);
+        s_abort = 0;
+        s_consumed = 0;
+        s_issued = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"((uint32_t)p.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == 4 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        const int arow = b * p.M + tm * BM;
+        const int prow = tn * p.bn;
+        int issued = 0;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % S;
+            const uint32_t ph = (uint32_t)((kb / S) & 1);
+            if (!mbar_wait(bar_empty + 8 * s, ph ^ 1u, abort_flag, p.err)) break;
+            const uint32_t st = smem_u32(smem + (size_t)s * p.stage_bytes);
+            const uint32_t fb = bar_full + 8 * s;
+            mbar_expect_tx(fb, p.tx_bytes);
+            const int k0 = kb * BKF;
+            tma_load_2d(st, &mA_hi, fb, k0, arow);
+            tma_load_2d(st + 2 * A_BYTES, &mP_hi, fb, k0, prow);
+            if (p.products == 3) {
+                tma_load_2d(st + A_BYTES, &mA_lo, fb, k0, arow);
+                tma_load_2d(st + 2 * A_BYTES + p.b_bytes, &mP_lo, fb, k0, prow);
+            }
+            issued = kb + 1;
+        }
+        s_issued = issued;
+    } else if (warp == 5 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idesc = idesc_tf32(BM, p.bn);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % S;
+            const uint32_t ph = (uint32_t)((kb / S) & 1);
+            if (!mbar_wait(bar_full + 8 * s, ph, abort_flag, p.err)) break;
+            tc_fence_after();
+            const uint32_t a_hi = smem_u32(smem + (size_t)s * p.stage_bytes);
+            const uint32_t a_lo = a_hi + A_BYTES;
+            const uint32_t b_hi = a_hi + 2 * A_BYTES;
+            const uint32_t b_lo = b_hi + p.b_bytes;
+#pragma unroll
+            for (int kk = 0; kk < BKF / 8; ++kk) {
+                const uint32_t off = kk * 32;  // 8 TF32 values = 32 bytes per MMA
+                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                if (p.products == 3) {
+                    mma_tf32(tmem, sdesc_sw128(a_lo + off), sdesc_sw128(b_hi + off), idesc, acc);
+                    mma_tf32(tmem, sdesc_sw128(a_hi + off), sdesc_sw128(b_lo + off), idesc, 1u);
+                    mma_tf32(tmem, sdesc_sw128(a_hi + off), sdesc_sw128(b_hi + off), idesc, 1u);
+                } else {
+                    mma_tf32(tmem, sdesc_sw128(a_hi + off), sdesc_sw128(b_hi + off), idesc, acc);
+                }
+            }
+            mma_commit(bar_empty + 8 * s);
+            s_consumed = kb + 1;
+        }
+        mma_commit(bar_accum);  // arrives when every product issued above has completed
+    } else if (warp < 4) {
+        // ---------------- epilogue ----------------
+        const bool ok = mbar_wait(bar_accum, 0u, abort_flag, p.err);
+        tc_fence_after();
+        if (ok && !*abort_flag) {
+            const int mm = tm * BM + warp * 32 + lane;
+            const bool row_ok = mm < p.M;
+            const int mh = mm / p.n, ml = mm - mh * p.n;
+            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+            for (int c0 = 0; c0 < p.bn; c0 += 16) {
+                float v[16];
+                tmem_ld16(lane_base + (uint32_t)c0, v);
+                if (row_ok) {
+                    const int nn0 = tn * p.bn + c0;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (nn0 + j < p.n) p.e.apply(b, mh, ml, nn0 + j, v[j]);
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4 && lane == 0 && *abort_flag) {
+        // copies still in flight after an abort: wait for them (bounded) before exit
+        for (int kb = s_consumed; kb < s_issued; ++kb) {
+            const int s = kb % S;
+            const uint32_t fb = bar_full + 8 * s;
+            const unsigned long long t0 = globaltimer();
+            while (!mbar_try(fb, (uint32_t)((kb / S) & 1)) && globaltimer() - t0 < 100000000ull) {
+            }
+        }
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try(bar_accum, 0u) && globaltimer() - t0 < 100000000ull) {
+        }
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 4) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)p.tmem_cols)
+                     : "memory");
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+char g_driver_error[256] = "";
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* map, const float* base, int inner, long long rows, int ld, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) {
+        snprintf(g_driver_error, sizeof g_driver_error, "cuTensorMapEncodeTiled entry point not found");
+        return false;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {(cuuint32_t)BKF, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(g_driver_error, sizeof g_driver_error, "cuTensorMapEncodeTiled failed (%d) inner=%d rows=%lld ld=%d",
+                 (int)r, inner, rows, ld);
+        return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+const char* tc_last_driver_error() { return g_driver_error; }
+
+TcConfig tc_choose(int M, int n, int products) {
+    TcConfig c{};
+    c.products = products;
+    // tile width: the multiple of 16 in [64, 256] that wastes the fewest columns
+    int best = 256, best_waste = 1 << 30;
+    if (n <= 256) {
+        best = ((n + 15) / 16) * 16;
+    } else {
+        for (int bn = 256; bn >= 128; bn -= 16) {
+            const int waste = ((n + bn - 1) / bn) * bn - n;
+            if (waste < best_waste) {
+                best_waste = waste;
+                best = bn;
+            }
+        }
+    }
+    c.bn = best;
+    c.tiles_n = (n + c.bn - 1) / c.bn;
+    c.tiles_m = (M + BM - 1) / BM;
+    c.tmem_cols = 32;
+    while (c.tmem_cols < c.bn) c.tmem_cols *= 2;
+    const unsigned b_bytes = (unsigned)c.bn * BKF * 4;
+    c.stage_bytes = (products == 3) ? 2u * A_BYTES + 2u * b_bytes : (unsigned)A_BYTES + b_bytes;
+    // A hi | A lo | P hi | P lo inside a stage; keep the A-lo slot even when unused
+    // so that every offset stays 1024-byte aligned.
+    if (products != 3) c.stage_bytes = 2u * A_BYTES + b_bytes;
+    int s = (SMEM_LIMIT - 1024) / (int)c.stage_bytes;
+    if (s > 8) s = 8;
+    c.stages = s;
+    c.smem_bytes = s * (int)c.stage_bytes + 1024;
+    return c;
+}
+
+cudaError_t tc_maps_create(TcMaps** out, const TcConfig& cfg, int M, int n, int nbatch, int ld,
+                           const float* const* a_hi, const float* const* a_lo, int n_a, const float* p_hi,
+                           const float* p_lo) {
+    *out = nullptr;
+    if (n_a > 4 || cfg.stages < 2) return cudaErrorInvalidValue;
+    TcMaps* m = new TcMaps();
+    m->n_a = n_a;
+    bool ok = true;
+    for (int i = 0; i < n_a && ok; ++i) {
+        ok = make_map(&m->a_hi[i], a_hi[i], n, (long long)nbatch * M, ld, BM);
+        if (ok) ok = make_map(&m->a_lo[i], a_lo[i] ? a_lo[i] : a_hi[i], n, (long long)nbatch * M, ld, BM);
+    }
+    if (ok) ok = make_map(&m->p_hi, p_hi, n, n, ld, cfg.bn);
+    if (ok) ok = make_map(&m->p_lo, p_lo ? p_lo : p_hi, n, n, ld, cfg.bn);
+    if (!ok) {
+        delete m;
+        return cudaErrorInvalidValue;
+    }
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_tf32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM_LIMIT);
+        if (e != cudaSuccess) {
+            delete m;
+            return e;
+        }
+        attr_set = true;
+    }
+    *out = m;
+    return cudaSuccess;
+}
+
+void tc_maps_destroy(TcMaps* m) { delete m; }
+
+cudaError_t launch_gemm_tc(const TcConfig& cfg, const TcMaps* maps, int a_index, int M, int n, int nbatch,
+                           const Epi<float>& e, unsigned* err, cudaStream_t st) {
+    if (a_index < 0 || a_index >= maps->n_a) return cudaErrorInvalidValue;
+    KParams p;
+    p.M = M;
+    p.n = n;
+    p.bn = cfg.bn;
+    p.stages = cfg.stages;
+    p.products = cfg.products;
+    p.tiles_m = cfg.tiles_m;
+    p.tiles_n = cfg.tiles_n;
+    p.tmem_cols = cfg.tmem_cols;
+    p.stage_bytes = cfg.stage_bytes;
+    p.b_bytes = (unsigned)cfg.bn * BKF * 4;
+    p.tx_bytes = (cfg.products == 3) ? 2u * (A_BYTES + p.b_bytes) : (unsigned)A_BYTES + p.b_bytes;
+    p.err = err;
+    p.e = e;
+    const long long grid = (long long)nbatch * cfg.tiles_m * cfg.tiles_n;
+    gemm_tf32_tc_kernel<<<(unsigned)grid, NUM_THREADS, cfg.smem_bytes, st>>>(
+        maps->a_hi[a_index], maps->a_lo[a_index], maps->p_hi, maps->p_lo, p);
+    return cudaGetLastError();
+}
+
+}  // namespace etd

@@ -1,0 +1,269 @@
+"""Python binding of the ETD2RK-DS CUDA library (include/etd.h).
+
+Argument marshalling only: every step of the time integration runs in the
+sm_103a kernels of ``libetd.so``. The functions named ``etd_*`` mirror the C ABI
+one to one (pointers are passed as integers); :class:`Plan` wraps them for
+torch tensors. PyTorch provides device memory and the stream; nothing here
+computes. If the library has not been built, every call raises
+:class:`EtdError` -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libetd.so")
+
+ETD_OK, ETD_ERR_INVALID_ARG, ETD_ERR_OOM, ETD_ERR_CUDA, ETD_ERR_UNSUPPORTED, ETD_ERR_DIVERGED, ETD_ERR_TIMEOUT = range(7)
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4, "bf16x6": 5}
+REACTION = {"none": 0, "linear": 1, "allen_cahn": 2, "fhn": 3}
+FAMILY = {"exact": 0, 2: 2, 4: 4, 0: 0}
+
+# every symbol include/etd.h declares
+SYMBOLS = (
+    "etd_options_default", "etd_plan_create", "etd_step", "etd_step_host", "etd_transform",
+    "etd_plan_invalidate", "etd_set_time", "etd_sync", "etd_field_stats", "etd_get_plan_info",
+    "etd_set_timing", "etd_kernel_times", "etd_plan_destroy", "etd_status_string", "etd_last_error",
+)
+
+
+class EtdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class etd_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("reaction", ctypes.c_int),
+        ("rx_params", ctypes.c_double * 8),
+        ("n_comp", ctypes.c_int),
+        ("kappa_comp", ctypes.c_double * 2),
+        ("stream", ctypes.c_void_p),
+        ("flags", ctypes.c_int),
+    ]
+
+
+class etd_plan_info(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int), ("n", ctypes.c_int), ("n_comp", ctypes.c_int), ("precision", ctypes.c_int),
+        ("products", ctypes.c_int), ("gemms_per_step", ctypes.c_int),
+        ("unknowns", ctypes.c_longlong), ("gemm_flops", ctypes.c_double), ("step_flops", ctypes.c_double),
+        ("workspace_bytes", ctypes.c_longlong),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libetd.so; raise if it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise EtdError(ETD_ERR_UNSUPPORTED,
+                           f"CUDA library not built: {LIB_PATH} is missing (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+        sig = {
+            "etd_options_default": ([ctypes.POINTER(etd_options)], i),
+            "etd_plan_create": ([ctypes.POINTER(vp), i, i, d, d, d, i, ctypes.POINTER(etd_options)], i),
+            "etd_step": ([vp, vp, i], i),
+            "etd_step_host": ([vp, vp, i], i),
+            "etd_transform": ([vp, vp, vp], i),
+            "etd_plan_invalidate": ([vp], i),
+            "etd_set_time": ([vp, d], i),
+            "etd_sync": ([vp], i),
+            "etd_field_stats": ([vp, vp, ctypes.POINTER(d), ctypes.POINTER(ll)], i),
+            "etd_get_plan_info": ([vp, ctypes.POINTER(etd_plan_info)], i),
+            "etd_set_timing": ([vp, i], i),
+            "etd_kernel_times": ([vp, i, ctypes.POINTER(d), ctypes.POINTER(ll)], i),
+            "etd_plan_destroy": ([vp], i),
+            "etd_status_string": ([i], ctypes.c_char_p),
+            "etd_last_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+        return _lib
+
+
+def _check(status: int) -> None:
+    if status != ETD_OK:
+        L = lib()
+        raise EtdError(status, f"{L.etd_status_string(status).decode()}: {L.etd_last_error().decode()}")
+
+
+# ---- the C ABI, one Python function per entry point --------------------------
+
+def etd_options_default() -> etd_options:
+    o = etd_options()
+    _check(lib().etd_options_default(ctypes.byref(o)))
+    return o
+
+
+def etd_plan_create(d: int, m: int, kappa: float, q: float, dt: float, pade_order: int,
+                    opt: Optional[etd_options] = None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().etd_plan_create(ctypes.byref(h), d, m, kappa, q, dt, pade_order,
+                                 ctypes.byref(opt) if opt is not None else None))
+    return h.value
+
+
+def etd_step(plan: int, u_dev: int, n_steps: int) -> None:
+    _check(lib().etd_step(plan, u_dev, n_steps))
+
+
+def etd_step_host(plan: int, u_host: int, n_steps: int) -> None:
+    _check(lib().etd_step_host(plan, u_host, n_steps))
+
+
+def etd_transform(plan: int, in_dev: int, out_dev: int) -> None:
+    _check(lib().etd_transform(plan, in_dev, out_dev))
+
+
+def etd_plan_invalidate(plan: int) -> None:
+    _check(lib().etd_plan_invalidate(plan))
+
+
+def etd_set_time(plan: int, t: float) -> None:
+    _check(lib().etd_set_time(plan, t))
+
+
+def etd_sync(plan: int) -> None:
+    _check(lib().etd_sync(plan))
+
+
+def etd_field_stats(plan: int, u_dev: int):
+    m, bad = ctypes.c_double(), ctypes.c_longlong()
+    st = lib().etd_field_stats(plan, u_dev, ctypes.byref(m), ctypes.byref(bad))
+    if st not in (ETD_OK, ETD_ERR_DIVERGED):
+        _check(st)
+    return m.value, bad.value
+
+
+def etd_get_plan_info(plan: int) -> etd_plan_info:
+    info = etd_plan_info()
+    _check(lib().etd_get_plan_info(plan, ctypes.byref(info)))
+    return info
+
+
+def etd_set_timing(plan: int, enable: bool) -> None:
+    _check(lib().etd_set_timing(plan, int(bool(enable))))
+
+
+def etd_kernel_times(plan: int, kind: int):
+    ms, cnt = ctypes.c_double(), ctypes.c_longlong()
+    _check(lib().etd_kernel_times(plan, kind, ctypes.byref(ms), ctypes.byref(cnt)))
+    return ms.value, cnt.value
+
+
+def etd_plan_destroy(plan: int) -> None:
+    _check(lib().etd_plan_destroy(plan))
+
+
+# ---- torch-facing wrapper -----------------------------------------------------
+
+class Plan:
+    """One ETD2RK-DS problem on (0,1)^d with n interior points per axis.
+
+    ``pade``: 2 (P_{0,2}), 4 (P_{0,4}) or "exact" (eq. (9)-(10)).
+    ``precision``: one of PRECISION; fields are float64 for "fp64", else float32.
+    """
+
+    def __init__(self, d: int, n: int, kappa: float, q: float, dt: float, pade=2, precision: str = "tf32x3",
+                 reaction: str = "allen_cahn", rx_params: Sequence[float] = (), n_comp: int = 1,
+                 kappa_comp: Optional[Sequence[float]] = None, stream=None):
+        import torch
+
+        self.d, self.n, self.dt, self.n_comp = d, n, dt, n_comp
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        opt = etd_options_default()
+        opt.precision = PRECISION[precision]
+        opt.reaction = REACTION[reaction]
+        for i, v in enumerate(rx_params):
+            opt.rx_params[i] = float(v)
+        opt.n_comp = n_comp
+        if kappa_comp is not None:
+            for i, v in enumerate(kappa_comp):
+                opt.kappa_comp[i] = float(v)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        opt.stream = ctypes.c_void_p(stream.cuda_stream)
+        self.handle = etd_plan_create(d, n, kappa, q, dt, FAMILY[pade], opt)
+
+    @property
+    def shape(self):
+        return (self.n_comp,) + (self.n,) * self.d
+
+    def _check_field(self, u, name="u"):
+        if not u.is_cuda or u.dtype != self.dtype or tuple(u.shape) != self.shape or not u.is_contiguous():
+            raise EtdError(ETD_ERR_INVALID_ARG,
+                           f"{name} must be a contiguous {self.dtype} CUDA tensor of shape {self.shape}, "
+                           f"got {u.dtype} {tuple(u.shape)} on {u.device}")
+
+    def step(self, u, n_steps: int = 1):
+        """Advance u (CUDA tensor, shape (n_comp, n, ..)) in place; asynchronous."""
+        self._check_field(u)
+        etd_step(self.handle, u.data_ptr(), n_steps)
+        return u
+
+    def step_host(self, u_host, n_steps: int = 1):
+        """Advance a CPU tensor in place through etd_step_host (copies inside the call)."""
+        if u_host.is_cuda or u_host.dtype != self.dtype or tuple(u_host.shape) != self.shape or \
+                not u_host.is_contiguous():
+            raise EtdError(ETD_ERR_INVALID_ARG, f"u_host must be a contiguous CPU {self.dtype} tensor {self.shape}")
+        etd_step_host(self.handle, u_host.data_ptr(), n_steps)
+        return u_host
+
+    def transform(self, x):
+        import torch
+
+        self._check_field(x, "x")
+        out = torch.empty_like(x)
+        etd_transform(self.handle, x.data_ptr(), out.data_ptr())
+        return out
+
+    def invalidate(self):
+        etd_plan_invalidate(self.handle)
+
+    def set_time(self, t: float):
+        etd_set_time(self.handle, t)
+
+    def sync(self):
+        etd_sync(self.handle)
+
+    def stats(self, u):
+        self._check_field(u)
+        return etd_field_stats(self.handle, u.data_ptr())
+
+    def info(self) -> etd_plan_info:
+        return etd_get_plan_info(self.handle)
+
+    def set_timing(self, enable: bool):
+        etd_set_timing(self.handle, enable)
+
+    def kernel_times(self, kind: int):
+        return etd_kernel_times(self.handle, kind)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            etd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,65 @@
+"""C ABI checks that need no GPU: the library loads, exports every symbol that
+include/etd.h declares, and rejects bad arguments before touching the device."""
+import os
+import re
+
+import pytest
+
+from paper_2601_06849_gb300 import etd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "etd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(etd_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    return etd.lib()
+
+
+def test_header_and_binding_agree():
+    assert declared_symbols() == sorted(etd.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("args,what", [
+    ((5, 64, 0.1, 0.0, 1e-3, 2), "d"),
+    ((2, 1, 0.1, 0.0, 1e-3, 2), "m"),
+    ((3, 4096, 0.1, 0.0, 1e-3, 2), "m"),
+    ((2, 64, -1.0, 0.0, 1e-3, 2), "kappa"),
+    ((2, 64, 0.1, -0.5, 1e-3, 2), "q"),
+    ((2, 64, 0.1, 0.0, 0.0, 2), "dt"),
+    ((2, 64, 0.1, 0.0, 1e-3, 3), "pade"),
+])
+def test_plan_create_rejects_bad_arguments(lib, args, what):
+    with pytest.raises(etd.EtdError) as ei:
+        etd.etd_plan_create(*args)
+    assert ei.value.status == etd.ETD_ERR_INVALID_ARG
+
+
+def test_reaction_component_mismatch(lib):
+    o = etd.etd_options_default()
+    o.reaction = etd.REACTION["fhn"]
+    o.n_comp = 1
+    with pytest.raises(etd.EtdError) as ei:
+        etd.etd_plan_create(2, 64, 0.1, 0.0, 1e-3, 2, o)
+    assert ei.value.status == etd.ETD_ERR_INVALID_ARG
+
+
+def test_null_plan_calls_fail_cleanly(lib):
+    for call in (lambda: etd.etd_sync(0), lambda: etd.etd_plan_invalidate(0), lambda: etd.etd_set_time(0, 0.0)):
+        with pytest.raises(etd.EtdError):
+            call()
+    etd.etd_plan_destroy(0)  # NULL-safe
+    assert lib.etd_status_string(0) == b"ok"

@@ -1,0 +1,189 @@
+"""Full ETD2RK-DS steps through the C ABI against the FP64 CPU oracle.
+
+Error metric (relative, whole field): max |U_gpu - U_oracle| / max |U_oracle|,
+per component. Bounds per precision (derived in the design notes):
+  fp64    1e-10  (the benchmark spec's FP64 bar)
+  tf32x3  1e-6   (the benchmark spec's split-precision bar)
+  fp32    1e-6   (FP32 CUDA-core products, same storage as tf32x3)
+  tf32    3e-3   (one TF32 product, 11-bit operands: error stated, not a bar)
+Sizes span several 128-row tiles, ragged tails and padded rows (n % 4 != 0).
+"""
+import numpy as np
+import pytest
+
+from gpu_util import need_gpu, rel_err
+from oracle import oracle as O
+from oracle import spectral as S
+from paper_2601_06849_gb300 import etd, inputs
+
+TOL = {"fp64": 1e-10, "tf32x3": 1e-6, "fp32": 1e-6, "tf32": 3e-3}
+FHN = (1.0, 0.01, 0.5, 0.1)  # c3, eps, a, b of the 2D FitzHugh-Nagumo workload
+
+
+def run_gpu(torch, d, n, kappa, q, tau, u0, steps, precision, reaction, rp=(), pade=2, kappa_comp=None):
+    ncomp = u0.shape[0]
+    plan = etd.Plan(d, n, kappa, q, tau, pade=pade, precision=precision, reaction=reaction, rx_params=rp,
+                    n_comp=ncomp, kappa_comp=kappa_comp)
+    u = torch.tensor(u0, dtype=plan.dtype, device="cuda")
+    plan.step(u, steps)
+    plan.sync()
+    out = u.double().cpu().numpy()
+    plan.close()
+    return out
+
+
+def oracle_ref(d, n, kappa, q, tau, u0, steps, reaction, rp=(), pade=2):
+    return O.run(O.Problem(d=d, n=n, kappa=tuple(kappa), q=q, tau=tau, pade=pade, reaction=reaction, rp=rp),
+                 u0, steps)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "fp32", "tf32"])
+def test_allen_cahn_2d_n64_100_steps(precision):
+    """2D Allen-Cahn, n = 64, kappa = 0.01, q = 0, tau = 1e-3, 100 steps."""
+    torch = need_gpu()
+    u0 = inputs.allen_cahn_2d(64, workload=0)
+    ref = oracle_ref(2, 64, (0.01,), 0.0, 1e-3, u0, 100, "allen_cahn")
+    got = run_gpu(torch, 2, 64, 0.01, 0.0, 1e-3, u0, 100, precision, "allen_cahn")
+    assert rel_err(got, ref) < TOL[precision]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "fp32", "tf32"])
+@pytest.mark.parametrize("n", [300, 129])
+def test_fhn_2d_ragged(precision, n):
+    """2D FitzHugh-Nagumo with the workload's parameters on grids with ragged tiles."""
+    torch = need_gpu()
+    u0 = inputs.fhn_uniform(n, 2, workload=1)
+    ref = oracle_ref(2, n, (1e-3, 5e-3), 0.0, 1e-2, u0, 20, "fhn", FHN)
+    got = run_gpu(torch, 2, n, 1e-3, 0.0, 1e-2, u0, 20, precision, "fhn", FHN, kappa_comp=(1e-3, 5e-3))
+    for c in range(2):
+        assert rel_err(got[c], ref[c]) < TOL[precision]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "fp32"])
+@pytest.mark.parametrize("n", [48, 33])
+def test_allen_cahn_3d(precision, n):
+    """3D Allen-Cahn, kappa = 1e-3, q = 0.1, tau = 5e-3, Gaussian bump."""
+    torch = need_gpu()
+    u0 = inputs.gaussian_bump(n, 3)
+    ref = oracle_ref(3, n, (1e-3,), 0.1, 5e-3, u0, 10, "allen_cahn")
+    got = run_gpu(torch, 3, n, 1e-3, 0.1, 5e-3, u0, 10, precision, "allen_cahn")
+    assert rel_err(got, ref) < TOL[precision]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+def test_fhn_3d_two_components(precision):
+    torch = need_gpu()
+    n = 40
+    u0 = inputs.fhn_uniform(n, 3, workload=4)
+    ref = oracle_ref(3, n, (1e-3, 5e-3), 0.05, 1e-2, u0, 8, "fhn", FHN)
+    got = run_gpu(torch, 3, n, 1e-3, 0.05, 1e-2, u0, 8, precision, "fhn", FHN, kappa_comp=(1e-3, 5e-3))
+    for c in range(2):
+        assert rel_err(got[c], ref[c]) < TOL[precision]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("d,n", [(2, 96), (3, 30)])
+def test_pade04(precision, d, n):
+    torch = need_gpu()
+    u0 = inputs.allen_cahn_2d(n, workload=5) if d == 2 else inputs.gaussian_bump(n, 3)
+    ref = oracle_ref(d, n, (0.01,), 0.2, 2e-3, u0, 15, "allen_cahn", pade=4)
+    got = run_gpu(torch, d, n, 0.01, 0.2, 2e-3, u0, 15, precision, "allen_cahn", pade=4)
+    assert rel_err(got, ref) < TOL[precision]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+def test_exact_exponential_2d(precision):
+    """eq. (9)-(10) with exact exponentials against the FP64 Sylvester oracle."""
+    torch = need_gpu()
+    n, tau, steps = 80, 5e-3, 12
+    u0 = inputs.allen_cahn_2d(n, workload=6)
+    P = O.Problem(d=2, n=n, kappa=(1e-3,), q=0.1, tau=tau, reaction="allen_cahn")
+    ref = S.run(P, u0, steps, react=lambda t, u: u - u ** 3, kind="exact")
+    got = run_gpu(torch, 2, n, 1e-3, 0.1, tau, u0, steps, precision, "allen_cahn", pade="exact")
+    assert rel_err(got, ref) < TOL[precision]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("d", [2, 3])
+def test_smallest_grid(precision, d):
+    torch = need_gpu()
+    u0 = inputs.random_field((2,) + (2,) * d, workload=7, scale=0.2)
+    ref = oracle_ref(d, 2, (0.3, 0.1), 0.0, 1e-2, u0, 5, "fhn", FHN)
+    got = run_gpu(torch, d, 2, 0.3, 0.0, 1e-2, u0, 5, precision, "fhn", FHN, kappa_comp=(0.3, 0.1))
+    assert rel_err(got, ref) < TOL[precision]
+
+
+@pytest.mark.gpu
+def test_linear_reaction_two_components():
+    torch = need_gpu()
+    n = 50
+    u0 = inputs.random_field((2, n, n), workload=8)
+    ref = oracle_ref(2, n, (0.02, 0.02), 0.3, 1e-2, u0, 10, "linear", (0.7,))
+    got = run_gpu(torch, 2, n, 0.02, 0.3, 1e-2, u0, 10, "tf32x3", "linear", (0.7,))
+    assert rel_err(got, ref) < TOL["tf32x3"]
+
+
+@pytest.mark.gpu
+def test_split_calls_resume_and_repeat_bitwise():
+    """step(5) + step(5) == step(10) bit for bit (carried spectral state), and a
+    second run of the same input is bit-identical (deterministic reductions)."""
+    torch = need_gpu()
+    n = 130
+    u0 = inputs.fhn_uniform(n, 2, workload=9)
+    plan = etd.Plan(2, n, 1e-3, 0.0, 1e-2, precision="tf32x3", reaction="fhn", rx_params=FHN, n_comp=2,
+                    kappa_comp=(1e-3, 5e-3))
+    a = torch.tensor(u0, dtype=torch.float32, device="cuda")
+    b = a.clone()
+    plan.step(a, 10)
+    plan.invalidate()
+    plan.step(b, 5)
+    plan.step(b, 5)
+    plan.sync()
+    assert torch.equal(a, b)
+    c = torch.tensor(u0, dtype=torch.float32, device="cuda")
+    plan.invalidate()
+    plan.step(c, 10)
+    plan.sync()
+    assert torch.equal(a, c)
+    plan.close()
+
+
+@pytest.mark.gpu
+def test_host_entry_point_and_stats():
+    torch = need_gpu()
+    n = 100
+    u0 = inputs.fhn_uniform(n, 2, workload=10)
+    ref = oracle_ref(2, n, (1e-3, 5e-3), 0.0, 1e-2, u0, 6, "fhn", FHN)
+    plan = etd.Plan(2, n, 1e-3, 0.0, 1e-2, precision="tf32x3", reaction="fhn", rx_params=FHN, n_comp=2,
+                    kappa_comp=(1e-3, 5e-3))
+    host = torch.tensor(u0, dtype=torch.float32).pin_memory()
+    plan.step_host(host, 6)
+    assert rel_err(host.double().numpy(), ref) < TOL["tf32x3"]
+    dev = host.cuda()
+    m, bad = plan.stats(dev)
+    assert bad == 0 and m == pytest.approx(float(np.abs(host.numpy()).max()), rel=1e-7)
+    dev[0, 3, 4] = float("nan")
+    dev[1, 0, 0] = float("inf")
+    m2, bad2 = plan.stats(dev)
+    assert bad2 == 2
+    plan.close()
+
+
+@pytest.mark.gpu
+def test_bad_field_arguments():
+    torch = need_gpu()
+    plan = etd.Plan(2, 64, 0.01, 0.0, 1e-3, precision="tf32x3")
+    with pytest.raises(etd.EtdError):
+        plan.step(torch.zeros((1, 64, 65), device="cuda"))
+    host = torch.zeros((1, 64, 64))
+    with pytest.raises(etd.EtdError) as ei:
+        etd.etd_step(plan.handle, host.data_ptr(), 1)
+    assert ei.value.status == etd.ETD_ERR_INVALID_ARG
+    plan.close()
