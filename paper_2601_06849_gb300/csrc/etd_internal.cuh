@@ -39,6 +39,11 @@ __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float(r);
 }
 
+// The carried spectral state (U^, W^) and the factor grids are FP64 for every
+// precision: in the eigenbasis the linear part of a step is the elementwise
+// product E1x E1y.. U^, so rounding the state or the factors to FP32 would add
+// a systematic relative error of up to 2^-24 per step (about N 2^-24 after N
+// steps). Only the transform operands and the physical fields use T.
 template <typename T>
 struct Epi {
     int mode;        // EpiMode
@@ -52,26 +57,25 @@ struct Epi {
     T* dst;          // EPI_PLAIN destination
     int ld_dst;
     long long bs_dst;
-    T* uhat;         // carried spectral state U^   (internal layout)
-    T* what;         // W^ of the current step
+    double* uhat;    // carried spectral state U^   (internal layout)
+    double* what;    // W^ of the current step
     T* fq;           // E_1(tau A_2) F^ of the current step
-    const T* grid;   // [comp][3][n]: E_1, E_2, E_3 at tau * lambda_k
-    T tau;
+    const double* grid;  // [comp][3][n]: E_1, tau E_2, tau E_3 at tau * lambda_k
 
-    __device__ __forceinline__ void write_operand(long long o, T v) const {
+    __device__ __forceinline__ void write_operand(long long o, double v) const {
         if constexpr (sizeof(T) == 4) {
             if (split == SPLIT_TF32) {
-                float h = tf32_rna(v);
+                const float h = tf32_rna((float)v);
                 op_hi[o] = h;
-                op_lo[o] = tf32_rna(v - h);
+                op_lo[o] = tf32_rna((float)(v - (double)h));
                 return;
             }
             if (split == SPLIT_TF32_HI) {
-                op_hi[o] = tf32_rna(v);
+                op_hi[o] = tf32_rna((float)v);
                 return;
             }
         }
-        op_hi[o] = v;
+        op_hi[o] = (T)v;
     }
 
     // Value v = out(b, mm, nn) with mm = mh * n + ml.
@@ -83,24 +87,24 @@ struct Epi {
         const long long o = b * bs + ((long long)nn * mq + mh) * ld + ml;
         switch (mode) {
             case EPI_SPLIT:
-                write_operand(o, v);
+                write_operand(o, (double)v);
                 break;
             case EPI_CARRY:
-                uhat[o] = v;
+                uhat[o] = (double)v;
                 break;
             case EPI_STAGE1: {
                 // spectral indices: k = ml (x mode); 2D l = nn; 3D l = mh, p = nn
-                const T* g = grid + (long long)b * 3 * n;
-                T s = (d == 2) ? g[nn] : g[mh] * g[nn];  // E_1(tau A_2) [E_1(tau A_2^z)]
-                T w = g[ml] * s * uhat[o] + tau * g[n + ml] * s * v;
+                const double* g = grid + (long long)b * 3 * n;
+                const double s = (d == 2) ? g[nn] : g[mh] * g[nn];  // E_1(tau A_2) [E_1(tau A_2^z)]
+                const double w = (g[ml] * uhat[o] + g[n + ml] * (double)v) * s;
                 what[o] = w;
-                fq[o] = s * v;
+                fq[o] = (T)(s * (double)v);
                 write_operand(o, w);
                 break;
             }
             case EPI_STAGE2: {
-                const T* g = grid + (long long)b * 3 * n;
-                T u = what[o] + tau * g[2 * n + ml] * (v - fq[o]);
+                const double* g = grid + (long long)b * 3 * n;
+                const double u = what[o] + g[2 * n + ml] * ((double)v - (double)fq[o]);
                 uhat[o] = u;
                 write_operand(o, u);
                 break;

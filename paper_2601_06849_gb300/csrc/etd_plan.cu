@@ -207,11 +207,10 @@ Epi<T> base_epi(const etd_plan* p) {
     e.mq = p->mq;
     e.ld = p->ld;
     e.bs = p->bs;
-    e.uhat = (T*)p->uhat;
-    e.what = (T*)p->what;
+    e.uhat = (double*)p->uhat;
+    e.what = (double*)p->what;
     e.fq = (T*)p->fq;
-    e.grid = (const T*)p->grid;
-    e.tau = (T)p->tau;
+    e.grid = (const double*)p->grid;
     return e;
 }
 
@@ -408,7 +407,9 @@ etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q,
             const double lam = 4.0 * p->kappa[c] / (h * h) * sk * sk + q / d;
             double e[3];
             factor_grids(pade_order, dt * lam, e);
-            for (int l = 0; l < 3; ++l) grid[((size_t)c * 3 + l) * n + k] = e[l];
+            grid[((size_t)c * 3 + 0) * n + k] = e[0];
+            grid[((size_t)c * 3 + 1) * n + k] = dt * e[1];
+            grid[((size_t)c * 3 + 2) * n + k] = dt * e[2];
         }
 
     // ---- device buffers ----
@@ -421,9 +422,10 @@ etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q,
     cudaGetDevice(&dev);
     if (s == ETD_OK) s = dalloc(p, &p->P_hi, pbytes);
     if (s == ETD_OK && two_planes) s = dalloc(p, &p->P_lo, pbytes);
-    if (s == ETD_OK) s = dalloc(p, &p->grid, (size_t)p->ncomp * 3 * n * E);
-    if (s == ETD_OK) s = dalloc(p, &p->uhat, field_bytes);
-    if (s == ETD_OK) s = dalloc(p, &p->what, field_bytes);
+    const size_t state_bytes = (size_t)p->ncomp * p->bs * sizeof(double);
+    if (s == ETD_OK) s = dalloc(p, &p->grid, (size_t)p->ncomp * 3 * n * sizeof(double));
+    if (s == ETD_OK) s = dalloc(p, &p->uhat, state_bytes);
+    if (s == ETD_OK) s = dalloc(p, &p->what, state_bytes);
     if (s == ETD_OK) s = dalloc(p, &p->fq, field_bytes);
     if (s == ETD_OK) s = dalloc(p, &p->wphys, field_bytes);
     for (int i = 0; i < 2 && s == ETD_OK; ++i) {
@@ -452,16 +454,9 @@ etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q,
                 ((float*)hostbuf_lo.data())[o] = tf32_round_host((float)(v - (double)hi));
             }
         }
-    std::vector<char> gbuf((size_t)p->ncomp * 3 * n * E);
-    for (size_t i = 0; i < grid.size(); ++i) {
-        if (E == 8)
-            ((double*)gbuf.data())[i] = grid[i];
-        else
-            ((float*)gbuf.data())[i] = (float)grid[i];
-    }
     cudaError_t ce = cudaMemcpy(p->P_hi, hostbuf.data(), pbytes, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess && two_planes) ce = cudaMemcpy(p->P_lo, hostbuf_lo.data(), pbytes, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess) ce = cudaMemcpy(p->grid, gbuf.data(), gbuf.size(), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(p->grid, grid.data(), grid.size() * sizeof(double), cudaMemcpyHostToDevice);
     // zero the padded operand columns once (they are never written by the passes)
     for (int i = 0; i < 2 && ce == cudaSuccess; ++i) {
         ce = cudaMemset(p->op_hi[i], 0, field_bytes);
