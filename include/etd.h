@@ -49,10 +49,13 @@ enum {
     ETD_PREC_FP64 = 0,   /* double state, FP64 CUDA-core products */
     ETD_PREC_FP32 = 1,   /* float state, FP32 CUDA-core products */
     ETD_PREC_TF32 = 2,   /* float state, one TF32 tensor-core product */
-    ETD_PREC_TF32X3 = 3, /* float state, split TF32: hi*hi + hi*lo + lo*hi (default) */
-    ETD_PREC_BF16X3 = 4, /* float state, BF16 hi/lo split, three products */
-    ETD_PREC_BF16X6 = 5  /* float state, BF16 hi/mid/lo split, six products */
+    ETD_PREC_TF32X3 = 3, /* float fields, split TF32: hi*hi + hi*lo + lo*hi; the transform
+                            that returns the field uses the six-product split (default) */
+    ETD_PREC_BF16X3 = 4, /* float fields, BF16 hi/lo split, three products */
+    ETD_PREC_BF16X6 = 5, /* float fields, BF16 hi/mid/lo split, six products */
+    ETD_PREC_TF32X6 = 6  /* float fields, three-piece TF32 split, six products in every pass */
 };
+/* Every precision keeps the carried spectral state and the factor grids in FP64. */
 
 /* Reaction f(t, u), evaluated pointwise (autonomous kinds). */
 enum {

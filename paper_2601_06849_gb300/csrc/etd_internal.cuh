@@ -26,9 +26,10 @@ enum EpiMode : int {
 
 // How an operand is written for the tensor-core products.
 enum SplitKind : int {
-    SPLIT_NONE = 0,  // one plane, the value itself (CUDA-core products)
-    SPLIT_TF32 = 1,  // hi = rna_tf32(v), lo = rna_tf32(v - hi)
-    SPLIT_TF32_HI = 2  // hi only, rna_tf32(v) (single TF32 product)
+    SPLIT_NONE = 0,     // one plane, the value itself (CUDA-core products)
+    SPLIT_TF32 = 1,     // hi = rna_tf32(v), lo = rna_tf32(v - hi)
+    SPLIT_TF32_HI = 2,  // hi only, rna_tf32(v) (single TF32 product)
+    SPLIT_TF32_3 = 3    // hi, mid = rna_tf32(v - hi), lo = rna_tf32(v - hi - mid)
 };
 
 enum ErrBits : unsigned { ERR_TIMEOUT = 1u, ERR_BAD_CONFIG = 2u };
@@ -54,6 +55,7 @@ struct Epi {
     long long bs;    // component stride of internal buffers (elements)
     T* op_hi;        // operand output planes (layout of the next pass)
     T* op_lo;
+    T* op_lo2;       // third piece (SPLIT_TF32_3)
     T* dst;          // EPI_PLAIN destination
     int ld_dst;
     long long bs_dst;
@@ -72,6 +74,15 @@ struct Epi {
             }
             if (split == SPLIT_TF32_HI) {
                 op_hi[o] = tf32_rna((float)v);
+                return;
+            }
+            if (split == SPLIT_TF32_3) {
+                const float h = tf32_rna((float)v);
+                const double r = v - (double)h;
+                const float m = tf32_rna((float)r);
+                op_hi[o] = h;
+                op_lo[o] = m;
+                op_lo2[o] = tf32_rna((float)(r - (double)m));
                 return;
             }
         }
@@ -126,6 +137,7 @@ struct Rx {
     long long bs_in;
     T* out_hi;
     T* out_lo;
+    T* out_lo2;
     int ld_out;
     long long bs_out;
     int split;
@@ -144,9 +156,10 @@ void launch_stats_f64(const double* u, long long count, double* acc, cudaStream_
 
 // tcgen05 transform pass (gemm_tc.cu)
 struct TcConfig {
-    int bn;          // tile width along nn (multiple of 16, <= 256)
+    int bn;          // tile width along nn (multiple of 32, <= 256)
     int stages;      // shared-memory pipeline depth
-    int products;    // 1 (TF32) or 3 (split TF32)
+    int products;    // 1 (TF32), 3 (two-piece split) or 6 (three-piece split)
+    int pieces;      // operand pieces read per product mode
     int tiles_m, tiles_n;
     int tmem_cols;
     int smem_bytes;
@@ -154,11 +167,12 @@ struct TcConfig {
 };
 struct TcMaps;  // opaque holder of CUtensorMap objects (gemm_tc.cu)
 TcConfig tc_choose(int M, int n, int products);
-cudaError_t tc_maps_create(TcMaps** out, const TcConfig& cfg, int M, int n, int nbatch, int ld,
-                           const float* const* a_hi, const float* const* a_lo, int n_a, const float* p_hi,
-                           const float* p_lo);
+// a[i][j]: operand buffer i, piece j (NULL = reuse piece 0); pp[j]: pieces of P;
+// bn_slot: tile widths of the two configurations the maps serve.
+cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const float* const a[][3], int n_a,
+                           const float* const pp[3], const int bn_slot[2]);
 void tc_maps_destroy(TcMaps* m);
-cudaError_t launch_gemm_tc(const TcConfig& cfg, const TcMaps* maps, int a_index, int M, int n, int nbatch,
+cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, int a_index, int M, int n, int nbatch,
                            const Epi<float>& e, unsigned* err, cudaStream_t st);
 const char* tc_last_driver_error();
 

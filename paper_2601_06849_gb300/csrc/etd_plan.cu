@@ -53,18 +53,17 @@ struct etd_plan {
     int M = 0, mq = 0, ld = 0;
     long long bs = 0, npts = 0;
     size_t elem = 4;
-    int split = SPLIT_NONE;
     bool use_tc = false;
+    int pieces = 1;     // operand planes allocated per buffer
+    int out_slot = 0;   // config slot of the transform that returns the field
     // device memory
-    void* P_hi = nullptr;
-    void* P_lo = nullptr;
+    void* P[3] = {nullptr, nullptr, nullptr};  // pieces of the sine basis
     void* grid = nullptr;
     void* uhat = nullptr;
     void* what = nullptr;
     void* fq = nullptr;
     void* wphys = nullptr;
-    void* op_hi[2] = {nullptr, nullptr};
-    void* op_lo[2] = {nullptr, nullptr};
+    void* op[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // operand buffers x pieces
     unsigned* err = nullptr;
     double* stats = nullptr;
     void* host_field = nullptr;
@@ -72,8 +71,8 @@ struct etd_plan {
     // carried spectral state
     bool uhat_valid = false;
     const void* uhat_src = nullptr;
-    // tensor-core pass
-    TcConfig tc{};
+    // tensor-core pass: slot 0 = every internal pass, slot 1 = the output transform
+    TcConfig tc[2] = {};
     TcMaps* maps = nullptr;
     // timing
     bool timing = false;
@@ -154,8 +153,9 @@ etd_status dalloc(etd_plan* p, void** ptr, size_t bytes) {
 }
 
 void free_plan(etd_plan* p) {
-    void* bufs[] = {p->P_hi, p->P_lo, p->grid, p->uhat, p->what, p->fq, p->wphys, p->op_hi[0], p->op_hi[1],
-                    p->op_lo[0], p->op_lo[1], p->err, p->stats, p->host_field};
+    void* bufs[] = {p->P[0],     p->P[1],     p->P[2],     p->grid,     p->uhat,     p->what,
+                    p->fq,       p->wphys,    p->op[0][0], p->op[0][1], p->op[0][2], p->op[1][0],
+                    p->op[1][1], p->op[1][2], p->err,      p->stats,    p->host_field};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->maps) tc_maps_destroy(p->maps);
@@ -200,7 +200,6 @@ struct TimerScope {
 template <typename T>
 Epi<T> base_epi(const etd_plan* p) {
     Epi<T> e{};
-    e.split = p->split;
     e.d = p->d;
     e.n = p->n;
     e.M = p->M;
@@ -214,28 +213,38 @@ Epi<T> base_epi(const etd_plan* p) {
     return e;
 }
 
-// One pass reading operand buffer `cur`; the epilogue's operand output (if any)
-// goes to buffer 1 - cur.
+int split_for(const etd_plan* p, int slot) {
+    if (!p->use_tc) return SPLIT_NONE;
+    const int pieces = p->tc[slot].pieces;
+    return pieces == 3 ? SPLIT_TF32_3 : (pieces == 2 ? SPLIT_TF32 : SPLIT_TF32_HI);
+}
+
+// One pass reading operand buffer `cur` with the products of config `slot`; the
+// epilogue's operand output (if any) goes to buffer 1 - cur split as `out_split`.
 template <typename T>
-etd_status run_pass(etd_plan* p, int cur, int mode, void* dst, int ld_dst, long long bs_dst) {
+etd_status run_pass(etd_plan* p, int cur, int slot, int mode, int out_split, void* dst, int ld_dst,
+                    long long bs_dst) {
     Epi<T> e = base_epi<T>(p);
     e.mode = mode;
-    e.op_hi = (T*)p->op_hi[1 - cur];
-    e.op_lo = (T*)p->op_lo[1 - cur];
+    e.split = out_split;
+    e.op_hi = (T*)p->op[1 - cur][0];
+    e.op_lo = (T*)p->op[1 - cur][1];
+    e.op_lo2 = (T*)p->op[1 - cur][2];
     e.dst = (T*)dst;
     e.ld_dst = ld_dst;
     e.bs_dst = bs_dst;
     TimerScope ts(p, 0);
     if constexpr (sizeof(T) == 8) {
-        launch_gemm_simt_f64((const double*)p->op_hi[cur], (const double*)p->P_hi, p->M, p->n, p->ncomp, e,
+        launch_gemm_simt_f64((const double*)p->op[cur][0], (const double*)p->P[0], p->M, p->n, p->ncomp, e,
                              p->stream);
     } else {
         if (p->use_tc) {
-            cudaError_t ce = launch_gemm_tc(p->tc, p->maps, cur, p->M, p->n, p->ncomp, e, p->err, p->stream);
+            cudaError_t ce =
+                launch_gemm_tc(p->tc[slot], slot, p->maps, cur, p->M, p->n, p->ncomp, e, p->err, p->stream);
             if (ce != cudaSuccess) return fail(ETD_ERR_CUDA, "tensor-core pass launch: %s", cudaGetErrorString(ce));
             return ETD_OK;
         }
-        launch_gemm_simt_f32((const float*)p->op_hi[cur], (const float*)p->P_hi, p->M, p->n, p->ncomp, e,
+        launch_gemm_simt_f32((const float*)p->op[cur][0], (const float*)p->P[0], p->M, p->n, p->ncomp, e,
                              p->stream);
     }
     cudaError_t ce = cudaGetLastError();
@@ -243,12 +252,15 @@ etd_status run_pass(etd_plan* p, int cur, int mode, void* dst, int ld_dst, long 
     return ETD_OK;
 }
 
-// d passes starting from operand buffer `cur`; the last pass uses final_mode.
+// d passes of config `slot` starting from operand buffer `cur`; the last pass
+// uses final_mode and, if it writes an operand, splits it as final_split.
 template <typename T>
-etd_status run_chain(etd_plan* p, int& cur, int final_mode, void* dst, int ld_dst, long long bs_dst) {
+etd_status run_chain(etd_plan* p, int& cur, int slot, int final_mode, int final_split, void* dst, int ld_dst,
+                     long long bs_dst) {
     for (int pass = 0; pass < p->d; ++pass) {
         const bool last = pass == p->d - 1;
-        etd_status s = run_pass<T>(p, cur, last ? final_mode : EPI_SPLIT, dst, ld_dst, bs_dst);
+        etd_status s = run_pass<T>(p, cur, slot, last ? final_mode : EPI_SPLIT, last ? final_split : split_for(p, slot),
+                                   dst, ld_dst, bs_dst);
         if (s != ETD_OK) return s;
         cur = 1 - cur;
     }
@@ -257,7 +269,7 @@ etd_status run_chain(etd_plan* p, int& cur, int final_mode, void* dst, int ld_ds
 
 // Reaction (kind >= 0) or plain split (kind = -1) of a physical field into operand buffer 0.
 template <typename T>
-etd_status run_react(etd_plan* p, int kind, const void* in, int ld_in, long long bs_in, double t) {
+etd_status run_react(etd_plan* p, int kind, const void* in, int ld_in, long long bs_in, double t, int split) {
     (void)t;  // the supported reactions are autonomous
     Rx<T> r{};
     r.kind = kind;
@@ -267,11 +279,12 @@ etd_status run_react(etd_plan* p, int kind, const void* in, int ld_in, long long
     r.in = (const T*)in;
     r.ld_in = ld_in;
     r.bs_in = bs_in;
-    r.out_hi = (T*)p->op_hi[0];
-    r.out_lo = (T*)p->op_lo[0];
+    r.out_hi = (T*)p->op[0][0];
+    r.out_lo = (T*)p->op[0][1];
+    r.out_lo2 = (T*)p->op[0][2];
     r.ld_out = p->ld;
     r.bs_out = p->bs;
-    r.split = p->split;
+    r.split = split;
     for (int i = 0; i < 4; ++i) r.rp[i] = (T)p->rp[i];
     TimerScope ts(p, 1);
     if constexpr (sizeof(T) == 8)
@@ -283,28 +296,34 @@ etd_status run_react(etd_plan* p, int kind, const void* in, int ld_in, long long
     return ETD_OK;
 }
 
+// n_steps time steps. Every transform runs with config slot 0, except the one
+// that produces the field handed back to the caller (last step), which runs
+// with p->out_slot: that field is the only result that is not damped by tau
+// before it matters, so only it gets the six-product split in TF32X3 mode.
 template <typename T>
 etd_status step_impl(etd_plan* p, void* u, int n_steps) {
     const int n = p->n;
     const long long N = p->npts;
+    const int sp0 = split_for(p, 0), spo = split_for(p, p->out_slot);
     etd_status s;
     int cur = 0;
     if (!p->uhat_valid || p->uhat_src != u) {
-        if ((s = run_react<T>(p, -1, u, n, N, p->t)) != ETD_OK) return s;
+        if ((s = run_react<T>(p, -1, u, n, N, p->t, sp0)) != ETD_OK) return s;
         cur = 0;
-        if ((s = run_chain<T>(p, cur, EPI_CARRY, nullptr, 0, 0)) != ETD_OK) return s;
+        if ((s = run_chain<T>(p, cur, 0, EPI_CARRY, sp0, nullptr, 0, 0)) != ETD_OK) return s;
         p->uhat_valid = true;
         p->uhat_src = u;
     }
     for (int it = 0; it < n_steps; ++it) {
-        if ((s = run_react<T>(p, p->reaction, u, n, N, p->t)) != ETD_OK) return s;
+        const bool last = it == n_steps - 1;
+        if ((s = run_react<T>(p, p->reaction, u, n, N, p->t, sp0)) != ETD_OK) return s;
         cur = 0;
-        if ((s = run_chain<T>(p, cur, EPI_STAGE1, nullptr, 0, 0)) != ETD_OK) return s;
-        if ((s = run_chain<T>(p, cur, EPI_PLAIN, p->wphys, p->ld, p->bs)) != ETD_OK) return s;
-        if ((s = run_react<T>(p, p->reaction, p->wphys, p->ld, p->bs, p->t + p->tau)) != ETD_OK) return s;
+        if ((s = run_chain<T>(p, cur, 0, EPI_STAGE1, sp0, nullptr, 0, 0)) != ETD_OK) return s;
+        if ((s = run_chain<T>(p, cur, 0, EPI_PLAIN, sp0, p->wphys, p->ld, p->bs)) != ETD_OK) return s;
+        if ((s = run_react<T>(p, p->reaction, p->wphys, p->ld, p->bs, p->t + p->tau, sp0)) != ETD_OK) return s;
         cur = 0;
-        if ((s = run_chain<T>(p, cur, EPI_STAGE2, nullptr, 0, 0)) != ETD_OK) return s;
-        if ((s = run_chain<T>(p, cur, EPI_PLAIN, u, n, N)) != ETD_OK) return s;
+        if ((s = run_chain<T>(p, cur, 0, EPI_STAGE2, last ? spo : sp0, nullptr, 0, 0)) != ETD_OK) return s;
+        if ((s = run_chain<T>(p, cur, last ? p->out_slot : 0, EPI_PLAIN, sp0, u, n, N)) != ETD_OK) return s;
         p->t += p->tau;
     }
     return ETD_OK;
@@ -361,7 +380,7 @@ etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q,
         return fail(ETD_ERR_INVALID_ARG, "FitzHugh-Nagumo needs n_comp = 2");
     if (opt.reaction == ETD_RX_ALLEN_CAHN && opt.n_comp != 1)
         return fail(ETD_ERR_INVALID_ARG, "Allen-Cahn needs n_comp = 1");
-    if (opt.precision < ETD_PREC_FP64 || opt.precision > ETD_PREC_BF16X6)
+    if (opt.precision < ETD_PREC_FP64 || opt.precision > ETD_PREC_TF32X6)
         return fail(ETD_ERR_INVALID_ARG, "unknown precision");
     if (opt.precision == ETD_PREC_BF16X3 || opt.precision == ETD_PREC_BF16X6)
         return fail(ETD_ERR_UNSUPPORTED, "BF16 split precisions are not built yet");
@@ -380,8 +399,8 @@ etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q,
     p->tau = dt;
     p->stream = (cudaStream_t)opt.stream;
     p->elem = (opt.precision == ETD_PREC_FP64) ? 8 : 4;
-    p->use_tc = (opt.precision == ETD_PREC_TF32 || opt.precision == ETD_PREC_TF32X3);
-    p->split = opt.precision == ETD_PREC_TF32X3 ? SPLIT_TF32 : (opt.precision == ETD_PREC_TF32 ? SPLIT_TF32_HI : SPLIT_NONE);
+    p->use_tc = (opt.precision == ETD_PREC_TF32 || opt.precision == ETD_PREC_TF32X3 ||
+                 opt.precision == ETD_PREC_TF32X6);
     const int n = m;
     p->M = (d == 2) ? n : n * n;
     p->mq = (d == 2) ? 1 : n;
@@ -412,67 +431,79 @@ etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q,
             grid[((size_t)c * 3 + 2) * n + k] = dt * e[2];
         }
 
+    // ---- tensor-core configurations ----
+    if (p->use_tc) {
+        const int prod0 = opt.precision == ETD_PREC_TF32 ? 1 : (opt.precision == ETD_PREC_TF32X6 ? 6 : 3);
+        p->tc[0] = tc_choose(p->M, n, prod0);
+        if (opt.precision == ETD_PREC_TF32X3) {
+            p->tc[1] = tc_choose(p->M, n, 6);
+            p->out_slot = 1;
+        } else {
+            p->tc[1] = p->tc[0];
+        }
+        p->pieces = p->tc[0].pieces > p->tc[1].pieces ? p->tc[0].pieces : p->tc[1].pieces;
+    }
+
     // ---- device buffers ----
     etd_status s = ETD_OK;
     const size_t E = p->elem;
     const size_t field_bytes = (size_t)p->ncomp * p->bs * E;
-    const size_t pbytes = (size_t)n * p->ld * E;
-    const bool two_planes = p->precision == ETD_PREC_TF32X3;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (s == ETD_OK) s = dalloc(p, &p->P_hi, pbytes);
-    if (s == ETD_OK && two_planes) s = dalloc(p, &p->P_lo, pbytes);
     const size_t state_bytes = (size_t)p->ncomp * p->bs * sizeof(double);
+    const size_t pbytes = (size_t)n * p->ld * E;
+    for (int j = 0; j < p->pieces && s == ETD_OK; ++j) s = dalloc(p, &p->P[j], pbytes);
     if (s == ETD_OK) s = dalloc(p, &p->grid, (size_t)p->ncomp * 3 * n * sizeof(double));
     if (s == ETD_OK) s = dalloc(p, &p->uhat, state_bytes);
     if (s == ETD_OK) s = dalloc(p, &p->what, state_bytes);
     if (s == ETD_OK) s = dalloc(p, &p->fq, field_bytes);
     if (s == ETD_OK) s = dalloc(p, &p->wphys, field_bytes);
-    for (int i = 0; i < 2 && s == ETD_OK; ++i) {
-        s = dalloc(p, &p->op_hi[i], field_bytes);
-        if (s == ETD_OK && two_planes) s = dalloc(p, &p->op_lo[i], field_bytes);
-    }
+    for (int i = 0; i < 2 && s == ETD_OK; ++i)
+        for (int j = 0; j < p->pieces && s == ETD_OK; ++j) s = dalloc(p, &p->op[i][j], field_bytes);
     if (s == ETD_OK) s = dalloc(p, (void**)&p->err, sizeof(unsigned) * 4);
     if (s == ETD_OK) s = dalloc(p, (void**)&p->stats, sizeof(double) * 4);
     if (s != ETD_OK) {
         free_plan(p);
         return s;
     }
-    std::vector<char> hostbuf(pbytes, 0);
-    std::vector<char> hostbuf_lo(pbytes, 0);
-    for (int j = 0; j < n; ++j)
-        for (int k = 0; k < n; ++k) {
-            const double v = P[(size_t)j * n + k];
-            const size_t o = (size_t)j * p->ld + k;
-            if (E == 8) {
-                ((double*)hostbuf.data())[o] = v;
-            } else if (p->split == SPLIT_NONE) {
-                ((float*)hostbuf.data())[o] = (float)v;
-            } else {
-                const float hi = tf32_round_host((float)v);
-                ((float*)hostbuf.data())[o] = hi;
-                ((float*)hostbuf_lo.data())[o] = tf32_round_host((float)(v - (double)hi));
+    // P in its pieces: FP64 for ETD_PREC_FP64, FP32 for FP32 products, TF32
+    // pieces (each rounded from the FP64 remainder) for the tensor-core modes
+    cudaError_t ce = cudaSuccess;
+    for (int j = 0; j < p->pieces && ce == cudaSuccess; ++j) {
+        std::vector<char> hostbuf(pbytes, 0);
+        for (int r = 0; r < n; ++r)
+            for (int k = 0; k < n; ++k) {
+                double v = P[(size_t)r * n + k];
+                const size_t o = (size_t)r * p->ld + k;
+                if (E == 8) {
+                    ((double*)hostbuf.data())[o] = v;
+                } else if (!p->use_tc) {
+                    ((float*)hostbuf.data())[o] = (float)v;
+                } else {
+                    float piece = 0.f;
+                    for (int q = 0; q <= j; ++q) {
+                        piece = tf32_round_host((float)v);
+                        v -= (double)piece;
+                    }
+                    ((float*)hostbuf.data())[o] = piece;
+                }
             }
-        }
-    cudaError_t ce = cudaMemcpy(p->P_hi, hostbuf.data(), pbytes, cudaMemcpyHostToDevice);
-    if (ce == cudaSuccess && two_planes) ce = cudaMemcpy(p->P_lo, hostbuf_lo.data(), pbytes, cudaMemcpyHostToDevice);
+        ce = cudaMemcpy(p->P[j], hostbuf.data(), pbytes, cudaMemcpyHostToDevice);
+    }
     if (ce == cudaSuccess) ce = cudaMemcpy(p->grid, grid.data(), grid.size() * sizeof(double), cudaMemcpyHostToDevice);
     // zero the padded operand columns once (they are never written by the passes)
-    for (int i = 0; i < 2 && ce == cudaSuccess; ++i) {
-        ce = cudaMemset(p->op_hi[i], 0, field_bytes);
-        if (ce == cudaSuccess && p->op_lo[i]) ce = cudaMemset(p->op_lo[i], 0, field_bytes);
-    }
+    for (int i = 0; i < 2 && ce == cudaSuccess; ++i)
+        for (int j = 0; j < p->pieces && ce == cudaSuccess; ++j) ce = cudaMemset(p->op[i][j], 0, field_bytes);
     if (ce == cudaSuccess) ce = cudaMemset(p->err, 0, sizeof(unsigned) * 4);
     if (ce != cudaSuccess) {
         free_plan(p);
         return fail(ETD_ERR_CUDA, "plan upload: %s", cudaGetErrorString(ce));
     }
     if (p->use_tc) {
-        p->tc = tc_choose(p->M, n, two_planes ? 3 : 1);
-        const float* ahi[2] = {(const float*)p->op_hi[0], (const float*)p->op_hi[1]};
-        const float* alo[2] = {(const float*)p->op_lo[0], (const float*)p->op_lo[1]};
-        ce = tc_maps_create(&p->maps, p->tc, p->M, n, p->ncomp, p->ld, ahi, alo, 2, (const float*)p->P_hi,
-                            (const float*)p->P_lo);
+        const float* a[2][3];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 3; ++j) a[i][j] = (const float*)p->op[i][j];
+        const float* pp[3] = {(const float*)p->P[0], (const float*)p->P[1], (const float*)p->P[2]};
+        const int bn_slot[2] = {p->tc[0].bn, p->tc[1].bn};
+        ce = tc_maps_create(&p->maps, p->M, n, p->ncomp, p->ld, a, 2, pp, bn_slot);
         if (ce != cudaSuccess) {
             std::string why = tc_last_driver_error();
             free_plan(p);
@@ -530,12 +561,13 @@ etd_status etd_transform(etd_plan* p, const void* in_dev, void* out_dev) {
     if (s == ETD_OK) s = check_device_ptr(out_dev, "out_dev");
     if (s != ETD_OK) return s;
     int cur = 0;
+    const int sp = split_for(p, p->out_slot);
     if (p->elem == 8) {
-        if ((s = run_react<double>(p, -1, in_dev, p->n, p->npts, p->t)) != ETD_OK) return s;
-        s = run_chain<double>(p, cur, EPI_PLAIN, out_dev, p->n, p->npts);
+        if ((s = run_react<double>(p, -1, in_dev, p->n, p->npts, p->t, sp)) != ETD_OK) return s;
+        s = run_chain<double>(p, cur, p->out_slot, EPI_PLAIN, sp, out_dev, p->n, p->npts);
     } else {
-        if ((s = run_react<float>(p, -1, in_dev, p->n, p->npts, p->t)) != ETD_OK) return s;
-        s = run_chain<float>(p, cur, EPI_PLAIN, out_dev, p->n, p->npts);
+        if ((s = run_react<float>(p, -1, in_dev, p->n, p->npts, p->t, sp)) != ETD_OK) return s;
+        s = run_chain<float>(p, cur, p->out_slot, EPI_PLAIN, sp, out_dev, p->n, p->npts);
     }
     return s;
 }
@@ -582,7 +614,7 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
     info->n = p->n;
     info->n_comp = p->ncomp;
     info->precision = p->precision;
-    info->products = p->use_tc ? p->tc.products : 0;
+    info->products = p->use_tc ? p->tc[0].products : 0;
     info->gemms_per_step = 4 * p->d;
     info->unknowns = (long long)p->ncomp * p->npts;
     info->gemm_flops = 2.0 * (double)p->npts * (double)p->n * p->ncomp;

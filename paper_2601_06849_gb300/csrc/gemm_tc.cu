@@ -30,10 +30,8 @@
 namespace etd {
 
 struct TcMaps {
-    CUtensorMap a_hi[4];
-    CUtensorMap a_lo[4];
-    CUtensorMap p_hi;
-    CUtensorMap p_lo;
+    CUtensorMap a[4][3];  // operand buffer i, piece j (hi, mid, lo)
+    CUtensorMap p[2][3];  // P pieces, boxes as tall as the tile width of config slot 0 / 1
     int n_a;
 };
 
@@ -42,12 +40,16 @@ namespace {
 constexpr int BM = 128;
 constexpr int BKF = 32;                  // FP32 elements per k-block = one 128-byte row
 constexpr int A_BYTES = BM * BKF * 4;    // 16 KiB per operand plane
-constexpr int NUM_THREADS = 192;
+constexpr int NUM_EPI_WARPS = 8;         // two per TMEM lane quarter, one per column half
+constexpr int WARP_TMA = 8;
+constexpr int WARP_MMA = 9;
+constexpr int NUM_THREADS = 320;
+constexpr int MAX_HALF = 128;            // columns per epilogue warp (bn <= 256)
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
 constexpr int SMEM_LIMIT = 227 * 1024 - 1024;  // dynamic bytes; leaves room for the static barriers
 
 struct KParams {
-    int M, n, bn, stages, products, tiles_m, tiles_n, tmem_cols;
+    int M, n, bn, stages, products, pieces, tiles_m, tiles_n, tmem_cols;
     unsigned stage_bytes, b_bytes, tx_bytes;
     unsigned* err;
     Epi<float> e;
@@ -152,8 +154,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-    gemm_tf32_tc_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
-                        const __grid_constant__ CUtensorMap mP_hi, const __grid_constant__ CUtensorMap mP_lo,
+    gemm_tf32_tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                        const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mP0,
+                        const __grid_constant__ CUtensorMap mP1, const __grid_constant__ CUtensorMap mP2,
                         const KParams p) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ int s_skip;
@@ -161,7 +164,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     __shared__ int s_abort;
     __shared__ int s_consumed;
     __shared__ int s_issued;
-    __shared__ __align__(8) uint64_t s_bar[2 * 8 + 1];  // full[8], empty[8], accum
+    // full[8], empty[8] (shared-memory ring), acc_full[2], acc_empty[2] (TMEM ring), done
+    __shared__ __align__(8) uint64_t s_bar[8 + 8 + 2 + 2 + 1];
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) s_skip = (*(volatile unsigned*)p.err != 0u);
@@ -173,7 +177,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     volatile int* abort_flag = &s_abort;
     const uint32_t bar_full = smem_u32(&s_bar[0]);
     const uint32_t bar_empty = smem_u32(&s_bar[8]);
-    const uint32_t bar_accum = smem_u32(&s_bar[16]);
+    const uint32_t bar_acc_full = smem_u32(&s_bar[16]);
+    const uint32_t bar_acc_empty = smem_u32(&s_bar[18]);
+    const uint32_t bar_done = smem_u32(&s_bar[20]);
 
     int t = blockIdx.x;
     const int tn = t % p.tiles_n;
@@ -181,20 +187,25 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int tm = t % p.tiles_m;
     const int b = t / p.tiles_m;
     const int nk = (p.n + BKF - 1) / BKF;
+    const uint32_t acc_cols = (uint32_t)(p.tmem_cols / 2);  // one accumulator buffer
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(bar_full + 8 * s, 1);
             mbar_init(bar_empty + 8 * s, 1);
         }
-        mbar_init(bar_accum, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(bar_acc_full + 8 * a, 1);
+            mbar_init(bar_acc_empty + 8 * a, NUM_EPI_WARPS);
+        }
+        mbar_init(bar_done, 1);
         s_abort = 0;
         s_consumed = 0;
         s_issued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 4) {
+    if (warp == WARP_TMA) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                      "r"((uint32_t)p.tmem_cols)
                      : "memory");
@@ -205,7 +216,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = s_tmem;
 
-    if (warp == 4 && lane == 0) {
+    if (warp == WARP_TMA && lane == 0) {
         // ---------------- TMA producer ----------------
         const int arow = b * p.M + tm * BM;
         const int prow = tn * p.bn;
@@ -218,83 +229,117 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const uint32_t fb = bar_full + 8 * s;
             mbar_expect_tx(fb, p.tx_bytes);
             const int k0 = kb * BKF;
-            tma_load_2d(st, &mA_hi, fb, k0, arow);
-            tma_load_2d(st + 2 * A_BYTES, &mP_hi, fb, k0, prow);
-            if (p.products == 3) {
-                tma_load_2d(st + A_BYTES, &mA_lo, fb, k0, arow);
-                tma_load_2d(st + 2 * A_BYTES + p.b_bytes, &mP_lo, fb, k0, prow);
+            const uint32_t sb = st + (uint32_t)p.pieces * A_BYTES;  // first P piece
+            tma_load_2d(st, &mA0, fb, k0, arow);
+            tma_load_2d(sb, &mP0, fb, k0, prow);
+            if (p.pieces > 1) {
+                tma_load_2d(st + A_BYTES, &mA1, fb, k0, arow);
+                tma_load_2d(sb + p.b_bytes, &mP1, fb, k0, prow);
+            }
+            if (p.pieces > 2) {
+                tma_load_2d(st + 2 * A_BYTES, &mA2, fb, k0, arow);
+                tma_load_2d(sb + 2 * p.b_bytes, &mP2, fb, k0, prow);
             }
             issued = kb + 1;
         }
         s_issued = issued;
-    } else if (warp == 5 && lane == 0) {
-        // ---------------- MMA issuer ----------------
+    } else if (warp == WARP_MMA && lane == 0) {
+        // ---------------- MMA issuer: one k-block per accumulator buffer ----------------
         const uint32_t idesc = idesc_tf32(BM, p.bn);
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % S;
-            const uint32_t ph = (uint32_t)((kb / S) & 1);
-            if (!mbar_wait(bar_full + 8 * s, ph, abort_flag, p.err)) break;
+            const int a = kb & 1;
+            if (!mbar_wait(bar_full + 8 * s, (uint32_t)((kb / S) & 1), abort_flag, p.err)) break;
+            if (kb >= 2 && !mbar_wait(bar_acc_empty + 8 * a, (uint32_t)(((kb >> 1) - 1) & 1), abort_flag, p.err))
+                break;
             tc_fence_after();
-            const uint32_t a_hi = smem_u32(smem + (size_t)s * p.stage_bytes);
-            const uint32_t a_lo = a_hi + A_BYTES;
-            const uint32_t b_hi = a_hi + 2 * A_BYTES;
-            const uint32_t b_lo = b_hi + p.b_bytes;
+            const uint32_t d = tmem + (uint32_t)a * acc_cols;
+            const uint32_t a0 = smem_u32(smem + (size_t)s * p.stage_bytes);
+            const uint32_t a1 = a0 + A_BYTES, a2 = a0 + 2 * A_BYTES;
+            const uint32_t b0 = a0 + (uint32_t)p.pieces * A_BYTES;
+            const uint32_t b1 = b0 + p.b_bytes, b2 = b0 + 2 * p.b_bytes;
 #pragma unroll
             for (int kk = 0; kk < BKF / 8; ++kk) {
                 const uint32_t off = kk * 32;  // 8 TF32 values = 32 bytes per MMA
-                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-                if (p.products == 3) {
-                    mma_tf32(tmem, sdesc_sw128(a_lo + off), sdesc_sw128(b_hi + off), idesc, acc);
-                    mma_tf32(tmem, sdesc_sw128(a_hi + off), sdesc_sw128(b_lo + off), idesc, 1u);
-                    mma_tf32(tmem, sdesc_sw128(a_hi + off), sdesc_sw128(b_hi + off), idesc, 1u);
-                } else {
-                    mma_tf32(tmem, sdesc_sw128(a_hi + off), sdesc_sw128(b_hi + off), idesc, acc);
+                // terms of (a0 + a1 + a2)(b0 + b1 + b2) down to the 2^-22 level
+                mma_tf32(d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
+                if (p.products >= 3) {
+                    mma_tf32(d, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, 1u);
+                    mma_tf32(d, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                }
+                if (p.products == 6) {
+                    mma_tf32(d, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                    mma_tf32(d, sdesc_sw128(a2 + off), sdesc_sw128(b0 + off), idesc, 1u);
+                    mma_tf32(d, sdesc_sw128(a0 + off), sdesc_sw128(b2 + off), idesc, 1u);
                 }
             }
-            mma_commit(bar_empty + 8 * s);
+            mma_commit(bar_empty + 8 * s);     // stage s may be refilled once these products finish
+            mma_commit(bar_acc_full + 8 * a);  // the k-block sum is ready for the epilogue
             s_consumed = kb + 1;
         }
-        mma_commit(bar_accum);  // arrives when every product issued above has completed
-    } else if (warp < 4) {
-        // ---------------- epilogue ----------------
-        const bool ok = mbar_wait(bar_accum, 0u, abort_flag, p.err);
-        tc_fence_after();
-        if (ok && !*abort_flag) {
-            const int mm = tm * BM + warp * 32 + lane;
-            const bool row_ok = mm < p.M;
-            const int mh = mm / p.n, ml = mm - mh * p.n;
-            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-            for (int c0 = 0; c0 < p.bn; c0 += 16) {
-                float v[16];
-                tmem_ld16(lane_base + (uint32_t)c0, v);
-                if (row_ok) {
-                    const int nn0 = tn * p.bn + c0;
+        mma_commit(bar_done);  // arrives when every product issued above has completed
+    } else if (warp < NUM_EPI_WARPS) {
+        // ---------------- epilogue: FP32 round-to-nearest sum of the k-block sums ----------------
+        const int quarter = warp & 3;         // TMEM lanes 32*quarter .. +31
+        const int half = warp >> 2;           // which half of the tile's columns
+        const int hcols = p.bn / 2;           // multiple of 16
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * hcols);
+        float sum[MAX_HALF];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (nn0 + j < p.n) p.e.apply(b, mh, ml, nn0 + j, v[j]);
+        for (int i = 0; i < MAX_HALF; ++i) sum[i] = 0.f;
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int a = kb & 1;
+            if (!mbar_wait(bar_acc_full + 8 * a, (uint32_t)((kb >> 1) & 1), abort_flag, p.err)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t src = lane_base + (uint32_t)a * acc_cols;
+#pragma unroll
+            for (int c = 0; c < MAX_HALF / 16; ++c) {
+                if (c * 16 < hcols) {
+                    float v[16];
+                    tmem_ld16(src + (uint32_t)(c * 16), v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) sum[c * 16 + j] += v[j];
                 }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_acc_empty + 8 * a) : "memory");
+        }
+        if (ok && !*abort_flag) {
+            const int mm = tm * BM + quarter * 32 + lane;
+            if (mm < p.M) {
+                const int mh = mm / p.n, ml = mm - mh * p.n;
+                const int nn0 = tn * p.bn + half * hcols;
+#pragma unroll
+                for (int c = 0; c < MAX_HALF; ++c)
+                    if (c < hcols && nn0 + c < p.n) p.e.apply(b, mh, ml, nn0 + c, sum[c]);
             }
         }
     }
 
     tc_fence_before();
     __syncthreads();
-    if (warp == 4 && lane == 0 && *abort_flag) {
-        // copies still in flight after an abort: wait for them (bounded) before exit
-        for (int kb = s_consumed; kb < s_issued; ++kb) {
-            const int s = kb % S;
-            const uint32_t fb = bar_full + 8 * s;
-            const unsigned long long t0 = globaltimer();
-            while (!mbar_try(fb, (uint32_t)((kb / S) & 1)) && globaltimer() - t0 < 100000000ull) {
+    if (warp == WARP_TMA && lane == 0) {
+        if (*abort_flag) {
+            // copies still in flight after an abort: wait for them (bounded) before exit
+            for (int kb = s_consumed; kb < s_issued; ++kb) {
+                const int s = kb % S;
+                const unsigned long long t0 = globaltimer();
+                while (!mbar_try(bar_full + 8 * s, (uint32_t)((kb / S) & 1)) && globaltimer() - t0 < 100000000ull) {
+                }
             }
         }
-        const unsigned long long t0 = globaltimer();
-        while (!mbar_try(bar_accum, 0u) && globaltimer() - t0 < 100000000ull) {
+        const unsigned long long t0 = globaltimer();  // every product has completed
+        while (!mbar_try(bar_done, 0u) && globaltimer() - t0 < 200000000ull) {
         }
     }
     __syncthreads();
     tc_fence_after();
-    if (warp == 4) {
+    if (warp == WARP_TMA) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)p.tmem_cols)
                      : "memory");
     }
@@ -347,12 +392,16 @@ const char* tc_last_driver_error() { return g_driver_error; }
 TcConfig tc_choose(int M, int n, int products) {
     TcConfig c{};
     c.products = products;
-    // tile width: the multiple of 16 in [64, 256] that wastes the fewest columns
-    int best = 256, best_waste = 1 << 30;
-    if (n <= 256) {
-        best = ((n + 15) / 16) * 16;
+    c.pieces = products == 6 ? 3 : (products == 3 ? 2 : 1);
+    // tile width: the multiple of 32 up to bn_max that wastes the fewest columns
+    // (each of the two column halves is a whole number of 16-column TMEM loads);
+    // three operand pieces leave room for two 128-wide stages only
+    const int bn_max = (c.pieces == 3) ? 128 : 256;
+    int best = bn_max, best_waste = 1 << 30;
+    if (n <= bn_max) {
+        best = ((n + 31) / 32) * 32;
     } else {
-        for (int bn = 256; bn >= 128; bn -= 16) {
+        for (int bn = bn_max; bn >= 128; bn -= 32) {
             const int waste = ((n + bn - 1) / bn) * bn - n;
             if (waste < best_waste) {
                 best_waste = waste;
@@ -363,13 +412,11 @@ TcConfig tc_choose(int M, int n, int products) {
     c.bn = best;
     c.tiles_n = (n + c.bn - 1) / c.bn;
     c.tiles_m = (M + BM - 1) / BM;
-    c.tmem_cols = 32;
-    while (c.tmem_cols < c.bn) c.tmem_cols *= 2;
+    int acc = 32;
+    while (acc < c.bn) acc *= 2;
+    c.tmem_cols = 2 * acc;  // two accumulator buffers
     const unsigned b_bytes = (unsigned)c.bn * BKF * 4;
-    c.stage_bytes = (products == 3) ? 2u * A_BYTES + 2u * b_bytes : (unsigned)A_BYTES + b_bytes;
-    // A hi | A lo | P hi | P lo inside a stage; keep the A-lo slot even when unused
-    // so that every offset stays 1024-byte aligned.
-    if (products != 3) c.stage_bytes = 2u * A_BYTES + b_bytes;
+    c.stage_bytes = (unsigned)c.pieces * ((unsigned)A_BYTES + b_bytes);
     int s = (SMEM_LIMIT - 1024) / (int)c.stage_bytes;
     if (s > 8) s = 8;
     c.stages = s;
@@ -377,20 +424,23 @@ TcConfig tc_choose(int M, int n, int products) {
     return c;
 }
 
-cudaError_t tc_maps_create(TcMaps** out, const TcConfig& cfg, int M, int n, int nbatch, int ld,
-                           const float* const* a_hi, const float* const* a_lo, int n_a, const float* p_hi,
-                           const float* p_lo) {
+cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const float* const a[][3], int n_a,
+                           const float* const pp[3], const int bn_slot[2]) {
     *out = nullptr;
-    if (n_a > 4 || cfg.stages < 2) return cudaErrorInvalidValue;
+    if (n_a > 4) return cudaErrorInvalidValue;
     TcMaps* m = new TcMaps();
     m->n_a = n_a;
     bool ok = true;
-    for (int i = 0; i < n_a && ok; ++i) {
-        ok = make_map(&m->a_hi[i], a_hi[i], n, (long long)nbatch * M, ld, BM);
-        if (ok) ok = make_map(&m->a_lo[i], a_lo[i] ? a_lo[i] : a_hi[i], n, (long long)nbatch * M, ld, BM);
-    }
-    if (ok) ok = make_map(&m->p_hi, p_hi, n, n, ld, cfg.bn);
-    if (ok) ok = make_map(&m->p_lo, p_lo ? p_lo : p_hi, n, n, ld, cfg.bn);
+    for (int i = 0; i < n_a && ok; ++i)
+        for (int j = 0; j < 3 && ok; ++j) {
+            const float* base = a[i][j] ? a[i][j] : a[i][0];
+            ok = make_map(&m->a[i][j], base, n, (long long)nbatch * M, ld, BM);
+        }
+    for (int slot = 0; slot < 2 && ok; ++slot)
+        for (int j = 0; j < 3 && ok; ++j) {
+            const float* base = pp[j] ? pp[j] : pp[0];
+            ok = make_map(&m->p[slot][j], base, n, n, ld, bn_slot[slot] > 0 ? bn_slot[slot] : 32);
+        }
     if (!ok) {
         delete m;
         return cudaErrorInvalidValue;
@@ -411,26 +461,28 @@ cudaError_t tc_maps_create(TcMaps** out, const TcConfig& cfg, int M, int n, int 
 
 void tc_maps_destroy(TcMaps* m) { delete m; }
 
-cudaError_t launch_gemm_tc(const TcConfig& cfg, const TcMaps* maps, int a_index, int M, int n, int nbatch,
+cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, int a_index, int M, int n, int nbatch,
                            const Epi<float>& e, unsigned* err, cudaStream_t st) {
-    if (a_index < 0 || a_index >= maps->n_a) return cudaErrorInvalidValue;
+    if (a_index < 0 || a_index >= maps->n_a || slot < 0 || slot > 1) return cudaErrorInvalidValue;
     KParams p;
     p.M = M;
     p.n = n;
     p.bn = cfg.bn;
     p.stages = cfg.stages;
     p.products = cfg.products;
+    p.pieces = cfg.pieces;
     p.tiles_m = cfg.tiles_m;
     p.tiles_n = cfg.tiles_n;
     p.tmem_cols = cfg.tmem_cols;
     p.stage_bytes = cfg.stage_bytes;
     p.b_bytes = (unsigned)cfg.bn * BKF * 4;
-    p.tx_bytes = (cfg.products == 3) ? 2u * (A_BYTES + p.b_bytes) : (unsigned)A_BYTES + p.b_bytes;
+    p.tx_bytes = cfg.stage_bytes;
     p.err = err;
     p.e = e;
     const long long grid = (long long)nbatch * cfg.tiles_m * cfg.tiles_n;
-    gemm_tf32_tc_kernel<<<(unsigned)grid, NUM_THREADS, cfg.smem_bytes, st>>>(
-        maps->a_hi[a_index], maps->a_lo[a_index], maps->p_hi, maps->p_lo, p);
+    const CUtensorMap* A = maps->a[a_index];
+    const CUtensorMap* P = maps->p[slot];
+    gemm_tf32_tc_kernel<<<(unsigned)grid, NUM_THREADS, cfg.smem_bytes, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
     return cudaGetLastError();
 }
 

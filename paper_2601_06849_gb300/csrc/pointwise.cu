@@ -11,8 +11,16 @@
 namespace etd {
 
 template <typename T>
-__device__ __forceinline__ void store_split(T* hi, T* lo, long long o, T v, int split) {
+__device__ __forceinline__ void store_split(T* hi, T* lo, T* lo2, long long o, T v, int split) {
     if constexpr (sizeof(T) == 4) {
+        if (split == SPLIT_TF32_3) {  // three TF32 pieces hold all 24 bits of v
+            const float h = tf32_rna(v);
+            const float m = tf32_rna(v - h);
+            hi[o] = h;
+            lo[o] = m;
+            lo2[o] = tf32_rna(v - h - m);
+            return;
+        }
         if (split == SPLIT_TF32) {
             float h = tf32_rna(v);
             hi[o] = h;
@@ -39,14 +47,14 @@ __global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
             case ETD_RX_FHN: {
                 // f_u = u - c3 u^3 - v,  f_v = eps (u - a v - b)
                 const T u = r.in[oi], v = r.in[r.bs_in + oi];
-                store_split(r.out_hi, r.out_lo, oo, u - r.rp[0] * u * u * u - v, r.split);
-                store_split(r.out_hi + r.bs_out, r.out_lo + r.bs_out, oo, r.rp[1] * (u - r.rp[2] * v - r.rp[3]),
-                            r.split);
+                store_split(r.out_hi, r.out_lo, r.out_lo2, oo, u - r.rp[0] * u * u * u - v, r.split);
+                store_split(r.out_hi + r.bs_out, r.out_lo + r.bs_out, r.out_lo2 + r.bs_out, oo,
+                            r.rp[1] * (u - r.rp[2] * v - r.rp[3]), r.split);
                 break;
             }
             case ETD_RX_ALLEN_CAHN: {
                 const T u = r.in[oi];
-                store_split(r.out_hi, r.out_lo, oo, u - u * u * u, r.split);
+                store_split(r.out_hi, r.out_lo, r.out_lo2, oo, u - u * u * u, r.split);
                 break;
             }
             default:
@@ -55,7 +63,8 @@ __global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
                     T f = (T)0;
                     if (r.kind == ETD_RX_LINEAR) f = r.rp[0] * u;
                     else if (r.kind < 0) f = u;  // identity: split the field itself
-                    store_split(r.out_hi + c * r.bs_out, r.out_lo + c * r.bs_out, oo, f, r.split);
+                    store_split(r.out_hi + c * r.bs_out, r.out_lo + c * r.bs_out, r.out_lo2 + c * r.bs_out, oo, f,
+                                r.split);
                 }
                 break;
         }

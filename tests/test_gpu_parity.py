@@ -1,11 +1,13 @@
 """Full ETD2RK-DS steps through the C ABI against the FP64 CPU oracle.
 
 Error metric (relative, whole field): max |U_gpu - U_oracle| / max |U_oracle|,
-per component. Bounds per precision (derived in the design notes):
-  fp64    1e-10  (the benchmark spec's FP64 bar)
-  tf32x3  1e-6   (the benchmark spec's split-precision bar)
-  fp32    1e-6   (FP32 CUDA-core products, same storage as tf32x3)
-  tf32    3e-3   (one TF32 product, 11-bit operands: error stated, not a bar)
+per component. Every precision carries the spectral state in FP64, so the
+error of the returned field is set by the transform that produces it:
+  fp64    1e-10                 the FP64 bar
+  tf32x3  1e-6                  the split-precision bar (output transform: 3-piece split)
+  tf32x6  1e-6                  same, three-piece split in every pass
+  fp32    4 sqrt(n) 2^-24       FP32 round-to-nearest sums of n terms in each output pass
+  tf32    3e-3                  one TF32 product: 11-bit operands (2^-11 = 4.9e-4 per pass)
 Sizes span several 128-row tiles, ragged tails and padded rows (n % 4 != 0).
 """
 import numpy as np
@@ -16,7 +18,13 @@ from oracle import oracle as O
 from oracle import spectral as S
 from paper_2601_06849_gb300 import etd, inputs
 
-TOL = {"fp64": 1e-10, "tf32x3": 1e-6, "fp32": 1e-6, "tf32": 3e-3}
+TOL = {"fp64": 1e-10, "tf32x3": 1e-6, "tf32x6": 1e-6, "tf32": 3e-3}
+
+
+def tol(precision, n):
+    if precision == "fp32":
+        return 4 * np.sqrt(n) * 2.0 ** -24
+    return TOL[precision]
 FHN = (1.0, 0.01, 0.5, 0.1)  # c3, eps, a, b of the 2D FitzHugh-Nagumo workload
 
 
@@ -38,18 +46,19 @@ def oracle_ref(d, n, kappa, q, tau, u0, steps, reaction, rp=(), pade=2):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "fp32", "tf32"])
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "tf32x6", "fp32", "tf32"])
 def test_allen_cahn_2d_n64_100_steps(precision):
     """2D Allen-Cahn, n = 64, kappa = 0.01, q = 0, tau = 1e-3, 100 steps."""
     torch = need_gpu()
+    n = 64
     u0 = inputs.allen_cahn_2d(64, workload=0)
     ref = oracle_ref(2, 64, (0.01,), 0.0, 1e-3, u0, 100, "allen_cahn")
     got = run_gpu(torch, 2, 64, 0.01, 0.0, 1e-3, u0, 100, precision, "allen_cahn")
-    assert rel_err(got, ref) < TOL[precision]
+    assert rel_err(got, ref) < tol(precision, n)
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "fp32", "tf32"])
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "tf32x6", "fp32", "tf32"])
 @pytest.mark.parametrize("n", [300, 129])
 def test_fhn_2d_ragged(precision, n):
     """2D FitzHugh-Nagumo with the workload's parameters on grids with ragged tiles."""
@@ -58,7 +67,7 @@ def test_fhn_2d_ragged(precision, n):
     ref = oracle_ref(2, n, (1e-3, 5e-3), 0.0, 1e-2, u0, 20, "fhn", FHN)
     got = run_gpu(torch, 2, n, 1e-3, 0.0, 1e-2, u0, 20, precision, "fhn", FHN, kappa_comp=(1e-3, 5e-3))
     for c in range(2):
-        assert rel_err(got[c], ref[c]) < TOL[precision]
+        assert rel_err(got[c], ref[c]) < tol(precision, n)
 
 
 @pytest.mark.gpu
@@ -70,11 +79,11 @@ def test_allen_cahn_3d(precision, n):
     u0 = inputs.gaussian_bump(n, 3)
     ref = oracle_ref(3, n, (1e-3,), 0.1, 5e-3, u0, 10, "allen_cahn")
     got = run_gpu(torch, 3, n, 1e-3, 0.1, 5e-3, u0, 10, precision, "allen_cahn")
-    assert rel_err(got, ref) < TOL[precision]
+    assert rel_err(got, ref) < tol(precision, n)
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "tf32x6"])
 def test_fhn_3d_two_components(precision):
     torch = need_gpu()
     n = 40
@@ -82,7 +91,7 @@ def test_fhn_3d_two_components(precision):
     ref = oracle_ref(3, n, (1e-3, 5e-3), 0.05, 1e-2, u0, 8, "fhn", FHN)
     got = run_gpu(torch, 3, n, 1e-3, 0.05, 1e-2, u0, 8, precision, "fhn", FHN, kappa_comp=(1e-3, 5e-3))
     for c in range(2):
-        assert rel_err(got[c], ref[c]) < TOL[precision]
+        assert rel_err(got[c], ref[c]) < tol(precision, n)
 
 
 @pytest.mark.gpu
@@ -93,7 +102,7 @@ def test_pade04(precision, d, n):
     u0 = inputs.allen_cahn_2d(n, workload=5) if d == 2 else inputs.gaussian_bump(n, 3)
     ref = oracle_ref(d, n, (0.01,), 0.2, 2e-3, u0, 15, "allen_cahn", pade=4)
     got = run_gpu(torch, d, n, 0.01, 0.2, 2e-3, u0, 15, precision, "allen_cahn", pade=4)
-    assert rel_err(got, ref) < TOL[precision]
+    assert rel_err(got, ref) < tol(precision, n)
 
 
 @pytest.mark.gpu
@@ -106,7 +115,7 @@ def test_exact_exponential_2d(precision):
     P = O.Problem(d=2, n=n, kappa=(1e-3,), q=0.1, tau=tau, reaction="allen_cahn")
     ref = S.run(P, u0, steps, react=lambda t, u: u - u ** 3, kind="exact")
     got = run_gpu(torch, 2, n, 1e-3, 0.1, tau, u0, steps, precision, "allen_cahn", pade="exact")
-    assert rel_err(got, ref) < TOL[precision]
+    assert rel_err(got, ref) < tol(precision, n)
 
 
 @pytest.mark.gpu
@@ -114,10 +123,11 @@ def test_exact_exponential_2d(precision):
 @pytest.mark.parametrize("d", [2, 3])
 def test_smallest_grid(precision, d):
     torch = need_gpu()
+    n = 2
     u0 = inputs.random_field((2,) + (2,) * d, workload=7, scale=0.2)
     ref = oracle_ref(d, 2, (0.3, 0.1), 0.0, 1e-2, u0, 5, "fhn", FHN)
     got = run_gpu(torch, d, 2, 0.3, 0.0, 1e-2, u0, 5, precision, "fhn", FHN, kappa_comp=(0.3, 0.1))
-    assert rel_err(got, ref) < TOL[precision]
+    assert rel_err(got, ref) < tol(precision, n)
 
 
 @pytest.mark.gpu
@@ -127,7 +137,7 @@ def test_linear_reaction_two_components():
     u0 = inputs.random_field((2, n, n), workload=8)
     ref = oracle_ref(2, n, (0.02, 0.02), 0.3, 1e-2, u0, 10, "linear", (0.7,))
     got = run_gpu(torch, 2, n, 0.02, 0.3, 1e-2, u0, 10, "tf32x3", "linear", (0.7,))
-    assert rel_err(got, ref) < TOL["tf32x3"]
+    assert rel_err(got, ref) < tol("tf32x3", n)
 
 
 @pytest.mark.gpu
@@ -165,7 +175,7 @@ def test_host_entry_point_and_stats():
                     kappa_comp=(1e-3, 5e-3))
     host = torch.tensor(u0, dtype=torch.float32).pin_memory()
     plan.step_host(host, 6)
-    assert rel_err(host.double().numpy(), ref) < TOL["tf32x3"]
+    assert rel_err(host.double().numpy(), ref) < tol("tf32x3", n)
     dev = host.cuda()
     m, bad = plan.stats(dev)
     assert bad == 0 and m == pytest.approx(float(np.abs(host.numpy()).max()), rel=1e-7)
