@@ -160,6 +160,7 @@ struct TcConfig {
     int stages;      // shared-memory pipeline depth
     int products;    // 1 (TF32), 3 (two-piece split) or 6 (three-piece split)
     int pieces;      // operand pieces read per product mode
+    bool accurate;   // separate correction accumulator + compensated k-block sums
     int tiles_m, tiles_n;
     int tmem_cols;
     int smem_bytes;

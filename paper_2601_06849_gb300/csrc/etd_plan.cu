@@ -296,10 +296,11 @@ etd_status run_react(etd_plan* p, int kind, const void* in, int ld_in, long long
     return ETD_OK;
 }
 
-// n_steps time steps. Every transform runs with config slot 0, except the one
-// that produces the field handed back to the caller (last step), which runs
-// with p->out_slot: that field is the only result that is not damped by tau
-// before it matters, so only it gets the six-product split in TF32X3 mode.
+// n_steps time steps. Every transform runs with config slot 0 except two, which
+// run with p->out_slot (the accurate six-product kernel in TF32X3 mode): the
+// U -> U^ transform that (re)builds the carried state, and the transform that
+// produces the field handed back to the caller. Errors of the other transforms
+// reach the state only through f(U) and f(W), scaled by tau.
 template <typename T>
 etd_status step_impl(etd_plan* p, void* u, int n_steps) {
     const int n = p->n;
@@ -308,9 +309,10 @@ etd_status step_impl(etd_plan* p, void* u, int n_steps) {
     etd_status s;
     int cur = 0;
     if (!p->uhat_valid || p->uhat_src != u) {
-        if ((s = run_react<T>(p, -1, u, n, N, p->t, sp0)) != ETD_OK) return s;
+        // U -> U^ with the output slot: an error made here stays in the carried state
+        if ((s = run_react<T>(p, -1, u, n, N, p->t, spo)) != ETD_OK) return s;
         cur = 0;
-        if ((s = run_chain<T>(p, cur, 0, EPI_CARRY, sp0, nullptr, 0, 0)) != ETD_OK) return s;
+        if ((s = run_chain<T>(p, cur, p->out_slot, EPI_CARRY, spo, nullptr, 0, 0)) != ETD_OK) return s;
         p->uhat_valid = true;
         p->uhat_src = u;
     }

@@ -50,6 +50,7 @@ constexpr int SMEM_LIMIT = 227 * 1024 - 1024;  // dynamic bytes; leaves room for
 
 struct KParams {
     int M, n, bn, stages, products, pieces, tiles_m, tiles_n, tmem_cols;
+    int acc_cols;  // columns of one accumulator region (power of two >= bn)
     unsigned stage_bytes, b_bytes, tx_bytes;
     unsigned* err;
     Epi<float> e;
@@ -153,6 +154,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// ACCURATE = false: every product of a k-step into the k-block accumulator,
+//   FP32 round-to-nearest running sums (the per-step passes).
+// ACCURATE = true (bn <= 128, three operand pieces): only hi*hi goes to the
+//   k-block accumulator; the five correction products accumulate over the whole
+//   K range in a third TMEM region, and the k-block sums are added with
+//   compensated (2Sum) FP32 arithmetic. Used for the transforms whose error
+//   stays in the result: U -> U^ when the carried state is (re)built and the
+//   transform that returns the field.
+template <bool ACCURATE>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     gemm_tf32_tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                         const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mP0,
@@ -187,7 +197,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int tm = t % p.tiles_m;
     const int b = t / p.tiles_m;
     const int nk = (p.n + BKF - 1) / BKF;
-    const uint32_t acc_cols = (uint32_t)(p.tmem_cols / 2);  // one accumulator buffer
+    // TMEM columns: [0, acc) and [acc, 2 acc) k-block buffers, [2 acc, 3 acc) corrections (ACCURATE)
+    const uint32_t acc_cols = (uint32_t)p.acc_cols;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -254,6 +265,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 break;
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)a * acc_cols;
+            const uint32_t dc = ACCURATE ? tmem + 2u * acc_cols : d;  // correction products
             const uint32_t a0 = smem_u32(smem + (size_t)s * p.stage_bytes);
             const uint32_t a1 = a0 + A_BYTES, a2 = a0 + 2 * A_BYTES;
             const uint32_t b0 = a0 + (uint32_t)p.pieces * A_BYTES;
@@ -263,14 +275,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const uint32_t off = kk * 32;  // 8 TF32 values = 32 bytes per MMA
                 // terms of (a0 + a1 + a2)(b0 + b1 + b2) down to the 2^-22 level
                 mma_tf32(d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
+                const uint32_t cacc = ACCURATE ? ((kb > 0 || kk > 0) ? 1u : 0u) : 1u;
                 if (p.products >= 3) {
-                    mma_tf32(d, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, 1u);
-                    mma_tf32(d, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                    mma_tf32(dc, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, cacc);
+                    mma_tf32(dc, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
                 }
                 if (p.products == 6) {
-                    mma_tf32(d, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), idesc, 1u);
-                    mma_tf32(d, sdesc_sw128(a2 + off), sdesc_sw128(b0 + off), idesc, 1u);
-                    mma_tf32(d, sdesc_sw128(a0 + off), sdesc_sw128(b2 + off), idesc, 1u);
+                    mma_tf32(dc, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                    mma_tf32(dc, sdesc_sw128(a2 + off), sdesc_sw128(b0 + off), idesc, 1u);
+                    mma_tf32(dc, sdesc_sw128(a0 + off), sdesc_sw128(b2 + off), idesc, 1u);
                 }
             }
             mma_commit(bar_empty + 8 * s);     // stage s may be refilled once these products finish
@@ -284,9 +297,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int half = warp >> 2;           // which half of the tile's columns
         const int hcols = p.bn / 2;           // multiple of 16
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * hcols);
-        float sum[MAX_HALF];
+        constexpr int HALF = ACCURATE ? MAX_HALF / 2 : MAX_HALF;
+        float sum[HALF];
+        float comp[ACCURATE ? HALF : 1];  // 2Sum error terms (ACCURATE)
 #pragma unroll
-        for (int i = 0; i < MAX_HALF; ++i) sum[i] = 0.f;
+        for (int i = 0; i < HALF; ++i) sum[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < (ACCURATE ? HALF : 1); ++i) comp[i] = 0.f;
         bool ok = true;
         for (int kb = 0; kb < nk; ++kb) {
             const int a = kb & 1;
@@ -297,17 +314,45 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             tc_fence_after();
             const uint32_t src = lane_base + (uint32_t)a * acc_cols;
 #pragma unroll
-            for (int c = 0; c < MAX_HALF / 16; ++c) {
+            for (int c = 0; c < HALF / 16; ++c) {
                 if (c * 16 < hcols) {
                     float v[16];
                     tmem_ld16(src + (uint32_t)(c * 16), v);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) sum[c * 16 + j] += v[j];
+                    for (int j = 0; j < 16; ++j) {
+                        const int i = c * 16 + j;
+                        if constexpr (ACCURATE) {
+                            const float t = sum[i] + v[j];  // Knuth's 2Sum: t + e == sum + v exactly
+                            const float z = t - sum[i];
+                            comp[i] += (sum[i] - (t - z)) + (v[j] - z);
+                            sum[i] = t;
+                        } else {
+                            sum[i] += v[j];
+                        }
+                    }
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_acc_empty + 8 * a) : "memory");
+        }
+        if constexpr (ACCURATE) {
+            // the correction accumulator is complete once every product has finished
+            if (ok && !mbar_wait(bar_done, 0u, abort_flag, p.err)) ok = false;
+            tc_fence_after();
+            if (ok) {
+#pragma unroll
+                for (int c = 0; c < HALF / 16; ++c) {
+                    if (c * 16 < hcols) {
+                        float v[16];
+                        tmem_ld16(lane_base + 2u * acc_cols + (uint32_t)(c * 16), v);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) comp[c * 16 + j] += v[j];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < HALF; ++i) sum[i] += comp[i];
+            }
         }
         if (ok && !*abort_flag) {
             const int mm = tm * BM + quarter * 32 + lane;
@@ -315,7 +360,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const int mh = mm / p.n, ml = mm - mh * p.n;
                 const int nn0 = tn * p.bn + half * hcols;
 #pragma unroll
-                for (int c = 0; c < MAX_HALF; ++c)
+                for (int c = 0; c < HALF; ++c)
                     if (c < hcols && nn0 + c < p.n) p.e.apply(b, mh, ml, nn0 + c, sum[c]);
             }
         }
@@ -414,7 +459,10 @@ TcConfig tc_choose(int M, int n, int products) {
     c.tiles_m = (M + BM - 1) / BM;
     int acc = 32;
     while (acc < c.bn) acc *= 2;
-    c.tmem_cols = 2 * acc;  // two accumulator buffers
+    c.accurate = (c.pieces == 3);
+    // two k-block accumulator buffers (+ the correction accumulator, rounded up
+    // to the power of two that tcgen05.alloc needs)
+    c.tmem_cols = c.accurate ? 4 * acc : 2 * acc;
     const unsigned b_bytes = (unsigned)c.bn * BKF * 4;
     c.stage_bytes = (unsigned)c.pieces * ((unsigned)A_BYTES + b_bytes);
     int s = (SMEM_LIMIT - 1024) / (int)c.stage_bytes;
@@ -447,8 +495,11 @@ cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const
     }
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_tf32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(gemm_tf32_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              SMEM_LIMIT);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(gemm_tf32_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     SMEM_LIMIT);
         if (e != cudaSuccess) {
             delete m;
             return e;
@@ -474,6 +525,7 @@ cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, in
     p.tiles_m = cfg.tiles_m;
     p.tiles_n = cfg.tiles_n;
     p.tmem_cols = cfg.tmem_cols;
+    p.acc_cols = cfg.tmem_cols / (cfg.accurate ? 4 : 2);
     p.stage_bytes = cfg.stage_bytes;
     p.b_bytes = (unsigned)cfg.bn * BKF * 4;
     p.tx_bytes = cfg.stage_bytes;
@@ -482,7 +534,12 @@ cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, in
     const long long grid = (long long)nbatch * cfg.tiles_m * cfg.tiles_n;
     const CUtensorMap* A = maps->a[a_index];
     const CUtensorMap* P = maps->p[slot];
-    gemm_tf32_tc_kernel<<<(unsigned)grid, NUM_THREADS, cfg.smem_bytes, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
+    if (cfg.accurate)
+        gemm_tf32_tc_kernel<true>
+            <<<(unsigned)grid, NUM_THREADS, cfg.smem_bytes, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
+    else
+        gemm_tf32_tc_kernel<false>
+            <<<(unsigned)grid, NUM_THREADS, cfg.smem_bytes, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
     return cudaGetLastError();
 }
 
