@@ -265,8 +265,8 @@ def main():
         plan.step(u, args.warmup)
         plan.sync()
         plan.set_timing(True)
-        plan.kernel_times(0)
-        plan.kernel_times(1)
+        for kind in (0, 1, 2):
+            plan.kernel_times(kind)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier(world)
         torch.cuda.synchronize()
@@ -280,6 +280,7 @@ def main():
         plan.sync()
         gemm_ms, gemm_n = plan.kernel_times(0)
         rx_ms, rx_n = plan.kernel_times(1)
+        acc_ms, acc_n = plan.kernel_times(2)
         plan.set_timing(False)
     el_max = barrier_max(el_ms, world)
     m, bad = plan.stats(u)
@@ -339,7 +340,7 @@ def main():
         "roofline": roof,
         "gpu_launches": launches_per_step * args.steps,
         "kernel_ms": {"transform_passes": gemm_ms, "transform_launches": gemm_n, "reaction_ms": rx_ms,
-                      "reaction_launches": rx_n},
+                      "reaction_launches": rx_n, "accurate_transform_ms": acc_ms, "accurate_transform_launches": acc_n},
         "e2e": {"value": world * unknowns * e2e_steps / e2e_s, "unit": "unknown-updates/s",
                 "h2d_bytes_per_step": bytes_field, "d2h_bytes_per_step": bytes_field,
                 "steps": e2e_steps, "api": "etd_step_host (pinned host field, 1 step per call)"},

@@ -160,8 +160,10 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info);
 /*
  * Kernel timing: when enabled, every launch of the plan is bracketed by CUDA
  * events on the plan stream. etd_kernel_times (after etd_sync) returns, for
- * kind 0 = transform GEMM passes, 1 = pointwise reaction/split kernels, the
- * summed milliseconds and launch count since the last reset.
+ * kind 0 = transform passes of the time steps, 1 = pointwise reaction/split
+ * kernels, 2 = the accurate transform passes (state rebuild and returned field,
+ * ETD_PREC_TF32X3 only), the summed milliseconds and launch count since the
+ * last call for that kind.
  */
 etd_status etd_set_timing(etd_plan* p, int enable);
 etd_status etd_kernel_times(etd_plan* p, int kind, double* total_ms, long long* launches);

@@ -233,7 +233,7 @@ etd_status run_pass(etd_plan* p, int cur, int slot, int mode, int out_split, voi
     e.dst = (T*)dst;
     e.ld_dst = ld_dst;
     e.bs_dst = bs_dst;
-    TimerScope ts(p, 0);
+    TimerScope ts(p, slot == p->out_slot && p->out_slot != 0 ? 2 : 0);
     if constexpr (sizeof(T) == 8) {
         launch_gemm_simt_f64((const double*)p->op[cur][0], (const double*)p->P[0], p->M, p->n, p->ncomp, e,
                              p->stream);

@@ -141,17 +141,26 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
+// tcgen05.ld of 16 consecutive accumulator columns of this warp's 32 lanes;
+// asynchronous until tmem_wait16 on the same registers.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// tcgen05.wait::ld, with the loaded registers as operands so that no use of
+// them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
 }
 
 // ACCURATE = false: every product of a k-step into the k-block accumulator,
@@ -316,18 +325,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
             for (int c = 0; c < HALF / 16; ++c) {
                 if (c * 16 < hcols) {
-                    float v[16];
-                    tmem_ld16(src + (uint32_t)(c * 16), v);
+                    uint32_t r[16];
+                    tmem_ld16(src + (uint32_t)(c * 16), r);
+                    tmem_wait16(r);
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int i = c * 16 + j;
+                        const float v = __uint_as_float(r[j]);
                         if constexpr (ACCURATE) {
-                            const float t = sum[i] + v[j];  // Knuth's 2Sum: t + e == sum + v exactly
+                            const float t = sum[i] + v;  // Knuth's 2Sum: t + e == sum + v exactly
                             const float z = t - sum[i];
-                            comp[i] += (sum[i] - (t - z)) + (v[j] - z);
+                            comp[i] += (sum[i] - (t - z)) + (v - z);
                             sum[i] = t;
                         } else {
-                            sum[i] += v[j];
+                            sum[i] += v;
                         }
                     }
                 }
@@ -344,10 +355,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
                 for (int c = 0; c < HALF / 16; ++c) {
                     if (c * 16 < hcols) {
-                        float v[16];
-                        tmem_ld16(lane_base + 2u * acc_cols + (uint32_t)(c * 16), v);
+                        uint32_t r[16];
+                        tmem_ld16(lane_base + 2u * acc_cols + (uint32_t)(c * 16), r);
+                        tmem_wait16(r);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) comp[c * 16 + j] += v[j];
+                        for (int j = 0; j < 16; ++j) comp[c * 16 + j] += __uint_as_float(r[j]);
                     }
                 }
 #pragma unroll
