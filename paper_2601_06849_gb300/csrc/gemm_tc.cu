@@ -45,6 +45,7 @@ constexpr int WARP_TMA = 8;
 constexpr int WARP_MMA = 9;
 constexpr int NUM_THREADS = 320;
 constexpr int MAX_HALF = 128;            // columns per epilogue warp (bn <= 256)
+constexpr int STAGE_BYTES_EPI = NUM_EPI_WARPS * 32 * MAX_HALF * 4;
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
 constexpr int SMEM_LIMIT = 227 * 1024 - 1024;  // dynamic bytes; leaves room for the static barriers
 
@@ -161,6 +162,42 @@ __device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16]) {
                    "+r"(r[15])
                  :
                  : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// sum += v (ACCURATE: compensated, Knuth's 2Sum keeps the rounding error in comp)
+template <bool ACCURATE>
+__device__ __forceinline__ void acc_add(float& sum, float& comp, float v) {
+    if constexpr (ACCURATE) {
+        const float t = sum + v;
+        const float z = t - sum;
+        comp += (sum - (t - z)) + (v - z);
+        sum = t;
+    } else {
+        sum += v;
+    }
 }
 
 // ACCURATE = false: every product of a k-step into the k-block accumulator,
@@ -322,25 +359,23 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
             tc_fence_after();
             const uint32_t src = lane_base + (uint32_t)a * acc_cols;
+            // 32-column loads where the half-width allows, 16-column loads for a tail
 #pragma unroll
-            for (int c = 0; c < HALF / 16; ++c) {
-                if (c * 16 < hcols) {
+            for (int g = 0; g < HALF / 32; ++g) {
+                if ((g + 1) * 32 <= hcols) {
+                    uint32_t r[32];
+                    tmem_ld32(src + (uint32_t)(g * 32), r);
+                    tmem_wait32(r);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        acc_add<ACCURATE>(sum[g * 32 + j], comp[ACCURATE ? g * 32 + j : 0], __uint_as_float(r[j]));
+                } else if (g * 32 + 16 <= hcols) {
                     uint32_t r[16];
-                    tmem_ld16(src + (uint32_t)(c * 16), r);
+                    tmem_ld16(src + (uint32_t)(g * 32), r);
                     tmem_wait16(r);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int i = c * 16 + j;
-                        const float v = __uint_as_float(r[j]);
-                        if constexpr (ACCURATE) {
-                            const float t = sum[i] + v;  // Knuth's 2Sum: t + e == sum + v exactly
-                            const float z = t - sum[i];
-                            comp[i] += (sum[i] - (t - z)) + (v - z);
-                            sum[i] = t;
-                        } else {
-                            sum[i] += v;
-                        }
-                    }
+                    for (int j = 0; j < 16; ++j)
+                        acc_add<ACCURATE>(sum[g * 32 + j], comp[ACCURATE ? g * 32 + j : 0], __uint_as_float(r[j]));
                 }
             }
             tc_fence_before();
@@ -367,13 +402,23 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
         }
         if (ok && !*abort_flag) {
+            // Every product has completed (the last k-block sum was waited for), so
+            // the pipeline's shared memory is free: stage this warp's 32 x hcols sums
+            // there column-major and apply the epilogue in a rolled loop (one copy
+            // of its code instead of one per column).
+            float* stage = reinterpret_cast<float*>(smem) + (size_t)warp * 32 * MAX_HALF;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the TMA writes there
+#pragma unroll
+            for (int c = 0; c < HALF; ++c)
+                if (c < hcols) stage[c * 32 + lane] = sum[c];
+            __syncwarp();
             const int mm = tm * BM + quarter * 32 + lane;
             if (mm < p.M) {
                 const int mh = mm / p.n, ml = mm - mh * p.n;
                 const int nn0 = tn * p.bn + half * hcols;
-#pragma unroll
-                for (int c = 0; c < HALF; ++c)
-                    if (c < hcols && nn0 + c < p.n) p.e.apply(b, mh, ml, nn0 + c, sum[c]);
+                const int cols = min(hcols, p.n - nn0);
+#pragma unroll 4
+                for (int c = 0; c < cols; ++c) p.e.apply(b, mh, ml, nn0 + c, stage[c * 32 + lane]);
             }
         }
     }
@@ -479,6 +524,8 @@ TcConfig tc_choose(int M, int n, int products) {
     c.stage_bytes = (unsigned)c.pieces * ((unsigned)A_BYTES + b_bytes);
     int s = (SMEM_LIMIT - 1024) / (int)c.stage_bytes;
     if (s > 8) s = 8;
+    // the epilogue stages 8 warps x 32 rows x MAX_HALF sums in the pipeline buffers
+    while (s * (int)c.stage_bytes < STAGE_BYTES_EPI && (s + 1) * (int)c.stage_bytes <= SMEM_LIMIT - 1024) ++s;
     c.stages = s;
     c.smem_bytes = s * (int)c.stage_bytes + 1024;
     return c;
