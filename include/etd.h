@@ -168,6 +168,27 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info);
 etd_status etd_set_timing(etd_plan* p, int enable);
 etd_status etd_kernel_times(etd_plan* p, int kind, double* total_ms, long long* launches);
 
+/*
+ * Spectral transform without device allocation. The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory at
+ * the time of the call (a host framework's caching allocator has reserved the
+ * GPU's memory, or a latency-critical loop cannot afford the device-wide
+ * synchronisation of cudaFree).
+ *   out_dev = T(in_dev) per component, the transform of etd_transform with FP32
+ *   CUDA-core products; fields float32, [comp][z][y][x], device memory, caller-owned.
+ *   d 2 or 3, n >= 2, n_comp 1 or 2, stream a cudaStream_t (NULL = legacy default).
+ * Workspace: a static device array of ETD_NOALLOC_MAX_ELEMS floats (16 MiB)
+ * that every GPU loading the library holds until the process exits; a call needs
+ * n^2 + k n_comp n^d floats (k = 1 in 2D, 2 in 3D) and returns ETD_ERR_INVALID_ARG
+ * beyond that. The call allocates nothing. Its first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device current);
+ * make that first call before any stream capture. All calls share the array and
+ * it keeps the last call's contents: calls that overlap on the GPU (other streams,
+ * other host threads) race. Asynchronous on `stream`.
+ */
+#define ETD_NOALLOC_MAX_ELEMS 4194304
+etd_status etd_transform_noalloc(int d, int n, int n_comp, const void* in_dev, void* out_dev, void* stream);
+
 /* Release every resource of the plan. NULL-safe. */
 etd_status etd_plan_destroy(etd_plan* p);
 

@@ -144,6 +144,9 @@ struct Rx {
     T rp[4];
 };
 
+// Record the message etd_last_error() returns on this host thread (etd_plan.cu).
+void set_last_error(const char* msg);
+
 // ---- launchers (defined in the .cu files) ----
 void launch_gemm_simt_f32(const float* A, const float* P, int M, int n, int nbatch, const Epi<float>& e,
                           cudaStream_t st);

@@ -347,6 +347,10 @@ etd_status check_device_ptr(const void* ptr, const char* what) {
 
 }  // namespace
 
+namespace etd {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace etd
+
 extern "C" {
 
 etd_status etd_options_default(etd_options* opt) {

@@ -27,7 +27,9 @@ SYMBOLS = (
     "etd_options_default", "etd_plan_create", "etd_step", "etd_step_host", "etd_transform",
     "etd_plan_invalidate", "etd_set_time", "etd_sync", "etd_field_stats", "etd_get_plan_info",
     "etd_set_timing", "etd_kernel_times", "etd_plan_destroy", "etd_status_string", "etd_last_error",
+    "etd_transform_noalloc",
 )
+ETD_NOALLOC_MAX_ELEMS = 4194304
 
 
 class EtdError(RuntimeError):
@@ -88,6 +90,7 @@ def lib():
             "etd_plan_destroy": ([vp], i),
             "etd_status_string": ([i], ctypes.c_char_p),
             "etd_last_error": ([], ctypes.c_char_p),
+            "etd_transform_noalloc": ([i, i, i, vp, vp, vp], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -165,6 +168,15 @@ def etd_kernel_times(plan: int, kind: int):
     ms, cnt = ctypes.c_double(), ctypes.c_longlong()
     _check(lib().etd_kernel_times(plan, kind, ctypes.byref(ms), ctypes.byref(cnt)))
     return ms.value, cnt.value
+
+
+def etd_transform_noalloc(d: int, n: int, n_comp: int, in_dev: int, out_dev: int, stream: int = 0) -> None:
+    """T(in) into out (float32 device fields) with no device allocation: the
+    workspace is a fixed 16 MiB device array inside the library. For callers
+    that must not allocate device memory during the call (a framework allocator
+    owns the GPU's memory, or cudaFree's device-wide synchronisation cannot be
+    afforded). Concurrent calls on the GPU share that array and race."""
+    _check(lib().etd_transform_noalloc(d, n, n_comp, in_dev, out_dev, stream))
 
 
 def etd_plan_destroy(plan: int) -> None:
