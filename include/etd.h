@@ -57,14 +57,19 @@ enum {
 };
 /* Every precision keeps the carried spectral state and the factor grids in FP64. */
 
-/* Reaction f(t, u), evaluated pointwise (autonomous kinds). */
+/* Reaction f(t, u), evaluated pointwise. */
 enum {
     ETD_RX_NONE = 0,       /* f = 0 */
     ETD_RX_LINEAR = 1,     /* f = c u; rx_params[0] = c; any n_comp */
     ETD_RX_ALLEN_CAHN = 2, /* f = u - u^3; n_comp = 1 (Example 5.1 without forcing) */
-    ETD_RX_FHN = 3         /* FitzHugh-Nagumo (Example 5.3), n_comp = 2:
+    ETD_RX_FHN = 3,        /* FitzHugh-Nagumo (Example 5.3), n_comp = 2:
                               f_u = u - c3 u^3 - v, f_v = eps (u - a v - b);
                               rx_params = {c3, eps, a, b} */
+    ETD_RX_SINGULAR = 4,   /* f = rho u / (1 - u) (Example 5.2); rx_params[0] = rho; n_comp = 1 */
+    ETD_RX_AC_FORCED = 5   /* f = u (1 - u^2) + psi(x, t) (Example 5.1): psi makes
+                              u = e^{-lambda t} prod sin(pi x_i) exact, with
+                              -kappa Lap u0 = d pi^2 kappa u0; rx_params[0] = lambda;
+                              n_comp = 1; time-dependent (see etd_set_time) */
 };
 
 /* Time-integration factor family, the pade_order argument. */

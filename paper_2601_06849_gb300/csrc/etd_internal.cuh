@@ -142,6 +142,10 @@ struct Rx {
     long long bs_out;
     int split;
     T rp[4];
+    // ETD_RX_AC_FORCED: psi(x, t) = (-lambda + d pi^2 kappa) e u0 - e u0 (1 - (e u0)^2), e = e^{-lambda t}
+    int d;
+    double decay;     // e^{-lambda t}
+    double psi_coef;  // -lambda + d pi^2 kappa
 };
 
 // Record the message etd_last_error() returns on this host thread (etd_plan.cu).

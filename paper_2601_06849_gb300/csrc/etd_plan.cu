@@ -270,8 +270,13 @@ etd_status run_chain(etd_plan* p, int& cur, int slot, int final_mode, int final_
 // Reaction (kind >= 0) or plain split (kind = -1) of a physical field into operand buffer 0.
 template <typename T>
 etd_status run_react(etd_plan* p, int kind, const void* in, int ld_in, long long bs_in, double t, int split) {
-    (void)t;  // the supported reactions are autonomous
     Rx<T> r{};
+    r.d = p->d;
+    if (kind == ETD_RX_AC_FORCED) {
+        const double lam = p->rp[0], pi = 3.14159265358979323846;
+        r.decay = std::exp(-lam * t);
+        r.psi_coef = -lam + p->d * pi * pi * p->kappa[0];
+    }
     r.kind = kind;
     r.ncomp = p->ncomp;
     r.n = p->n;
@@ -381,11 +386,13 @@ etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q,
         return fail(ETD_ERR_INVALID_ARG, "pade_order must be 2, 4 or 0 (exact exponential)");
     if (opt.n_comp < 1 || opt.n_comp > 2) return fail(ETD_ERR_INVALID_ARG, "n_comp must be 1 or 2");
     if (opt.flags != 0) return fail(ETD_ERR_INVALID_ARG, "flags must be 0");
-    if (opt.reaction < ETD_RX_NONE || opt.reaction > ETD_RX_FHN) return fail(ETD_ERR_INVALID_ARG, "unknown reaction");
+    if (opt.reaction < ETD_RX_NONE || opt.reaction > ETD_RX_AC_FORCED)
+        return fail(ETD_ERR_INVALID_ARG, "unknown reaction");
     if (opt.reaction == ETD_RX_FHN && opt.n_comp != 2)
         return fail(ETD_ERR_INVALID_ARG, "FitzHugh-Nagumo needs n_comp = 2");
-    if (opt.reaction == ETD_RX_ALLEN_CAHN && opt.n_comp != 1)
-        return fail(ETD_ERR_INVALID_ARG, "Allen-Cahn needs n_comp = 1");
+    if ((opt.reaction == ETD_RX_ALLEN_CAHN || opt.reaction == ETD_RX_SINGULAR || opt.reaction == ETD_RX_AC_FORCED) &&
+        opt.n_comp != 1)
+        return fail(ETD_ERR_INVALID_ARG, "this reaction needs n_comp = 1");
     if (opt.precision < ETD_PREC_FP64 || opt.precision > ETD_PREC_TF32X6)
         return fail(ETD_ERR_INVALID_ARG, "unknown precision");
     if (opt.precision == ETD_PREC_BF16X3 || opt.precision == ETD_PREC_BF16X6)

@@ -57,6 +57,24 @@ __global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
                 store_split(r.out_hi, r.out_lo, r.out_lo2, oo, u - u * u * u, r.split);
                 break;
             }
+            case ETD_RX_SINGULAR: {
+                const T u = r.in[oi];
+                store_split(r.out_hi, r.out_lo, r.out_lo2, oo, r.rp[0] * u / ((T)1 - u), r.split);
+                break;
+            }
+            case ETD_RX_AC_FORCED: {
+                // u0 = prod sin(pi x_axis) at x_i = (i+1)/(n+1); psi in FP64
+                const double inv = 1.0 / (double)(r.n + 1);
+                const long long y = row % r.n, z = row / r.n;
+                double u0 = sinpi((double)(x + 1) * inv) * sinpi((double)(y + 1) * inv);
+                if (r.d == 3) u0 *= sinpi((double)(z + 1) * inv);
+                const double ue = r.decay * u0;
+                const double psi = r.psi_coef * ue - ue * (1.0 - ue * ue);
+                const T u = r.in[oi];
+                store_split(r.out_hi, r.out_lo, r.out_lo2, oo, (T)((double)u * (1.0 - (double)u * (double)u) + psi),
+                            r.split);
+                break;
+            }
             default:
                 for (int c = 0; c < r.ncomp; ++c) {
                     const T u = r.in[c * r.bs_in + oi];

@@ -1,0 +1,105 @@
+"""The GPU path reproduces the paper's printed errors E(N) (Section 5).
+
+E(N) = max over the coarse times S_16 (2D) / S_10 (3D) of the l-infinity error
+(Tables 1, 2: against the exact solution e^{-t} prod sin(pi x) of Example 5.1;
+Table 4: against the same scheme at N = 512, Example 5.2). The GPU runs the
+split-TF32 path; each coarse interval is one etd_step call. The printed values
+have three digits; the GPU value must round to them.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from gpu_util import need_gpu, rel_err
+from oracle import oracle as O
+from paper_2601_06849_gb300 import etd, inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden(name, max_n):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            p, N, E = line.split()
+            if int(N) <= max_n:
+                rows.append((int(p), int(N), float(E)))
+    return rows
+
+
+def three_sig(x):
+    return float(f"{x:.2E}")
+
+
+def gpu_manufactured_error(torch, d, n, N, pade, coarse):
+    u0 = inputs.sine_mode(n, d, (1,) * d)
+    plan = etd.Plan(d, n, 1.0, 0.0, 1.0 / N, pade=pade, precision="tf32x3", reaction="ac_forced", rx_params=(1.0,))
+    u = torch.tensor(u0[None], dtype=torch.float32, device="cuda")
+    E, per = 0.0, N // coarse
+    for c in range(coarse):
+        plan.step(u, per)
+        plan.sync()
+        t = (c + 1) * per / N
+        E = max(E, float(np.abs(u[0].double().cpu().numpy() - np.exp(-t) * u0).max()))
+    plan.close()
+    return E
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("pade,N,E", golden("table1_ex51_2d.txt", 64))
+def test_table1_on_gpu(pade, N, E):
+    torch = need_gpu()
+    assert three_sig(gpu_manufactured_error(torch, 2, 511, N, pade, 16)) == pytest.approx(E, rel=1e-9)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("pade,N,E", golden("table2_ex51_3d.txt", 40))
+def test_table2_on_gpu(pade, N, E):
+    torch = need_gpu()
+    assert three_sig(gpu_manufactured_error(torch, 3, 79, N, pade, 10)) == pytest.approx(E, rel=1e-9)
+
+
+def gpu_singular_trajectory(torch, N, n=511):
+    u0 = 0.99 * inputs.sine_mode(n, 2, (1, 1))
+    plan = etd.Plan(2, n, 1.0, 1.0, 1.0 / N, pade=2, precision="tf32x3", reaction="singular", rx_params=(0.1,))
+    u = torch.tensor(u0[None], dtype=torch.float32, device="cuda")
+    out, per = [], N // 16
+    for c in range(16):
+        plan.step(u, per)
+        plan.sync()
+        out.append(u[0].double().cpu().numpy())
+    plan.close()
+    return out
+
+
+@pytest.mark.gpu
+def test_table4_on_gpu():
+    torch = need_gpu()
+    ref = gpu_singular_trajectory(torch, 512)
+    for pade, N, E in golden("table4_ex52_2d.txt", 64):
+        tr = gpu_singular_trajectory(torch, N)
+        err = max(np.abs(a - b).max() for a, b in zip(tr, ref))
+        assert three_sig(err) == pytest.approx(E, rel=1e-9), (N, err)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind,rp,q", [("ac_forced", (1.0,), 0.0), ("singular", (0.1,), 1.0)])
+@pytest.mark.parametrize("d,n", [(2, 63), (3, 21)])
+def test_time_dependent_and_singular_parity(kind, rp, q, d, n):
+    """Direct parity with the oracle, t advancing across calls (etd_set_time)."""
+    torch = need_gpu()
+    tau, steps = 1.0 / 32, 8
+    u0 = (0.99 if kind == "singular" else 1.0) * inputs.sine_mode(n, d, (1,) * d)[None]
+    oracle_kind = {"ac_forced": "ac_manufactured"}.get(kind, kind)
+    ref = O.run(O.Problem(d=d, n=n, kappa=(1.0,), q=q, tau=tau, reaction=oracle_kind, rp=rp), u0, 2 * steps,
+                t0=0.25)
+    plan = etd.Plan(d, n, 1.0, q, tau, precision="tf32x3", reaction=kind, rx_params=rp)
+    plan.set_time(0.25)
+    u = torch.tensor(u0, dtype=torch.float32, device="cuda")
+    plan.step(u, steps)
+    plan.step(u, steps)
+    plan.sync()
+    assert rel_err(u.double().cpu().numpy(), ref) < 1e-6
+    plan.close()
