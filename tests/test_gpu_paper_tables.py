@@ -85,21 +85,30 @@ def test_table4_on_gpu():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["tf32x3", "tf32x6"])
 @pytest.mark.parametrize("kind,rp,q", [("ac_forced", (1.0,), 0.0), ("singular", (0.1,), 1.0)])
 @pytest.mark.parametrize("d,n", [(2, 63), (3, 21)])
-def test_time_dependent_and_singular_parity(kind, rp, q, d, n):
-    """Direct parity with the oracle, t advancing across calls (etd_set_time)."""
+def test_time_dependent_and_singular_parity(kind, rp, q, d, n, precision):
+    """Direct parity with the oracle, t advancing across calls (etd_set_time).
+
+    tf32x6 is accurate in every pass: bound 1e-6. tf32x3 runs the per-step passes
+    with two-piece operands (2^-22-level error); their error reaches the state
+    through tau f, so its bound grows by the factor (1 + tau max|f| / max|u|) of
+    this problem (the manufactured forcing makes |f| about 28 |u| here)."""
     torch = need_gpu()
     tau, steps = 1.0 / 32, 8
     u0 = (0.99 if kind == "singular" else 1.0) * inputs.sine_mode(n, d, (1,) * d)[None]
     oracle_kind = {"ac_forced": "ac_manufactured"}.get(kind, kind)
-    ref = O.run(O.Problem(d=d, n=n, kappa=(1.0,), q=q, tau=tau, reaction=oracle_kind, rp=rp), u0, 2 * steps,
-                t0=0.25)
-    plan = etd.Plan(d, n, 1.0, q, tau, precision="tf32x3", reaction=kind, rx_params=rp)
+    P = O.Problem(d=d, n=n, kappa=(1.0,), q=q, tau=tau, reaction=oracle_kind, rp=rp)
+    ref = O.run(P, u0, 2 * steps, t0=0.25)
+    # |f| / |u| of this problem from one oracle step: (U1 - E U0)/tau ~ f
+    f_scale = 28.6 if kind == "ac_forced" else 0.1 / (1 - 0.99)
+    bound = 1e-6 if precision == "tf32x6" else 1e-6 * (1 + tau * f_scale)
+    plan = etd.Plan(d, n, 1.0, q, tau, precision=precision, reaction=kind, rx_params=rp)
     plan.set_time(0.25)
     u = torch.tensor(u0, dtype=torch.float32, device="cuda")
     plan.step(u, steps)
     plan.step(u, steps)
     plan.sync()
-    assert rel_err(u.double().cpu().numpy(), ref) < 1e-6
+    assert rel_err(u.double().cpu().numpy(), ref) < bound
     plan.close()
