@@ -41,6 +41,7 @@ WORKLOADS = {
     "ac2d_64": (2, 64, 1e-2, None, 0.0, 1e-3, "allen_cahn", "2D Allen-Cahn n=64, kappa=1e-2 q=0 tau=1e-3"),
 }
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
+KERNEL_FILES = ["paper_2601_06849_gb300/csrc/gemm_tc.cu", "paper_2601_06849_gb300/csrc/etd_internal.cuh"]
 L2_BYTES = 129e6
 
 
@@ -164,8 +165,15 @@ def barrier(world):
         dist.barrier()
 
 
-def cpu_baseline(name, steps=5):
-    """The FP64 CPU oracle as it stands, all host cores, `steps` time steps of the workload."""
+def cpu_baseline(name, gpu_field=None, gpu_steps=0, max_steps=200):
+    """The FP64 CPU oracle as it stands, all host cores, on the same workload.
+
+    It runs min(gpu_steps, max_steps) time steps (at least 5) from the same
+    initial field; when that covers every step the GPU took, the GPU's field is
+    compared with the oracle's (max |U_gpu - U_oracle| / max |U_oracle| per
+    component, the error the metric is quoted at)."""
+    import numpy as np
+
     from oracle import oracle as O
 
     d, n, ku, kv, q, tau, rx, _ = WORKLOADS[name]
@@ -173,13 +181,37 @@ def cpu_baseline(name, steps=5):
     P = O.Problem(d=d, n=n, kappa=kap, q=q, tau=tau, pade=2, reaction=rx, rp=FHN if rx == "fhn" else ())
     u0 = initial_field(name)
     O.lib()  # build and load before timing
+    steps = max(5, min(gpu_steps, max_steps))
     t0 = time.perf_counter()
-    O.run(P, u0, steps)
+    ref = O.run(P, u0, steps)
     dt = time.perf_counter() - t0
-    unknowns = u0.size
-    return {"value": unknowns * steps / dt, "unit": "unknown-updates/s", "cores": O.max_threads(), "kind": "oracle",
-            "sample": f"{steps} FP64 time step(s) of the full {name} workload ({unknowns} unknowns), "
-                      f"Thomas/LU oracle, OpenMP over 1D lines", "seconds": dt}
+    out = {"value": u0.size * steps / dt, "unit": "unknown-updates/s", "cores": O.max_threads(), "kind": "oracle",
+           "sample": f"{steps} FP64 time steps of the full {name} workload ({u0.size} unknowns), "
+                     f"Thomas/LU oracle, OpenMP over 1D lines", "seconds": dt}
+    if gpu_field is not None and steps == gpu_steps:
+        err = [float(np.abs(gpu_field[c] - ref[c]).max() / np.abs(ref[c]).max()) for c in range(ref.shape[0])]
+        out["rel_err_vs_gpu"] = max(err)
+        out["rel_err_per_component"] = err
+    return out
+
+
+def recorded_traffic(kernel_files, record):
+    """Bytes per launch from a committed ncu record, if the kernel sources still
+    hash to what was profiled; else None."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in kernel_files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    try:
+        with open(os.path.join(ROOT, record)) as fh:
+            rec = dict(line.strip().split(": ", 1) for line in fh if ": " in line and not line.startswith("#"))
+    except OSError:
+        return None, h.hexdigest()
+    if rec.get("kernel_source_sha256") != h.hexdigest():
+        return None, h.hexdigest()
+    return float(rec["dram_bytes_per_launch"]), h.hexdigest()
 
 
 def run_reference(args, world, rank):
@@ -298,14 +330,19 @@ def main():
     e2e_s = barrier_max(time.perf_counter() - t0, world)
     bytes_field = unknowns * (8 if plan.dtype == torch.float64 else 4)
 
+    gpu_field = u.double().cpu().numpy()
     peaks, src = measured_peaks()
     avg_gemm_ms = gemm_ms / max(gemm_n, 1)
     if info.products > 0:
         flops = info.gemm_flops * info.products
         peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
         achieved = flops / (avg_gemm_ms * 1e-3) / 1e12
+        traffic, src_hash = (None, None)
+        if name == "fhn2d_4096" and args.precision == "tf32x3":
+            traffic, src_hash = recorded_traffic(KERNEL_FILES, "profiles/gemm_tf32_tc_fhn4096_traffic.md")
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "gemm_tf32_tc_kernel (transform pass)",
+                "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "kernel": "gemm_tf32_tc_kernel<false> (per-step transform pass)",
                 "peak_source": f"{src}: bf16_tflops_sustained x 1.1/2.25 (TF32/BF16 nominal)",
                 "flops_per_launch": flops, "avg_launch_ms": avg_gemm_ms}
     else:
@@ -351,7 +388,9 @@ def main():
     if cs:
         line["clocks"] = cs
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(name)
+        line["cpu_baseline"] = cpu_baseline(name, gpu_field, args.warmup + args.steps)
+        if "rel_err_vs_gpu" in line["cpu_baseline"]:
+            line["rel_err_vs_fp64_oracle"] = line["cpu_baseline"]["rel_err_vs_gpu"]
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
