@@ -168,6 +168,7 @@ struct TcConfig {
     int products;    // 1 (TF32), 3 (two-piece split) or 6 (three-piece split)
     int pieces;      // operand pieces read per product mode
     bool accurate;   // separate correction accumulator + compensated k-block sums
+    bool persistent; // one CTA per SM, epilogue overlapped with the next tile
     int tiles_m, tiles_n;
     int tmem_cols;
     int smem_bytes;

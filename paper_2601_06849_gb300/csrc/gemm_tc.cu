@@ -52,6 +52,7 @@ constexpr int SMEM_LIMIT = 227 * 1024 - 1024;  // dynamic bytes; leaves room for
 struct KParams {
     int M, n, bn, stages, products, pieces, tiles_m, tiles_n, tmem_cols;
     int acc_cols;  // columns of one accumulator region (power of two >= bn)
+    int nbatch;
     unsigned stage_bytes, b_bytes, tx_bytes;
     unsigned* err;
     Epi<float> e;
@@ -447,6 +448,285 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent variant of the per-step pass (two operand pieces or one, no
+// ACCURATE mode): one CTA per SM walks the tiles blockIdx.x, + gridDim.x, ...
+// The tile's epilogue runs while the next tile's products are already issued:
+//   warp 12     TMA producer (one lane), TMEM allocator (whole warp)
+//   warp 13     MMA issuer (one lane), k-blocks into TMEM buffers 0/1
+//   warps 0-7   drain each k-block buffer into FP32 register sums (two warps
+//               per TMEM lane quarter, one per 64-column half); at tile end
+//               they write the sums into TMEM staging buffer 0/1 (tcgen05.st)
+//   warps 8-11  read a staging buffer (tcgen05.ld) and run the epilogue
+// TMEM columns: [0,128) [128,256) k-block buffers, [256,384) [384,512) staging.
+// Shared memory holds only the TMA ring (three 64 KB stages at bn = 128).
+namespace pk {
+constexpr int BN = 128;
+constexpr int HALF = BN / 2;
+constexpr int NUM_DRAIN = 8;
+constexpr int NUM_STORE = 4;
+constexpr int WARP_TMA = 12;
+constexpr int WARP_MMA = 13;
+constexpr int THREADS = 14 * 32;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t KB_COLS = 128;        // one k-block buffer
+constexpr uint32_t STAGING0 = 256;       // first staging buffer
+}  // namespace pk
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]),
+        "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]),
+        "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(pk::THREADS, 1)
+    gemm_tf32_persistent_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                                const __grid_constant__ CUtensorMap mP0, const __grid_constant__ CUtensorMap mP1,
+                                const KParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ int s_skip;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    __shared__ int s_consumed;
+    __shared__ int s_issued;
+    // full[8], empty[8], kb_full[2], kb_empty[2], stage_full[2], stage_empty[2], done
+    __shared__ __align__(8) uint64_t s_bar[8 + 8 + 2 + 2 + 2 + 2 + 1];
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) s_skip = (*(volatile unsigned*)p.err != 0u);
+    __syncthreads();
+    if (s_skip) return;
+
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int S = p.stages;
+    volatile int* abort_flag = &s_abort;
+    const uint32_t bar_full = smem_u32(&s_bar[0]);
+    const uint32_t bar_empty = smem_u32(&s_bar[8]);
+    const uint32_t bar_kb_full = smem_u32(&s_bar[16]);
+    const uint32_t bar_kb_empty = smem_u32(&s_bar[18]);
+    const uint32_t bar_st_full = smem_u32(&s_bar[20]);
+    const uint32_t bar_st_empty = smem_u32(&s_bar[22]);
+    const uint32_t bar_done = smem_u32(&s_bar[24]);
+    const int nk = (p.n + BKF - 1) / BKF;
+    const int ntiles = p.nbatch * p.tiles_m * p.tiles_n;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(bar_full + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(bar_kb_full + 8 * a, 1);
+            mbar_init(bar_kb_empty + 8 * a, pk::NUM_DRAIN);
+            mbar_init(bar_st_full + 8 * a, pk::NUM_DRAIN);
+            mbar_init(bar_st_empty + 8 * a, pk::NUM_STORE);
+        }
+        mbar_init(bar_done, 1);
+        s_abort = 0;
+        s_consumed = 0;
+        s_issued = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == pk::WARP_TMA) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(pk::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == pk::WARP_TMA && lane == 0) {
+        // ---------------- TMA producer: one ring across all tiles ----------------
+        int g = 0;
+        bool stop = false;
+        for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+            const int tn = t % p.tiles_n;
+            const int tm = (t / p.tiles_n) % p.tiles_m;
+            const int b = t / (p.tiles_n * p.tiles_m);
+            const int arow = b * p.M + tm * BM;
+            const int prow = tn * p.bn;
+            for (int kb = 0; kb < nk; ++kb, ++g) {
+                const int s = g % S;
+                if (!mbar_wait(bar_empty + 8 * s, (uint32_t)(((g / S) & 1) ^ 1), abort_flag, p.err)) {
+                    stop = true;
+                    break;
+                }
+                const uint32_t st = smem_u32(smem + (size_t)s * p.stage_bytes);
+                const uint32_t fb = bar_full + 8 * s;
+                mbar_expect_tx(fb, p.tx_bytes);
+                const int k0 = kb * BKF;
+                const uint32_t sb = st + (uint32_t)p.pieces * A_BYTES;
+                tma_load_2d(st, &mA0, fb, k0, arow);
+                tma_load_2d(sb, &mP0, fb, k0, prow);
+                if (p.pieces > 1) {
+                    tma_load_2d(st + A_BYTES, &mA1, fb, k0, arow);
+                    tma_load_2d(sb + p.b_bytes, &mP1, fb, k0, prow);
+                }
+                s_issued = g + 1;
+            }
+        }
+    } else if (warp == pk::WARP_MMA && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t idesc = idesc_tf32(BM, p.bn);
+        int g = 0;
+        bool stop = false;
+        for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+            for (int kb = 0; kb < nk; ++kb, ++g) {
+                const int s = g % S;
+                const int a = g & 1;
+                if (!mbar_wait(bar_full + 8 * s, (uint32_t)((g / S) & 1), abort_flag, p.err) ||
+                    (g >= 2 && !mbar_wait(bar_kb_empty + 8 * a, (uint32_t)(((g >> 1) - 1) & 1), abort_flag, p.err))) {
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)a * pk::KB_COLS;
+                const uint32_t a0 = smem_u32(smem + (size_t)s * p.stage_bytes);
+                const uint32_t a1 = a0 + A_BYTES;
+                const uint32_t b0 = a0 + (uint32_t)p.pieces * A_BYTES;
+                const uint32_t b1 = b0 + p.b_bytes;
+#pragma unroll
+                for (int kk = 0; kk < BKF / 8; ++kk) {
+                    const uint32_t off = kk * 32;
+                    mma_tf32(d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
+                    if (p.products >= 3) {
+                        mma_tf32(d, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, 1u);
+                        mma_tf32(d, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                    }
+                }
+                mma_commit(bar_empty + 8 * s);
+                mma_commit(bar_kb_full + 8 * a);
+                s_consumed = g + 1;
+            }
+        }
+        mma_commit(bar_done);
+    } else if (warp < pk::NUM_DRAIN) {
+        // ---------------- drain: k-block sums -> FP32 register sums -> TMEM staging ----------------
+        const int quarter = warp & 3, half = warp >> 2;
+        const uint32_t lane_off = ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * pk::HALF);
+        const int hcols = p.bn / 2;  // 16, 32, 48 or 64
+        int g = 0, j = 0;
+        bool stop = false;
+        for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x, ++j) {
+            float sum[pk::HALF];
+#pragma unroll
+            for (int i = 0; i < pk::HALF; ++i) sum[i] = 0.f;
+            for (int kb = 0; kb < nk; ++kb, ++g) {
+                const int a = g & 1;
+                if (!mbar_wait(bar_kb_full + 8 * a, (uint32_t)((g >> 1) & 1), abort_flag, p.err)) {
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t src = tmem + lane_off + (uint32_t)a * pk::KB_COLS;
+#pragma unroll
+                for (int c = 0; c < pk::HALF / 32; ++c) {
+                    if ((c + 1) * 32 <= hcols) {
+                        uint32_t r[32];
+                        tmem_ld32(src + (uint32_t)(c * 32), r);
+                        tmem_wait32(r);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) sum[c * 32 + i] += __uint_as_float(r[i]);
+                    } else if (c * 32 + 16 <= hcols) {
+                        uint32_t r[16];
+                        tmem_ld16(src + (uint32_t)(c * 32), r);
+                        tmem_wait16(r);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) sum[c * 32 + i] += __uint_as_float(r[i]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_kb_empty + 8 * a);
+            }
+            if (stop) break;
+            const int sb = j & 1;
+            if (j >= 2 && !mbar_wait(bar_st_empty + 8 * sb, (uint32_t)(((j >> 1) - 1) & 1), abort_flag, p.err)) break;
+            tc_fence_after();
+            const uint32_t dst = tmem + lane_off + pk::STAGING0 + (uint32_t)sb * pk::KB_COLS;
+#pragma unroll
+            for (int c = 0; c < pk::HALF / 32; ++c) {
+                uint32_t r[32];
+#pragma unroll
+                for (int i = 0; i < 32; ++i) r[i] = __float_as_uint(sum[c * 32 + i]);
+                tmem_st32(dst + (uint32_t)(c * 32), r);
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_st_full + 8 * sb);
+        }
+    } else if (warp < pk::NUM_DRAIN + pk::NUM_STORE) {
+        // ---------------- store warps: staging -> fused epilogue -> global ----------------
+        const int quarter = warp & 3;
+        int j = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+            const int tn = t % p.tiles_n;
+            const int tm = (t / p.tiles_n) % p.tiles_m;
+            const int b = t / (p.tiles_n * p.tiles_m);
+            const int sb = j & 1;
+            if (!mbar_wait(bar_st_full + 8 * sb, (uint32_t)((j >> 1) & 1), abort_flag, p.err)) break;
+            tc_fence_after();
+            const uint32_t src = tmem + ((uint32_t)(quarter * 32) << 16) + pk::STAGING0 + (uint32_t)sb * pk::KB_COLS;
+            const int mm = tm * BM + quarter * 32 + lane;
+            const bool row_ok = mm < p.M;
+            const int mh = mm / p.n, ml = mm - mh * p.n;
+            const int nn0 = tn * p.bn;
+            for (int c0 = 0; c0 < p.bn; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(src + (uint32_t)c0, r);
+                tmem_wait16(r);
+                if (row_ok) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+                        if (nn0 + c0 + i < p.n) p.e.apply(b, mh, ml, nn0 + c0 + i, __uint_as_float(r[i]));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_st_empty + 8 * sb);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == pk::WARP_TMA && lane == 0) {
+        if (*abort_flag) {
+            for (int g = s_consumed; g < s_issued; ++g) {
+                const int s = g % S;
+                const unsigned long long t0 = globaltimer();
+                while (!mbar_try(bar_full + 8 * s, (uint32_t)((g / S) & 1)) && globaltimer() - t0 < 100000000ull) {
+                }
+            }
+        }
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try(bar_done, 0u) && globaltimer() - t0 < 200000000ull) {
+        }
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (warp == pk::WARP_TMA) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(pk::TMEM_COLS)
+                     : "memory");
+    }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -495,15 +775,16 @@ TcConfig tc_choose(int M, int n, int products) {
     TcConfig c{};
     c.products = products;
     c.pieces = products == 6 ? 3 : (products == 3 ? 2 : 1);
+    c.accurate = (c.pieces == 3);
+    c.persistent = !c.accurate;
     // tile width: the multiple of 32 up to bn_max that wastes the fewest columns
-    // (each of the two column halves is a whole number of 16-column TMEM loads);
-    // three operand pieces leave room for two 128-wide stages only
-    const int bn_max = (c.pieces == 3) ? 128 : 256;
+    // (each of the two column halves is a whole number of 16-column TMEM loads)
+    const int bn_max = 128;
     int best = bn_max, best_waste = 1 << 30;
     if (n <= bn_max) {
         best = ((n + 31) / 32) * 32;
     } else {
-        for (int bn = bn_max; bn >= 128; bn -= 32) {
+        for (int bn = bn_max; bn >= 64; bn -= 32) {
             const int waste = ((n + bn - 1) / bn) * bn - n;
             if (waste < best_waste) {
                 best_waste = waste;
@@ -514,18 +795,21 @@ TcConfig tc_choose(int M, int n, int products) {
     c.bn = best;
     c.tiles_n = (n + c.bn - 1) / c.bn;
     c.tiles_m = (M + BM - 1) / BM;
-    int acc = 32;
-    while (acc < c.bn) acc *= 2;
-    c.accurate = (c.pieces == 3);
-    // two k-block accumulator buffers (+ the correction accumulator, rounded up
-    // to the power of two that tcgen05.alloc needs)
-    c.tmem_cols = c.accurate ? 4 * acc : 2 * acc;
     const unsigned b_bytes = (unsigned)c.bn * BKF * 4;
     c.stage_bytes = (unsigned)c.pieces * ((unsigned)A_BYTES + b_bytes);
     int s = (SMEM_LIMIT - 1024) / (int)c.stage_bytes;
     if (s > 8) s = 8;
-    // the epilogue stages 8 warps x 32 rows x MAX_HALF sums in the pipeline buffers
-    while (s * (int)c.stage_bytes < STAGE_BYTES_EPI && (s + 1) * (int)c.stage_bytes <= SMEM_LIMIT - 1024) ++s;
+    if (c.persistent) {
+        c.tmem_cols = (int)pk::TMEM_COLS;  // two k-block buffers + two staging buffers of 128 columns
+    } else {
+        int acc = 32;
+        while (acc < c.bn) acc *= 2;
+        // two k-block accumulator buffers + the correction accumulator, rounded up
+        // to the power of two that tcgen05.alloc needs
+        c.tmem_cols = 4 * acc;
+        // the epilogue stages 8 warps x 32 rows x MAX_HALF sums in the pipeline buffers
+        while (s * (int)c.stage_bytes < STAGE_BYTES_EPI && (s + 1) * (int)c.stage_bytes <= SMEM_LIMIT - 1024) ++s;
+    }
     c.stages = s;
     c.smem_bytes = s * (int)c.stage_bytes + 1024;
     return c;
@@ -559,6 +843,9 @@ cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(gemm_tf32_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      SMEM_LIMIT);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(gemm_tf32_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     SMEM_LIMIT);
         if (e != cudaSuccess) {
             delete m;
             return e;
@@ -590,15 +877,26 @@ cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, in
     p.tx_bytes = cfg.stage_bytes;
     p.err = err;
     p.e = e;
-    const long long grid = (long long)nbatch * cfg.tiles_m * cfg.tiles_n;
+    p.nbatch = nbatch;
+    const long long ntiles = (long long)nbatch * cfg.tiles_m * cfg.tiles_n;
     const CUtensorMap* A = maps->a[a_index];
     const CUtensorMap* P = maps->p[slot];
-    if (cfg.accurate)
+    if (cfg.persistent) {
+        static int sms = 0;
+        if (!sms) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+        }
+        const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
+        gemm_tf32_persistent_kernel<<<grid, pk::THREADS, cfg.smem_bytes, st>>>(A[0], A[1], P[0], P[1], p);
+    } else if (cfg.accurate) {
         gemm_tf32_tc_kernel<true>
-            <<<(unsigned)grid, NUM_THREADS, cfg.smem_bytes, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
-    else
+            <<<(unsigned)ntiles, NUM_THREADS, cfg.smem_bytes, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
+    } else {
         gemm_tf32_tc_kernel<false>
-            <<<(unsigned)grid, NUM_THREADS, cfg.smem_bytes, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
+            <<<(unsigned)ntiles, NUM_THREADS, cfg.smem_bytes, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
+    }
     return cudaGetLastError();
 }
 
