@@ -485,6 +485,15 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
         : "memory");
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -619,8 +628,8 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     } else if (warp < pk::NUM_DRAIN) {
         // ---------------- drain: k-block sums -> FP32 register sums -> TMEM staging ----------------
         const int quarter = warp & 3, half = warp >> 2;
-        const uint32_t lane_off = ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * pk::HALF);
-        const int hcols = p.bn / 2;  // 16, 32, 48 or 64
+        const int hcols = p.bn / 2;  // 16, 32, 48 or 64 columns per warp
+        const uint32_t lane_off = ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * hcols);
         int g = 0, j = 0;
         bool stop = false;
         for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x, ++j) {
@@ -662,10 +671,17 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
             const uint32_t dst = tmem + lane_off + pk::STAGING0 + (uint32_t)sb * pk::KB_COLS;
 #pragma unroll
             for (int c = 0; c < pk::HALF / 32; ++c) {
-                uint32_t r[32];
+                if ((c + 1) * 32 <= hcols) {
+                    uint32_t r[32];
 #pragma unroll
-                for (int i = 0; i < 32; ++i) r[i] = __float_as_uint(sum[c * 32 + i]);
-                tmem_st32(dst + (uint32_t)(c * 32), r);
+                    for (int i = 0; i < 32; ++i) r[i] = __float_as_uint(sum[c * 32 + i]);
+                    tmem_st32(dst + (uint32_t)(c * 32), r);
+                } else if (c * 32 + 16 <= hcols) {
+                    uint32_t r[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) r[i] = __float_as_uint(sum[c * 32 + i]);
+                    tmem_st16(dst + (uint32_t)(c * 32), r);
+                }
             }
             tmem_wait_st();
             tc_fence_before();
