@@ -126,6 +126,80 @@ struct Epi {
     }
 };
 
+// Epilogue of up to N consecutive columns nn0 .. nn0+count-1 of one row
+// (mm = mh * n + ml), values v[]. Loads of the carried state for all columns are
+// issued before any store, so they overlap instead of each waiting a DRAM
+// round trip behind the previous column's stores.
+template <typename T, int N>
+__device__ __forceinline__ void epi_apply_batch(const Epi<T>& e, int b, int mh, int ml, int nn0, const float* v,
+                                                int count) {
+    const long long base = (long long)b * e.bs + (long long)mh * e.ld + ml;
+    const long long step = (long long)e.mq * e.ld;  // offset between consecutive nn
+    if (e.mode == EPI_PLAIN) {
+        T* d = e.dst + (long long)b * e.bs_dst + ((long long)nn0 * e.mq + mh) * e.ld_dst + ml;
+        const long long sd = (long long)e.mq * e.ld_dst;
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j < count) d[j * sd] = (T)v[j];
+        return;
+    }
+    const long long o0 = base + (long long)nn0 * step;
+    if (e.mode == EPI_SPLIT) {
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j < count) e.write_operand(o0 + j * step, (double)v[j]);
+        return;
+    }
+    if (e.mode == EPI_CARRY) {
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j < count) e.uhat[o0 + j * step] = (double)v[j];
+        return;
+    }
+    const double* g = e.grid + (long long)b * 3 * e.n;
+    if (e.mode == EPI_STAGE1) {
+        double u[N], sl[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            u[j] = (j < count) ? e.uhat[o0 + j * step] : 0.0;
+            sl[j] = (j < count) ? g[nn0 + j] : 0.0;
+        }
+        const double g1 = g[ml], g2 = g[e.n + ml];
+        const double gm = (e.d == 2) ? 1.0 : g[mh];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            if (j < count) {
+                const long long o = o0 + j * step;
+                const double sj = gm * sl[j];  // E_1(tau A_2) [E_1(tau A_2^z)]
+                const double w = (g1 * u[j] + g2 * (double)v[j]) * sj;
+                e.what[o] = w;
+                e.fq[o] = (T)(sj * (double)v[j]);
+                e.write_operand(o, w);
+            }
+        }
+        return;
+    }
+    if (e.mode == EPI_STAGE2) {
+        double w[N];
+        T f[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            w[j] = (j < count) ? e.what[o0 + j * step] : 0.0;
+            f[j] = (j < count) ? e.fq[o0 + j * step] : (T)0;
+        }
+        const double g3 = g[2 * e.n + ml];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            if (j < count) {
+                const long long o = o0 + j * step;
+                const double u = w[j] + g3 * ((double)v[j] - (double)f[j]);
+                e.uhat[o] = u;
+                e.write_operand(o, u);
+            }
+        }
+    }
+}
+
 // Reaction / split kernel arguments (steps a1 and a5).
 template <typename T>
 struct Rx {

@@ -103,6 +103,24 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_fla
     }
 }
 
+// Wait by a whole warp: lane 0 spins (bounded), then every lane observes the
+// completed phase itself (one try_wait, which succeeds) for acquire ordering.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* err) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, err) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) {
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try(bar, parity)) {
+            if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+                ok = 0;
+                break;
+            }
+        }
+    }
+    return __all_sync(0xffffffffu, ok) != 0;
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
@@ -418,9 +436,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const int mh = mm / p.n, ml = mm - mh * p.n;
                 const int nn0 = tn * p.bn + half * hcols;
                 const int cols = min(hcols, p.n - nn0);
-#pragma unroll 4
-                for (int c = 0; c < cols; ++c) p.e.apply(b, mh, ml, nn0 + c, stage[c * 32 + lane]);
-            }
+                for (int c0 = 0; c0 < cols; c0 += 16) {
+                    float v[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = stage[(c0 + i < hcols ? c0 + i : 0) * 32 + lane];
+                    epi_apply_batch<float, 16>(p.e, b, mh, ml, nn0 + c0, v, min(16, cols - c0));
+                }            }
         }
     }
 
@@ -638,7 +659,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
             for (int i = 0; i < pk::HALF; ++i) sum[i] = 0.f;
             for (int kb = 0; kb < nk; ++kb, ++g) {
                 const int a = g & 1;
-                if (!mbar_wait(bar_kb_full + 8 * a, (uint32_t)((g >> 1) & 1), abort_flag, p.err)) {
+                if (!warp_wait(bar_kb_full + 8 * a, (uint32_t)((g >> 1) & 1), abort_flag, p.err)) {
                     stop = true;
                     break;
                 }
@@ -666,7 +687,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
             }
             if (stop) break;
             const int sb = j & 1;
-            if (j >= 2 && !mbar_wait(bar_st_empty + 8 * sb, (uint32_t)(((j >> 1) - 1) & 1), abort_flag, p.err)) break;
+            if (j >= 2 && !warp_wait(bar_st_empty + 8 * sb, (uint32_t)(((j >> 1) - 1) & 1), abort_flag, p.err)) break;
             tc_fence_after();
             const uint32_t dst = tmem + lane_off + pk::STAGING0 + (uint32_t)sb * pk::KB_COLS;
 #pragma unroll
@@ -697,7 +718,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
             const int tm = (t / p.tiles_n) % p.tiles_m;
             const int b = t / (p.tiles_n * p.tiles_m);
             const int sb = j & 1;
-            if (!mbar_wait(bar_st_full + 8 * sb, (uint32_t)((j >> 1) & 1), abort_flag, p.err)) break;
+            if (!warp_wait(bar_st_full + 8 * sb, (uint32_t)((j >> 1) & 1), abort_flag, p.err)) break;
             tc_fence_after();
             const uint32_t src = tmem + ((uint32_t)(quarter * 32) << 16) + pk::STAGING0 + (uint32_t)sb * pk::KB_COLS;
             const int mm = tm * BM + quarter * 32 + lane;
@@ -709,9 +730,10 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                 tmem_ld16(src + (uint32_t)c0, r);
                 tmem_wait16(r);
                 if (row_ok) {
+                    float v[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (nn0 + c0 + i < p.n) p.e.apply(b, mh, ml, nn0 + c0 + i, __uint_as_float(r[i]));
+                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+                    epi_apply_batch<float, 16>(p.e, b, mh, ml, nn0 + c0, v, min(16, p.n - nn0 - c0));
                 }
             }
             tc_fence_before();
