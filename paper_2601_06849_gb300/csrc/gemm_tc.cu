@@ -479,7 +479,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 //               per TMEM lane quarter, one per 64-column half); at tile end
 //               they write the sums into TMEM staging buffer 0/1 (tcgen05.st)
 //   warps 8-11  read a staging buffer (tcgen05.ld) and run the epilogue
-// TMEM columns: [0,128) [128,256) k-block buffers, [256,384) [384,512) staging.
+// TMEM: four 128-column regions, nkb k-block buffers followed by nsb staging
+// buffers: 3 + 1 when K is long (the products of one k-block take ~0.6 us at
+// bn = 128, so the MMA needs two blocks of slack ahead of the drain), 2 + 2
+// when K is short and the epilogue, not the products, sets the pace.
 // Shared memory holds only the TMA ring (three 64 KB stages at bn = 128).
 namespace pk {
 constexpr int BN = 128;
@@ -490,8 +493,7 @@ constexpr int WARP_TMA = 12;
 constexpr int WARP_MMA = 13;
 constexpr int THREADS = 14 * 32;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr uint32_t KB_COLS = 128;        // one k-block buffer
-constexpr uint32_t STAGING0 = 256;       // first staging buffer
+constexpr uint32_t KB_COLS = 128;        // one TMEM region (k-block or staging buffer)
 }  // namespace pk
 
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
@@ -531,8 +533,8 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     __shared__ int s_abort;
     __shared__ int s_consumed;
     __shared__ int s_issued;
-    // full[8], empty[8], kb_full[2], kb_empty[2], stage_full[2], stage_empty[2], done
-    __shared__ __align__(8) uint64_t s_bar[8 + 8 + 2 + 2 + 2 + 2 + 1];
+    // full[8], empty[8], kb_full[3], kb_empty[3], stage_full[2], stage_empty[2], done
+    __shared__ __align__(8) uint64_t s_bar[8 + 8 + 3 + 3 + 2 + 2 + 1];
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) s_skip = (*(volatile unsigned*)p.err != 0u);
@@ -545,11 +547,14 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     const uint32_t bar_full = smem_u32(&s_bar[0]);
     const uint32_t bar_empty = smem_u32(&s_bar[8]);
     const uint32_t bar_kb_full = smem_u32(&s_bar[16]);
-    const uint32_t bar_kb_empty = smem_u32(&s_bar[18]);
-    const uint32_t bar_st_full = smem_u32(&s_bar[20]);
-    const uint32_t bar_st_empty = smem_u32(&s_bar[22]);
-    const uint32_t bar_done = smem_u32(&s_bar[24]);
+    const uint32_t bar_kb_empty = smem_u32(&s_bar[19]);
+    const uint32_t bar_st_full = smem_u32(&s_bar[22]);
+    const uint32_t bar_st_empty = smem_u32(&s_bar[24]);
+    const uint32_t bar_done = smem_u32(&s_bar[26]);
     const int nk = (p.n + BKF - 1) / BKF;
+    const int nkb = nk >= 16 ? 3 : 2;  // k-block buffers
+    const int nsb = 4 - nkb;           // staging buffers
+    const uint32_t staging0 = (uint32_t)nkb * pk::KB_COLS;
     const int ntiles = p.nbatch * p.tiles_m * p.tiles_n;
 
     if (threadIdx.x == 0) {
@@ -557,9 +562,11 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
             mbar_init(bar_full + 8 * s, 1);
             mbar_init(bar_empty + 8 * s, 1);
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < 3; ++a) {
             mbar_init(bar_kb_full + 8 * a, 1);
             mbar_init(bar_kb_empty + 8 * a, pk::NUM_DRAIN);
+        }
+        for (int a = 0; a < 2; ++a) {
             mbar_init(bar_st_full + 8 * a, pk::NUM_DRAIN);
             mbar_init(bar_st_empty + 8 * a, pk::NUM_STORE);
         }
@@ -619,9 +626,10 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
         for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
             for (int kb = 0; kb < nk; ++kb, ++g) {
                 const int s = g % S;
-                const int a = g & 1;
+                const int a = g % nkb;
                 if (!mbar_wait(bar_full + 8 * s, (uint32_t)((g / S) & 1), abort_flag, p.err) ||
-                    (g >= 2 && !mbar_wait(bar_kb_empty + 8 * a, (uint32_t)(((g >> 1) - 1) & 1), abort_flag, p.err))) {
+                    (g >= nkb &&
+                     !mbar_wait(bar_kb_empty + 8 * a, (uint32_t)(((g / nkb) - 1) & 1), abort_flag, p.err))) {
                     stop = true;
                     break;
                 }
@@ -658,8 +666,8 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
 #pragma unroll
             for (int i = 0; i < pk::HALF; ++i) sum[i] = 0.f;
             for (int kb = 0; kb < nk; ++kb, ++g) {
-                const int a = g & 1;
-                if (!warp_wait(bar_kb_full + 8 * a, (uint32_t)((g >> 1) & 1), abort_flag, p.err)) {
+                const int a = g % nkb;
+                if (!warp_wait(bar_kb_full + 8 * a, (uint32_t)((g / nkb) & 1), abort_flag, p.err)) {
                     stop = true;
                     break;
                 }
@@ -686,10 +694,11 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                 if (lane == 0) mbar_arrive(bar_kb_empty + 8 * a);
             }
             if (stop) break;
-            const int sb = j & 1;
-            if (j >= 2 && !warp_wait(bar_st_empty + 8 * sb, (uint32_t)(((j >> 1) - 1) & 1), abort_flag, p.err)) break;
+            const int sb = j % nsb;
+            if (j >= nsb && !warp_wait(bar_st_empty + 8 * sb, (uint32_t)(((j / nsb) - 1) & 1), abort_flag, p.err))
+                break;
             tc_fence_after();
-            const uint32_t dst = tmem + lane_off + pk::STAGING0 + (uint32_t)sb * pk::KB_COLS;
+            const uint32_t dst = tmem + lane_off + staging0 + (uint32_t)sb * pk::KB_COLS;
 #pragma unroll
             for (int c = 0; c < pk::HALF / 32; ++c) {
                 if ((c + 1) * 32 <= hcols) {
@@ -717,10 +726,10 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
             const int tn = t % p.tiles_n;
             const int tm = (t / p.tiles_n) % p.tiles_m;
             const int b = t / (p.tiles_n * p.tiles_m);
-            const int sb = j & 1;
-            if (!warp_wait(bar_st_full + 8 * sb, (uint32_t)((j >> 1) & 1), abort_flag, p.err)) break;
+            const int sb = j % nsb;
+            if (!warp_wait(bar_st_full + 8 * sb, (uint32_t)((j / nsb) & 1), abort_flag, p.err)) break;
             tc_fence_after();
-            const uint32_t src = tmem + ((uint32_t)(quarter * 32) << 16) + pk::STAGING0 + (uint32_t)sb * pk::KB_COLS;
+            const uint32_t src = tmem + ((uint32_t)(quarter * 32) << 16) + staging0 + (uint32_t)sb * pk::KB_COLS;
             const int mm = tm * BM + quarter * 32 + lane;
             const bool row_ok = mm < p.M;
             const int mh = mm / p.n, ml = mm - mh * p.n;
