@@ -103,6 +103,22 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_fla
     }
 }
 
+// Tile t -> (component b, row tile tm, column tile tn). Tiles walk down groups of
+// gm row tiles before moving to the next column tile, so the tiles running at
+// the same time share a few A panels and a few P panels (working set of a wave
+// of 152 tiles ~100-140 MB, about the 129 MB L2) instead of all of P.
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int gm_max, int& b, int& tm, int& tn) {
+    const int per_b = tiles_m * tiles_n;
+    b = t / per_b;
+    const int r = t - b * per_b;
+    const int group = r / (gm_max * tiles_n);
+    const int first_m = group * gm_max;
+    const int gm = min(gm_max, tiles_m - first_m);
+    const int rr = r - group * gm_max * tiles_n;
+    tm = first_m + rr % gm;
+    tn = rr / gm;
+}
+
 // Wait by a whole warp: lane 0 spins (bounded), then every lane observes the
 // completed phase itself (one try_wait, which succeeds) for acquire ordering.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* err) {
@@ -256,11 +272,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const uint32_t bar_acc_empty = smem_u32(&s_bar[18]);
     const uint32_t bar_done = smem_u32(&s_bar[20]);
 
-    int t = blockIdx.x;
-    const int tn = t % p.tiles_n;
-    t /= p.tiles_n;
-    const int tm = t % p.tiles_m;
-    const int b = t / p.tiles_m;
+    int b, tm, tn;
+    tile_coords(blockIdx.x, p.tiles_m, p.tiles_n, 16, b, tm, tn);
     const int nk = (p.n + BKF - 1) / BKF;
     // TMEM columns: [0, acc) and [acc, 2 acc) k-block buffers, [2 acc, 3 acc) corrections (ACCURATE)
     const uint32_t acc_cols = (uint32_t)p.acc_cols;
@@ -593,9 +606,8 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
         int g = 0;
         bool stop = false;
         for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-            const int tn = t % p.tiles_n;
-            const int tm = (t / p.tiles_n) % p.tiles_m;
-            const int b = t / (p.tiles_n * p.tiles_m);
+            int b, tm, tn;
+            tile_coords(t, p.tiles_m, p.tiles_n, 12, b, tm, tn);
             const int arow = b * p.M + tm * BM;
             const int prow = tn * p.bn;
             for (int kb = 0; kb < nk; ++kb, ++g) {
@@ -723,9 +735,8 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
         const int quarter = warp & 3;
         int j = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
-            const int tn = t % p.tiles_n;
-            const int tm = (t / p.tiles_n) % p.tiles_m;
-            const int b = t / (p.tiles_n * p.tiles_m);
+            int b, tm, tn;
+            tile_coords(t, p.tiles_m, p.tiles_n, 12, b, tm, tn);
             const int sb = j % nsb;
             if (!warp_wait(bar_st_full + 8 * sb, (uint32_t)((j / nsb) & 1), abort_flag, p.err)) break;
             tc_fence_after();
@@ -823,15 +834,21 @@ TcConfig tc_choose(int M, int n, int products) {
     c.products = products;
     c.pieces = products == 6 ? 3 : (products == 3 ? 2 : 1);
     c.accurate = (c.pieces == 3);
-    c.persistent = !c.accurate;
+    // The 128 x 256 one-tile-per-CTA kernel wins when each tile has a long K loop
+    // and there are enough tiles to fill the SMs several times over (2D at large
+    // n); otherwise (3D: K = n is short, the epilogue dominates; mid-size 2D:
+    // few tiles) the persistent 128 x 128 kernel overlaps epilogue and products.
+    const int nk = (n + BKF - 1) / BKF;
+    const long long tiles256 = (long long)((M + BM - 1) / BM) * ((n + 255) / 256);
+    c.persistent = !c.accurate && !(nk >= 64 && tiles256 >= 4 * 152);
     // tile width: the multiple of 32 up to bn_max that wastes the fewest columns
     // (each of the two column halves is a whole number of 16-column TMEM loads)
-    const int bn_max = 128;
+    const int bn_max = (c.accurate || c.persistent) ? 128 : 256;
     int best = bn_max, best_waste = 1 << 30;
     if (n <= bn_max) {
         best = ((n + 31) / 32) * 32;
     } else {
-        for (int bn = bn_max; bn >= 64; bn -= 32) {
+        for (int bn = bn_max; bn >= (bn_max > 128 ? 128 : 64); bn -= 32) {
             const int waste = ((n + bn - 1) / bn) * bn - n;
             if (waste < best_waste) {
                 best_waste = waste;
@@ -851,9 +868,9 @@ TcConfig tc_choose(int M, int n, int products) {
     } else {
         int acc = 32;
         while (acc < c.bn) acc *= 2;
-        // two k-block accumulator buffers + the correction accumulator, rounded up
-        // to the power of two that tcgen05.alloc needs
-        c.tmem_cols = 4 * acc;
+        // two k-block accumulator buffers (+ the correction accumulator in ACCURATE
+        // mode), rounded up to the power of two that tcgen05.alloc needs
+        c.tmem_cols = c.accurate ? 4 * acc : 2 * acc;
         // the epilogue stages 8 warps x 32 rows x MAX_HALF sums in the pipeline buffers
         while (s * (int)c.stage_bytes < STAGE_BYTES_EPI && (s + 1) * (int)c.stage_bytes <= SMEM_LIMIT - 1024) ++s;
     }
