@@ -249,7 +249,7 @@ struct TcConfig {
     unsigned stage_bytes;
 };
 struct TcMaps;  // opaque holder of CUtensorMap objects (gemm_tc.cu)
-TcConfig tc_choose(int M, int n, int products);
+TcConfig tc_choose(int M, int n, int products, int nbatch);
 // a[i][j]: operand buffer i, piece j (NULL = reuse piece 0); pp[j]: pieces of P;
 // bn_slot: tile widths of the two configurations the maps serve.
 cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const float* const a[][3], int n_a,

@@ -447,9 +447,9 @@ etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q,
     // ---- tensor-core configurations ----
     if (p->use_tc) {
         const int prod0 = opt.precision == ETD_PREC_TF32 ? 1 : (opt.precision == ETD_PREC_TF32X6 ? 6 : 3);
-        p->tc[0] = tc_choose(p->M, n, prod0);
+        p->tc[0] = tc_choose(p->M, n, prod0, p->ncomp);
         if (opt.precision == ETD_PREC_TF32X3) {
-            p->tc[1] = tc_choose(p->M, n, 6);
+            p->tc[1] = tc_choose(p->M, n, 6, p->ncomp);
             p->out_slot = 1;
         } else {
             p->tc[1] = p->tc[0];

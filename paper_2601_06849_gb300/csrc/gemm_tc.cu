@@ -492,10 +492,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 //               per TMEM lane quarter, one per 64-column half); at tile end
 //               they write the sums into TMEM staging buffer 0/1 (tcgen05.st)
 //   warps 8-11  read a staging buffer (tcgen05.ld) and run the epilogue
-// TMEM: four 128-column regions, nkb k-block buffers followed by nsb staging
-// buffers: 3 + 1 when K is long (the products of one k-block take ~0.6 us at
-// bn = 128, so the MMA needs two blocks of slack ahead of the drain), 2 + 2
-// when K is short and the epilogue, not the products, sets the pace.
+// TMEM: four 128-column regions, nkb = 2 k-block buffers followed by nsb = 2
+// staging buffers (the layout code also handles 3 + 1).
 // Shared memory holds only the TMA ring (three 64 KB stages at bn = 128).
 namespace pk {
 constexpr int BN = 128;
@@ -565,7 +563,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     const uint32_t bar_st_empty = smem_u32(&s_bar[24]);
     const uint32_t bar_done = smem_u32(&s_bar[26]);
     const int nk = (p.n + BKF - 1) / BKF;
-    const int nkb = nk >= 16 ? 3 : 2;  // k-block buffers
+    const int nkb = 2;                 // k-block buffers (3 + 1 measured slower than 2 + 2)
     const int nsb = 4 - nkb;           // staging buffers
     const uint32_t staging0 = (uint32_t)nkb * pk::KB_COLS;
     const int ntiles = p.nbatch * p.tiles_m * p.tiles_n;
@@ -829,7 +827,7 @@ bool make_map(CUtensorMap* map, const float* base, int inner, long long rows, in
 
 const char* tc_last_driver_error() { return g_driver_error; }
 
-TcConfig tc_choose(int M, int n, int products) {
+TcConfig tc_choose(int M, int n, int products, int nbatch) {
     TcConfig c{};
     c.products = products;
     c.pieces = products == 6 ? 3 : (products == 3 ? 2 : 1);
@@ -839,7 +837,7 @@ TcConfig tc_choose(int M, int n, int products) {
     // n); otherwise (3D: K = n is short, the epilogue dominates; mid-size 2D:
     // few tiles) the persistent 128 x 128 kernel overlaps epilogue and products.
     const int nk = (n + BKF - 1) / BKF;
-    const long long tiles256 = (long long)((M + BM - 1) / BM) * ((n + 255) / 256);
+    const long long tiles256 = (long long)nbatch * ((M + BM - 1) / BM) * ((n + 255) / 256);
     c.persistent = !c.accurate && !(nk >= 64 && tiles256 >= 4 * 152);
     // tile width: the multiple of 32 up to bn_max that wastes the fewest columns
     // (each of the two column halves is a whole number of 16-column TMEM loads)
