@@ -143,6 +143,29 @@ etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps);
  */
 etd_status etd_transform(etd_plan* p, const void* in_dev, void* out_dev);
 
+/*
+ * Ensemble of independent problems stepped together (the batched workload of
+ * many instances with uneven grids): instance i has d[i], m[i] interior points,
+ * diffusivity kappa[i] (component 1, if any, uses opt->kappa_comp[1] when > 0),
+ * potential q[i] and time step dt[i]; pade_order and opt (reaction, precision,
+ * n_comp, stream) are shared. Instances on the same grid form one group that
+ * shares P and runs as one batched sequence of passes on a stream of its own;
+ * groups run concurrently. Time-dependent reactions are rejected. The handle is
+ * an etd_plan usable with etd_batch_step, etd_sync, etd_plan_invalidate,
+ * etd_get_plan_info, the timing calls and etd_plan_destroy.
+ */
+etd_status etd_batch_create(etd_plan** out, int count, const int* d, const int* m, const double* kappa,
+                            const double* q, const double* dt, int pade_order, const etd_options* opt);
+
+/*
+ * Advance every instance by n_steps of its own dt. u_dev[i] is instance i's
+ * device field (layout above, 16-byte aligned). Fields are gathered into each
+ * group's contiguous buffer, stepped, and scattered back, asynchronously with
+ * respect to the plan stream (it waits for every group at the end). Passing the
+ * same pointers again resumes the carried spectral states.
+ */
+etd_status etd_batch_step(etd_plan* p, void* const* u_dev, int n_steps);
+
 /* Forget the carried spectral state (after the caller changed u_dev). */
 etd_status etd_plan_invalidate(etd_plan* p);
 

@@ -205,6 +205,7 @@ template <typename T>
 struct Rx {
     int kind;        // ETD_RX_*, or -1 for "identity" (split u itself)
     int ncomp, n;
+    int ninst;       // instances; instance i's component c starts at (i * ncomp + c) * bs
     long long npts;  // n^d
     const T* in;
     int ld_in;

@@ -46,6 +46,7 @@ struct TimedLaunch {
 
 struct etd_plan {
     int d = 0, n = 0, ncomp = 1, precision = ETD_PREC_TF32X3, pade = 2, reaction = ETD_RX_ALLEN_CAHN;
+    int ninst = 1;  // instances stepped together (same d and n); batch index = instance * ncomp + comp
     double rp[8] = {0};
     double kappa[2] = {0, 0};
     double q = 0, tau = 0, t = 0;
@@ -78,6 +79,15 @@ struct etd_plan {
     bool timing = false;
     std::vector<TimedLaunch> timed;
     std::vector<cudaEvent_t> pool;
+    // ensemble container (etd_batch_create): one group plan per distinct (d, n)
+    bool is_batch = false;
+    std::vector<etd_plan*> groups;
+    std::vector<std::vector<int>> members;  // instance indices of each group
+    std::vector<void*> gfield;              // contiguous fields of each group
+    std::vector<const void*> last_ptrs;     // u_dev of the previous etd_batch_step
+    cudaEvent_t ev_start = nullptr;
+    std::vector<cudaEvent_t> ev_done;
+    long long count = 0;
 };
 
 namespace {
@@ -153,6 +163,15 @@ etd_status dalloc(etd_plan* p, void** ptr, size_t bytes) {
 }
 
 void free_plan(etd_plan* p) {
+    for (etd_plan* g : p->groups) {
+        if (g->stream) cudaStreamDestroy(g->stream);
+        free_plan(g);
+    }
+    for (void* f : p->gfield)
+        if (f) cudaFree(f);
+    if (p->ev_start) cudaEventDestroy(p->ev_start);
+    for (auto ev : p->ev_done)
+        if (ev) cudaEventDestroy(ev);
     void* bufs[] = {p->P[0],     p->P[1],     p->P[2],     p->grid,     p->uhat,     p->what,
                     p->fq,       p->wphys,    p->op[0][0], p->op[0][1], p->op[0][2], p->op[1][0],
                     p->op[1][1], p->op[1][2], p->err,      p->stats,    p->host_field};
@@ -235,17 +254,17 @@ etd_status run_pass(etd_plan* p, int cur, int slot, int mode, int out_split, voi
     e.bs_dst = bs_dst;
     TimerScope ts(p, slot == p->out_slot && p->out_slot != 0 ? 2 : 0);
     if constexpr (sizeof(T) == 8) {
-        launch_gemm_simt_f64((const double*)p->op[cur][0], (const double*)p->P[0], p->M, p->n, p->ncomp, e,
-                             p->stream);
+        launch_gemm_simt_f64((const double*)p->op[cur][0], (const double*)p->P[0], p->M, p->n, p->ninst * p->ncomp,
+                             e, p->stream);
     } else {
         if (p->use_tc) {
             cudaError_t ce =
-                launch_gemm_tc(p->tc[slot], slot, p->maps, cur, p->M, p->n, p->ncomp, e, p->err, p->stream);
+                launch_gemm_tc(p->tc[slot], slot, p->maps, cur, p->M, p->n, p->ninst * p->ncomp, e, p->err, p->stream);
             if (ce != cudaSuccess) return fail(ETD_ERR_CUDA, "tensor-core pass launch: %s", cudaGetErrorString(ce));
             return ETD_OK;
         }
-        launch_gemm_simt_f32((const float*)p->op[cur][0], (const float*)p->P[0], p->M, p->n, p->ncomp, e,
-                             p->stream);
+        launch_gemm_simt_f32((const float*)p->op[cur][0], (const float*)p->P[0], p->M, p->n, p->ninst * p->ncomp,
+                             e, p->stream);
     }
     cudaError_t ce = cudaGetLastError();
     if (ce != cudaSuccess) return fail(ETD_ERR_CUDA, "transform pass launch: %s", cudaGetErrorString(ce));
@@ -279,6 +298,7 @@ etd_status run_react(etd_plan* p, int kind, const void* in, int ld_in, long long
     }
     r.kind = kind;
     r.ncomp = p->ncomp;
+    r.ninst = p->ninst;
     r.n = p->n;
     r.npts = p->npts;
     r.in = (const T*)in;
@@ -367,21 +387,14 @@ etd_status etd_options_default(etd_options* opt) {
     return ETD_OK;
 }
 
-etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q, double dt, int pade_order,
-                           const etd_options* opt_in) {
-    if (!out) return fail(ETD_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    etd_options opt;
-    if (opt_in)
-        opt = *opt_in;
-    else
-        etd_options_default(&opt);
+}  // extern "C"
+
+namespace {
+
+etd_status validate_options(int d, int m, int pade_order, const etd_options& opt) {
     if (d != 2 && d != 3) return fail(ETD_ERR_INVALID_ARG, "d must be 2 or 3 (got %d)", d);
     const int mmax = (d == 2) ? 16384 : 1024;
     if (m < 2 || m > mmax) return fail(ETD_ERR_INVALID_ARG, "m must be in [2, %d] (got %d)", mmax, m);
-    if (!(kappa > 0) || !std::isfinite(kappa)) return fail(ETD_ERR_INVALID_ARG, "kappa must be > 0");
-    if (!(q >= 0) || !std::isfinite(q)) return fail(ETD_ERR_INVALID_ARG, "q must be >= 0");
-    if (!(dt > 0) || !std::isfinite(dt)) return fail(ETD_ERR_INVALID_ARG, "dt must be > 0");
     if (pade_order != ETD_PADE_02 && pade_order != ETD_PADE_04 && pade_order != ETD_EXACT_EXP)
         return fail(ETD_ERR_INVALID_ARG, "pade_order must be 2, 4 or 0 (exact exponential)");
     if (opt.n_comp < 1 || opt.n_comp > 2) return fail(ETD_ERR_INVALID_ARG, "n_comp must be 1 or 2");
@@ -397,24 +410,41 @@ etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q,
         return fail(ETD_ERR_INVALID_ARG, "unknown precision");
     if (opt.precision == ETD_PREC_BF16X3 || opt.precision == ETD_PREC_BF16X6)
         return fail(ETD_ERR_UNSUPPORTED, "BF16 split precisions are not built yet");
+    return ETD_OK;
+}
 
+etd_status validate_scalars(double kappa, double q, double dt) {
+    if (!(kappa > 0) || !std::isfinite(kappa)) return fail(ETD_ERR_INVALID_ARG, "kappa must be > 0");
+    if (!(q >= 0) || !std::isfinite(q)) return fail(ETD_ERR_INVALID_ARG, "q must be >= 0");
+    if (!(dt > 0) || !std::isfinite(dt)) return fail(ETD_ERR_INVALID_ARG, "dt must be > 0");
+    return ETD_OK;
+}
+
+// A plan for ninst instances on the same grid (d, n): kap[i * ncomp + c] is the
+// diffusivity of component c of instance i, qv[i] and dtv[i] its potential and
+// time step. Every (instance, component) gets its own factor grids; P is shared.
+etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap, const double* qv, const double* dtv,
+                      int pade_order, const etd_options& opt) {
+    *out = nullptr;
     etd_plan* p = new (std::nothrow) etd_plan();
     if (!p) return fail(ETD_ERR_OOM, "host allocation failed");
     p->d = d;
     p->n = m;
+    p->ninst = ninst;
     p->ncomp = opt.n_comp;
     p->precision = opt.precision;
     p->pade = pade_order;
     p->reaction = opt.reaction;
     std::memcpy(p->rp, opt.rx_params, sizeof p->rp);
-    for (int c = 0; c < p->ncomp; ++c) p->kappa[c] = (opt.kappa_comp[c] > 0) ? opt.kappa_comp[c] : kappa;
-    p->q = q;
-    p->tau = dt;
+    for (int c = 0; c < p->ncomp; ++c) p->kappa[c] = kap[c];
+    p->q = qv[0];
+    p->tau = dtv[0];
     p->stream = (cudaStream_t)opt.stream;
     p->elem = (opt.precision == ETD_PREC_FP64) ? 8 : 4;
     p->use_tc = (opt.precision == ETD_PREC_TF32 || opt.precision == ETD_PREC_TF32X3 ||
                  opt.precision == ETD_PREC_TF32X6);
     const int n = m;
+    const int nb = ninst * p->ncomp;
     p->M = (d == 2) ? n : n * n;
     p->mq = (d == 2) ? 1 : n;
     p->ld = (n + 3) / 4 * 4;
@@ -432,24 +462,27 @@ etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q,
             const long long r = ((long long)(j + 1) * (k + 1)) % period;  // reduce before sin()
             P[(size_t)j * n + k] = scale * std::sin(pi * (double)r / (double)(n + 1));
         }
-    std::vector<double> grid((size_t)p->ncomp * 3 * n);
-    for (int c = 0; c < p->ncomp; ++c)
+    std::vector<double> grid((size_t)nb * 3 * n);
+    for (int b = 0; b < nb; ++b) {
+        const int inst = b / p->ncomp;
+        const double dt = dtv[inst], q = qv[inst];
         for (int k = 0; k < n; ++k) {
             const double sk = std::sin(pi * (k + 1) / (2.0 * (n + 1)));
-            const double lam = 4.0 * p->kappa[c] / (h * h) * sk * sk + q / d;
+            const double lam = 4.0 * kap[b] / (h * h) * sk * sk + q / d;
             double e[3];
             factor_grids(pade_order, dt * lam, e);
-            grid[((size_t)c * 3 + 0) * n + k] = e[0];
-            grid[((size_t)c * 3 + 1) * n + k] = dt * e[1];
-            grid[((size_t)c * 3 + 2) * n + k] = dt * e[2];
+            grid[((size_t)b * 3 + 0) * n + k] = e[0];
+            grid[((size_t)b * 3 + 1) * n + k] = dt * e[1];
+            grid[((size_t)b * 3 + 2) * n + k] = dt * e[2];
         }
+    }
 
     // ---- tensor-core configurations ----
     if (p->use_tc) {
         const int prod0 = opt.precision == ETD_PREC_TF32 ? 1 : (opt.precision == ETD_PREC_TF32X6 ? 6 : 3);
-        p->tc[0] = tc_choose(p->M, n, prod0, p->ncomp);
+        p->tc[0] = tc_choose(p->M, n, prod0, nb);
         if (opt.precision == ETD_PREC_TF32X3) {
-            p->tc[1] = tc_choose(p->M, n, 6, p->ncomp);
+            p->tc[1] = tc_choose(p->M, n, 6, nb);
             p->out_slot = 1;
         } else {
             p->tc[1] = p->tc[0];
@@ -460,11 +493,11 @@ etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q,
     // ---- device buffers ----
     etd_status s = ETD_OK;
     const size_t E = p->elem;
-    const size_t field_bytes = (size_t)p->ncomp * p->bs * E;
-    const size_t state_bytes = (size_t)p->ncomp * p->bs * sizeof(double);
+    const size_t field_bytes = (size_t)nb * p->bs * E;
+    const size_t state_bytes = (size_t)nb * p->bs * sizeof(double);
     const size_t pbytes = (size_t)n * p->ld * E;
     for (int j = 0; j < p->pieces && s == ETD_OK; ++j) s = dalloc(p, &p->P[j], pbytes);
-    if (s == ETD_OK) s = dalloc(p, &p->grid, (size_t)p->ncomp * 3 * n * sizeof(double));
+    if (s == ETD_OK) s = dalloc(p, &p->grid, (size_t)nb * 3 * n * sizeof(double));
     if (s == ETD_OK) s = dalloc(p, &p->uhat, state_bytes);
     if (s == ETD_OK) s = dalloc(p, &p->what, state_bytes);
     if (s == ETD_OK) s = dalloc(p, &p->fq, field_bytes);
@@ -516,7 +549,7 @@ etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q,
             for (int j = 0; j < 3; ++j) a[i][j] = (const float*)p->op[i][j];
         const float* pp[3] = {(const float*)p->P[0], (const float*)p->P[1], (const float*)p->P[2]};
         const int bn_slot[2] = {p->tc[0].bn, p->tc[1].bn};
-        ce = tc_maps_create(&p->maps, p->M, n, p->ncomp, p->ld, a, 2, pp, bn_slot);
+        ce = tc_maps_create(&p->maps, p->M, n, nb, p->ld, a, 2, pp, bn_slot);
         if (ce != cudaSuccess) {
             std::string why = tc_last_driver_error();
             free_plan(p);
@@ -527,8 +560,144 @@ etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q,
     return ETD_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+etd_status etd_plan_create(etd_plan** out, int d, int m, double kappa, double q, double dt, int pade_order,
+                           const etd_options* opt_in) {
+    if (!out) return fail(ETD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    etd_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        etd_options_default(&opt);
+    etd_status s = validate_options(d, m, pade_order, opt);
+    if (s == ETD_OK) s = validate_scalars(kappa, q, dt);
+    if (s != ETD_OK) return s;
+    double kap[2];
+    for (int c = 0; c < opt.n_comp; ++c) kap[c] = (opt.kappa_comp[c] > 0) ? opt.kappa_comp[c] : kappa;
+    return build_plan(out, d, m, 1, kap, &q, &dt, pade_order, opt);
+}
+
+etd_status etd_batch_create(etd_plan** out, int count, const int* d, const int* m, const double* kappa,
+                            const double* q, const double* dt, int pade_order, const etd_options* opt_in) {
+    if (!out) return fail(ETD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !d || !m || !kappa || !q || !dt) return fail(ETD_ERR_INVALID_ARG, "empty or NULL instance arrays");
+    etd_options opt;
+    if (opt_in)
+        opt = *opt_in;
+    else
+        etd_options_default(&opt);
+    if (opt.reaction == ETD_RX_AC_FORCED)
+        return fail(ETD_ERR_INVALID_ARG, "time-dependent reactions are not supported in a batch");
+    for (int i = 0; i < count; ++i) {
+        etd_status s = validate_options(d[i], m[i], pade_order, opt);
+        if (s == ETD_OK) s = validate_scalars(kappa[i], q[i], dt[i]);
+        if (s != ETD_OK) return s;
+    }
+    etd_plan* B = new (std::nothrow) etd_plan();
+    if (!B) return fail(ETD_ERR_OOM, "host allocation failed");
+    B->is_batch = true;
+    B->count = count;
+    B->ncomp = opt.n_comp;
+    B->precision = opt.precision;
+    B->elem = (opt.precision == ETD_PREC_FP64) ? 8 : 4;
+    B->stream = (cudaStream_t)opt.stream;
+    // group the instances by grid (d, n), in order of first appearance
+    std::vector<std::pair<int, int>> keys;
+    for (int i = 0; i < count; ++i) {
+        size_t gi = 0;
+        while (gi < keys.size() && keys[gi] != std::make_pair(d[i], m[i])) ++gi;
+        if (gi == keys.size()) {
+            keys.push_back({d[i], m[i]});
+            B->members.emplace_back();
+        }
+        B->members[gi].push_back(i);
+    }
+    etd_status s = ETD_OK;
+    cudaError_t ce = cudaEventCreateWithFlags(&B->ev_start, cudaEventDisableTiming);
+    for (size_t gi = 0; gi < keys.size() && s == ETD_OK && ce == cudaSuccess; ++gi) {
+        const std::vector<int>& mem = B->members[gi];
+        const int ni = (int)mem.size();
+        std::vector<double> kap((size_t)ni * opt.n_comp), qv(ni), dtv(ni);
+        for (int li = 0; li < ni; ++li) {
+            const int i = mem[li];
+            for (int c = 0; c < opt.n_comp; ++c)
+                kap[(size_t)li * opt.n_comp + c] = (c > 0 && opt.kappa_comp[c] > 0) ? opt.kappa_comp[c] : kappa[i];
+            qv[li] = q[i];
+            dtv[li] = dt[i];
+        }
+        etd_options gopt = opt;
+        cudaStream_t gs = nullptr;
+        ce = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) break;
+        gopt.stream = gs;
+        etd_plan* g = nullptr;
+        s = build_plan(&g, keys[gi].first, keys[gi].second, ni, kap.data(), qv.data(), dtv.data(), pade_order, gopt);
+        if (s != ETD_OK) {
+            cudaStreamDestroy(gs);
+            break;
+        }
+        B->groups.push_back(g);
+        void* f = nullptr;
+        s = dalloc(B, &f, (size_t)ni * opt.n_comp * g->npts * g->elem);
+        B->gfield.push_back(f);
+        cudaEvent_t ev = nullptr;
+        if (s == ETD_OK) ce = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        B->ev_done.push_back(ev);
+    }
+    if (s == ETD_OK && ce != cudaSuccess) s = fail(ETD_ERR_CUDA, "batch streams/events: %s", cudaGetErrorString(ce));
+    if (s != ETD_OK) {
+        free_plan(B);
+        return s;
+    }
+    for (etd_plan* g : B->groups) B->workspace += g->workspace;
+    *out = B;
+    return ETD_OK;
+}
+
+etd_status etd_batch_step(etd_plan* B, void* const* u_dev, int n_steps) {
+    if (!B || !B->is_batch) return fail(ETD_ERR_INVALID_ARG, "not a batch plan (use etd_batch_create)");
+    if (!u_dev) return fail(ETD_ERR_INVALID_ARG, "u_dev is NULL");
+    if (n_steps < 0) return fail(ETD_ERR_INVALID_ARG, "n_steps must be >= 0");
+    for (long long i = 0; i < B->count; ++i) {
+        etd_status s = check_device_ptr(u_dev[i], "u_dev[i]");
+        if (s != ETD_OK) return s;
+    }
+    if (n_steps == 0) return ETD_OK;
+    // the carried spectral states stay valid only for the same fields as last time
+    bool same = B->last_ptrs.size() == (size_t)B->count;
+    for (long long i = 0; same && i < B->count; ++i) same = B->last_ptrs[i] == u_dev[i];
+    if (!same) {
+        for (etd_plan* g : B->groups) g->uhat_valid = false;
+        B->last_ptrs.assign(u_dev, u_dev + B->count);
+    }
+    ETD_CUDA(cudaEventRecord(B->ev_start, B->stream));
+    for (size_t gi = 0; gi < B->groups.size(); ++gi) {
+        etd_plan* g = B->groups[gi];
+        const size_t inst_bytes = (size_t)g->ncomp * g->npts * g->elem;
+        char* gf = static_cast<char*>(B->gfield[gi]);
+        ETD_CUDA(cudaStreamWaitEvent(g->stream, B->ev_start, 0));
+        for (size_t li = 0; li < B->members[gi].size(); ++li)
+            ETD_CUDA(cudaMemcpyAsync(gf + li * inst_bytes, u_dev[B->members[gi][li]], inst_bytes,
+                                     cudaMemcpyDeviceToDevice, g->stream));
+        etd_status s = (g->elem == 8) ? step_impl<double>(g, gf, n_steps) : step_impl<float>(g, gf, n_steps);
+        if (s != ETD_OK) return s;
+        for (size_t li = 0; li < B->members[gi].size(); ++li)
+            ETD_CUDA(cudaMemcpyAsync(u_dev[B->members[gi][li]], gf + li * inst_bytes, inst_bytes,
+                                     cudaMemcpyDeviceToDevice, g->stream));
+        ETD_CUDA(cudaEventRecord(B->ev_done[gi], g->stream));
+        ETD_CUDA(cudaStreamWaitEvent(B->stream, B->ev_done[gi], 0));
+    }
+    return ETD_OK;
+}
+
 etd_status etd_step(etd_plan* p, void* u_dev, int n_steps) {
     if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    if (p->is_batch) return fail(ETD_ERR_INVALID_ARG, "a batch plan is stepped with etd_batch_step");
     if (n_steps < 0) return fail(ETD_ERR_INVALID_ARG, "n_steps must be >= 0");
     etd_status s = check_device_ptr(u_dev, "u_dev");
     if (s != ETD_OK) return s;
@@ -538,7 +707,12 @@ etd_status etd_step(etd_plan* p, void* u_dev, int n_steps) {
 
 etd_status etd_sync(etd_plan* p) {
     if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    for (etd_plan* g : p->groups) {
+        etd_status s = etd_sync(g);
+        if (s != ETD_OK) return s;
+    }
     ETD_CUDA(cudaStreamSynchronize(p->stream));
+    if (p->is_batch) return ETD_OK;
     unsigned flags = 0;
     ETD_CUDA(cudaMemcpy(&flags, p->err, sizeof flags, cudaMemcpyDeviceToHost));
     if (flags) {
@@ -552,6 +726,7 @@ etd_status etd_sync(etd_plan* p) {
 
 etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps) {
     if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    if (p->is_batch) return fail(ETD_ERR_INVALID_ARG, "a batch plan is stepped with etd_batch_step");
     if (!u_host) return fail(ETD_ERR_INVALID_ARG, "u_host is NULL");
     if (n_steps < 0) return fail(ETD_ERR_INVALID_ARG, "n_steps must be >= 0");
     const size_t bytes = (size_t)p->ncomp * p->npts * p->elem;
@@ -570,6 +745,7 @@ etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps) {
 
 etd_status etd_transform(etd_plan* p, const void* in_dev, void* out_dev) {
     if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    if (p->is_batch) return fail(ETD_ERR_INVALID_ARG, "a batch plan is stepped with etd_batch_step");
     etd_status s = check_device_ptr(in_dev, "in_dev");
     if (s == ETD_OK) s = check_device_ptr(out_dev, "out_dev");
     if (s != ETD_OK) return s;
@@ -587,6 +763,8 @@ etd_status etd_transform(etd_plan* p, const void* in_dev, void* out_dev) {
 
 etd_status etd_plan_invalidate(etd_plan* p) {
     if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    for (etd_plan* g : p->groups) g->uhat_valid = false;
+    p->last_ptrs.clear();
     p->uhat_valid = false;
     p->uhat_src = nullptr;
     return ETD_OK;
@@ -594,6 +772,7 @@ etd_status etd_plan_invalidate(etd_plan* p) {
 
 etd_status etd_set_time(etd_plan* p, double t) {
     if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    if (p->is_batch) return fail(ETD_ERR_INVALID_ARG, "a batch plan is stepped with etd_batch_step");
     if (!std::isfinite(t)) return fail(ETD_ERR_INVALID_ARG, "t must be finite");
     p->t = t;
     return ETD_OK;
@@ -601,6 +780,7 @@ etd_status etd_set_time(etd_plan* p, double t) {
 
 etd_status etd_field_stats(etd_plan* p, const void* u_dev, double* max_abs, long long* n_nonfinite) {
     if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    if (p->is_batch) return fail(ETD_ERR_INVALID_ARG, "a batch plan is stepped with etd_batch_step");
     if (!max_abs || !n_nonfinite) return fail(ETD_ERR_INVALID_ARG, "output pointer is NULL");
     etd_status s = check_device_ptr(u_dev, "u_dev");
     if (s != ETD_OK) return s;
@@ -623,14 +803,31 @@ etd_status etd_field_stats(etd_plan* p, const void* u_dev, double* max_abs, long
 etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
     if (!p || !info) return fail(ETD_ERR_INVALID_ARG, "NULL argument");
     std::memset(info, 0, sizeof(*info));
+    if (p->is_batch) {
+        for (const etd_plan* g : p->groups) {
+            etd_plan_info gi;
+            etd_get_plan_info(g, &gi);
+            info->unknowns += gi.unknowns;
+            info->gemm_flops += gi.gemm_flops;
+            info->step_flops += gi.step_flops;
+            info->products = gi.products;
+            info->gemms_per_step = gi.gemms_per_step;
+            info->d = gi.d;
+        }
+        info->n = 0;  // several grids
+        info->n_comp = p->ncomp;
+        info->precision = p->precision;
+        info->workspace_bytes = p->workspace;
+        return ETD_OK;
+    }
     info->d = p->d;
     info->n = p->n;
     info->n_comp = p->ncomp;
     info->precision = p->precision;
     info->products = p->use_tc ? p->tc[0].products : 0;
     info->gemms_per_step = 4 * p->d;
-    info->unknowns = (long long)p->ncomp * p->npts;
-    info->gemm_flops = 2.0 * (double)p->npts * (double)p->n * p->ncomp;
+    info->unknowns = (long long)p->ninst * p->ncomp * p->npts;
+    info->gemm_flops = 2.0 * (double)p->npts * (double)p->n * p->ncomp * p->ninst;
     info->step_flops = info->gemm_flops * info->gemms_per_step;
     info->workspace_bytes = p->workspace;
     return ETD_OK;
@@ -638,6 +835,7 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
 
 etd_status etd_set_timing(etd_plan* p, int enable) {
     if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    for (etd_plan* g : p->groups) g->timing = enable != 0;
     p->timing = enable != 0;
     return ETD_OK;
 }
@@ -647,6 +845,14 @@ etd_status etd_kernel_times(etd_plan* p, int kind, double* total_ms, long long* 
     ETD_CUDA(cudaStreamSynchronize(p->stream));
     double ms = 0;
     long long cnt = 0;
+    for (etd_plan* g : p->groups) {
+        double gm = 0;
+        long long gc = 0;
+        etd_status s = etd_kernel_times(g, kind, &gm, &gc);
+        if (s != ETD_OK) return s;
+        ms += gm;
+        cnt += gc;
+    }
     std::vector<TimedLaunch> keep;
     for (auto& tl : p->timed) {
         if (tl.kind == kind) {
@@ -668,6 +874,7 @@ etd_status etd_kernel_times(etd_plan* p, int kind, double* total_ms, long long* 
 
 etd_status etd_plan_destroy(etd_plan* p) {
     if (!p) return ETD_OK;
+    for (etd_plan* g : p->groups) cudaStreamSynchronize(g->stream);
     cudaStreamSynchronize(p->stream);
     free_plan(p);
     return ETD_OK;

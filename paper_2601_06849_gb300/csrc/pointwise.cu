@@ -38,11 +38,14 @@ __device__ __forceinline__ void store_split(T* hi, T* lo, T* lo2, long long o, T
 template <typename T>
 __global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < r.npts; p += stride) {
+    const long long total = r.npts * r.ninst;
+    for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < total; pt += stride) {
+        const long long inst = pt / r.npts;
+        const long long p = pt - inst * r.npts;
         const long long row = p / r.n;
         const int x = (int)(p - row * r.n);
-        const long long oi = row * r.ld_in + x;
-        const long long oo = row * r.ld_out + x;
+        const long long oi = inst * r.ncomp * r.bs_in + row * r.ld_in + x;
+        const long long oo = inst * r.ncomp * r.bs_out + row * r.ld_out + x;
         switch (r.kind) {
             case ETD_RX_FHN: {
                 // f_u = u - c3 u^3 - v,  f_v = eps (u - a v - b)
@@ -98,10 +101,10 @@ static int grid_for(long long work, int threads) {
 }
 
 void launch_react_f32(const Rx<float>& r, cudaStream_t st) {
-    react_kernel<float><<<grid_for(r.npts, 256), 256, 0, st>>>(r);
+    react_kernel<float><<<grid_for(r.npts * r.ninst, 256), 256, 0, st>>>(r);
 }
 void launch_react_f64(const Rx<double>& r, cudaStream_t st) {
-    react_kernel<double><<<grid_for(r.npts, 256), 256, 0, st>>>(r);
+    react_kernel<double><<<grid_for(r.npts * r.ninst, 256), 256, 0, st>>>(r);
 }
 
 // acc[0] = max |u| (as the bit pattern of a non-negative double, so an

@@ -27,7 +27,7 @@ SYMBOLS = (
     "etd_options_default", "etd_plan_create", "etd_step", "etd_step_host", "etd_transform",
     "etd_plan_invalidate", "etd_set_time", "etd_sync", "etd_field_stats", "etd_get_plan_info",
     "etd_set_timing", "etd_kernel_times", "etd_plan_destroy", "etd_status_string", "etd_last_error",
-    "etd_transform_noalloc",
+    "etd_transform_noalloc", "etd_batch_create", "etd_batch_step",
 )
 ETD_NOALLOC_MAX_ELEMS = 4194304
 
@@ -91,6 +91,9 @@ def lib():
             "etd_status_string": ([i], ctypes.c_char_p),
             "etd_last_error": ([], ctypes.c_char_p),
             "etd_transform_noalloc": ([i, i, i, vp, vp, vp], i),
+            "etd_batch_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d),
+                                  ctypes.POINTER(d), ctypes.POINTER(d), i, ctypes.POINTER(etd_options)], i),
+            "etd_batch_step": ([vp, ctypes.POINTER(vp), i], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -179,11 +182,90 @@ def etd_transform_noalloc(d: int, n: int, n_comp: int, in_dev: int, out_dev: int
     _check(lib().etd_transform_noalloc(d, n, n_comp, in_dev, out_dev, stream))
 
 
+def etd_batch_create(d, m, kappa, q, dt, pade_order: int, opt: Optional[etd_options] = None) -> int:
+    count = len(m)
+    arr = lambda T, xs: (T * count)(*xs)
+    h = ctypes.c_void_p()
+    _check(lib().etd_batch_create(ctypes.byref(h), count, arr(ctypes.c_int, d), arr(ctypes.c_int, m),
+                                  arr(ctypes.c_double, kappa), arr(ctypes.c_double, q), arr(ctypes.c_double, dt),
+                                  pade_order, ctypes.byref(opt) if opt is not None else None))
+    return h.value
+
+
+def etd_batch_step(plan: int, u_dev_ptrs, n_steps: int) -> None:
+    ptrs = (ctypes.c_void_p * len(u_dev_ptrs))(*u_dev_ptrs)
+    _check(lib().etd_batch_step(plan, ptrs, n_steps))
+
+
 def etd_plan_destroy(plan: int) -> None:
     _check(lib().etd_plan_destroy(plan))
 
 
-# ---- torch-facing wrapper -----------------------------------------------------
+# ---- torch-facing wrappers ----------------------------------------------------
+
+class Batch:
+    """An ensemble of independent problems (one etd_batch_create handle).
+
+    ``n``, ``kappa``, ``q``, ``dt`` are per-instance sequences; the reaction,
+    precision, Pade order and component count are shared."""
+
+    def __init__(self, d, n, kappa, q, dt, pade=2, precision="tf32x3", reaction="fhn", rx_params=(), n_comp=2,
+                 kappa_v=None, stream=None):
+        import torch
+
+        count = len(n)
+        d = [d] * count if isinstance(d, int) else list(d)
+        self.n, self.d, self.n_comp = list(n), d, n_comp
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        opt = etd_options_default()
+        opt.precision = PRECISION[precision]
+        opt.reaction = REACTION[reaction]
+        for i, v in enumerate(rx_params):
+            opt.rx_params[i] = float(v)
+        opt.n_comp = n_comp
+        if kappa_v is not None:
+            opt.kappa_comp[1] = float(kappa_v)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        opt.stream = ctypes.c_void_p(stream.cuda_stream)
+        self.handle = etd_batch_create(d, self.n, kappa, q, dt, FAMILY[pade], opt)
+
+    def step(self, fields, n_steps: int = 1):
+        for i, u in enumerate(fields):
+            shape = (self.n_comp,) + (self.n[i],) * self.d[i]
+            if not u.is_cuda or u.dtype != self.dtype or tuple(u.shape) != shape or not u.is_contiguous():
+                raise EtdError(ETD_ERR_INVALID_ARG, f"field {i} must be a contiguous {self.dtype} CUDA tensor {shape}")
+        etd_batch_step(self.handle, [u.data_ptr() for u in fields], n_steps)
+        return fields
+
+    def sync(self):
+        etd_sync(self.handle)
+
+    def invalidate(self):
+        etd_plan_invalidate(self.handle)
+
+    def info(self) -> etd_plan_info:
+        return etd_get_plan_info(self.handle)
+
+    def set_timing(self, enable: bool):
+        etd_set_timing(self.handle, enable)
+
+    def kernel_times(self, kind: int):
+        return etd_kernel_times(self.handle, kind)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            etd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 
 class Plan:
     """One ETD2RK-DS problem on (0,1)^d with n interior points per axis.
