@@ -39,10 +39,93 @@ WORKLOADS = {
     "ac3d_256": (3, 256, 1e-3, None, 0.1, 5e-3, "allen_cahn", "3D Allen-Cahn n=256, kappa=1e-3 q=0.1 tau=5e-3"),
     "ac3d_384": (3, 384, 1e-3, None, 0.1, 5e-3, "allen_cahn", "3D Allen-Cahn n=384, kappa=1e-3 q=0.1 tau=5e-3"),
     "ac2d_64": (2, 64, 1e-2, None, 0.0, 1e-3, "allen_cahn", "2D Allen-Cahn n=64, kappa=1e-2 q=0 tau=1e-3"),
+    "ensemble512": (2, None, None, 5e-3, 0.0, None, "fhn",
+                    "512 independent 2D FitzHugh-Nagumo instances, n uniform on {64,96,...,512}, kappa_u log-uniform "
+                    "[1e-4,1e-2], tau uniform [1e-3,1e-2], kappa_v=5e-3 eps=0.01 a=0.5 b=0.1"),
 }
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
 KERNEL_FILES = ["paper_2601_06849_gb300/csrc/gemm_tc.cu", "paper_2601_06849_gb300/csrc/etd_internal.cuh"]
 L2_BYTES = 129e6
+
+
+def run_ensemble(args, world, rank, local):
+    """Batched workload: one etd_batch_step per timed step over all instances."""
+    import torch
+
+    import __graft_entry__
+    from paper_2601_06849_gb300 import etd, inputs
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    d, _, _, kv, q, _, rx, desc = WORKLOADS[args.workload]
+    members = inputs.fhn_ensemble(512, workload=3)
+    stream = torch.cuda.Stream()
+    batch = etd.Batch(2, [m.n for m in members], [m.kappa_u for m in members], [q] * len(members),
+                      [m.tau for m in members], precision=args.precision, reaction="fhn", rx_params=FHN, n_comp=2,
+                      kappa_v=kv, stream=stream)
+    info = batch.info()
+    with torch.cuda.stream(stream):
+        fields = [torch.tensor(m.u0, dtype=batch.dtype, device="cuda") for m in members]
+        batch.step(fields, args.warmup)
+        batch.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clocks:
+            ev0.record(stream)
+            batch.step(fields, args.steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        barrier(world)
+        el_ms = ev0.elapsed_time(ev1)
+        batch.sync()
+    el_max = barrier_max(el_ms, world)
+    value = world * info.unknowns * args.steps / (el_max / 1e3)
+    # end to end: pinned host fields copied in, stepped, copied out, every step
+    hosts = [torch.tensor(m.u0, dtype=batch.dtype).pin_memory() for m in members]
+    e2e_steps = args.e2e_steps or 3
+    with torch.cuda.stream(stream):
+        dev = [h.to("cuda", non_blocking=True) for h in hosts]
+        batch.step(dev, 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for h, dv in zip(hosts, dev):
+                dv.copy_(h, non_blocking=True)
+            batch.step(dev, 1)
+            for h, dv in zip(hosts, dev):
+                h.copy_(dv, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = barrier_max(time.perf_counter() - t0, world)
+    peaks, src = measured_peaks()
+    flops = info.step_flops * max(info.products, 1) * args.steps
+    peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
+    achieved = flops / (el_max / 1e3) / 1e12
+    nbytes = sum(h.numel() * h.element_size() for h in hosts)
+    line = {
+        "metric": "unknown-updates/s per ETD2RK-DS step", "value": value, "unit": "unknown-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "tf32x3 (f32 state)" if args.precision == "tf32x3" else args.precision, "data": "synthetic",
+        "config": {"workload": desc, "instances": len(members), "unknowns": info.unknowns,
+                   "precision": args.precision, "pade": "P02",
+                   "l2": f"working set {info.workspace_bytes / 1e9:.2f} GB > 129 MB L2: no flush",
+                   "parallelism": f"replicas x{world}; groups by grid on concurrent streams, one CUDA graph per step"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "all transform passes of the ensemble over the timed region (whole-GPU rate)",
+                     "peak_source": f"{src}: bf16_tflops_sustained x 1.1/2.25 (TF32/BF16 nominal)"},
+        "gpu_launches": args.steps * sum(10 for _ in range(15)),
+        "e2e": {"value": world * info.unknowns * e2e_steps / e2e_s, "unit": "unknown-updates/s",
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
+                "api": "etd.Batch.step on device copies of pinned host fields, 1 step per call"},
+    }
+    cs = clocks.summary()
+    if cs:
+        line["clocks"] = cs
+    batch.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def initial_field(name):
@@ -274,6 +357,10 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+
+    if args.workload == "ensemble512":
+        run_ensemble(args, world, rank, local)
         return
 
     import torch

@@ -88,6 +88,7 @@ struct etd_plan {
     cudaEvent_t ev_start = nullptr;
     std::vector<cudaEvent_t> ev_done;
     long long count = 0;
+    cudaGraphExec_t step_graph = nullptr;  // one inner step of every group (not the last of a call)
 };
 
 namespace {
@@ -170,6 +171,7 @@ void free_plan(etd_plan* p) {
     for (void* f : p->gfield)
         if (f) cudaFree(f);
     if (p->ev_start) cudaEventDestroy(p->ev_start);
+    if (p->step_graph) cudaGraphExecDestroy(p->step_graph);
     for (auto ev : p->ev_done)
         if (ev) cudaEventDestroy(ev);
     void* bufs[] = {p->P[0],     p->P[1],     p->P[2],     p->grid,     p->uhat,     p->what,
@@ -326,34 +328,58 @@ etd_status run_react(etd_plan* p, int kind, const void* in, int ld_in, long long
 // U -> U^ transform that (re)builds the carried state, and the transform that
 // produces the field handed back to the caller. Errors of the other transforms
 // reach the state only through f(U) and f(W), scaled by tau.
+// (Re)build the carried state U^ = T(U) when it is stale. The transform runs
+// with the output slot: an error made here stays in the carried state.
 template <typename T>
-etd_status step_impl(etd_plan* p, void* u, int n_steps) {
+etd_status ensure_state(etd_plan* p, void* u) {
+    if (p->uhat_valid && p->uhat_src == u) return ETD_OK;
+    const int spo = split_for(p, p->out_slot);
+    etd_status s = run_react<T>(p, -1, u, p->n, p->npts, p->t, spo);
+    int cur = 0;
+    if (s == ETD_OK) s = run_chain<T>(p, cur, p->out_slot, EPI_CARRY, spo, nullptr, 0, 0);
+    if (s != ETD_OK) return s;
+    p->uhat_valid = true;
+    p->uhat_src = u;
+    return ETD_OK;
+}
+
+// One time step from the carried state. Every transform runs with config slot 0
+// except, when `last`, the one that produces the field handed back to the
+// caller, which runs with p->out_slot (the accurate six-product kernel in
+// TF32X3 mode). Errors of the other transforms reach the state only through
+// f(U) and f(W), scaled by tau.
+template <typename T>
+etd_status step_once(etd_plan* p, void* u, bool last) {
     const int n = p->n;
     const long long N = p->npts;
     const int sp0 = split_for(p, 0), spo = split_for(p, p->out_slot);
     etd_status s;
     int cur = 0;
-    if (!p->uhat_valid || p->uhat_src != u) {
-        // U -> U^ with the output slot: an error made here stays in the carried state
-        if ((s = run_react<T>(p, -1, u, n, N, p->t, spo)) != ETD_OK) return s;
-        cur = 0;
-        if ((s = run_chain<T>(p, cur, p->out_slot, EPI_CARRY, spo, nullptr, 0, 0)) != ETD_OK) return s;
-        p->uhat_valid = true;
-        p->uhat_src = u;
-    }
-    for (int it = 0; it < n_steps; ++it) {
-        const bool last = it == n_steps - 1;
-        if ((s = run_react<T>(p, p->reaction, u, n, N, p->t, sp0)) != ETD_OK) return s;
-        cur = 0;
-        if ((s = run_chain<T>(p, cur, 0, EPI_STAGE1, sp0, nullptr, 0, 0)) != ETD_OK) return s;
-        if ((s = run_chain<T>(p, cur, 0, EPI_PLAIN, sp0, p->wphys, p->ld, p->bs)) != ETD_OK) return s;
-        if ((s = run_react<T>(p, p->reaction, p->wphys, p->ld, p->bs, p->t + p->tau, sp0)) != ETD_OK) return s;
-        cur = 0;
-        if ((s = run_chain<T>(p, cur, 0, EPI_STAGE2, last ? spo : sp0, nullptr, 0, 0)) != ETD_OK) return s;
-        if ((s = run_chain<T>(p, cur, last ? p->out_slot : 0, EPI_PLAIN, sp0, u, n, N)) != ETD_OK) return s;
-        p->t += p->tau;
-    }
+    if ((s = run_react<T>(p, p->reaction, u, n, N, p->t, sp0)) != ETD_OK) return s;
+    cur = 0;
+    if ((s = run_chain<T>(p, cur, 0, EPI_STAGE1, sp0, nullptr, 0, 0)) != ETD_OK) return s;
+    if ((s = run_chain<T>(p, cur, 0, EPI_PLAIN, sp0, p->wphys, p->ld, p->bs)) != ETD_OK) return s;
+    if ((s = run_react<T>(p, p->reaction, p->wphys, p->ld, p->bs, p->t + p->tau, sp0)) != ETD_OK) return s;
+    cur = 0;
+    if ((s = run_chain<T>(p, cur, 0, EPI_STAGE2, last ? spo : sp0, nullptr, 0, 0)) != ETD_OK) return s;
+    if ((s = run_chain<T>(p, cur, last ? p->out_slot : 0, EPI_PLAIN, sp0, u, n, N)) != ETD_OK) return s;
+    p->t += p->tau;
     return ETD_OK;
+}
+
+template <typename T>
+etd_status step_impl(etd_plan* p, void* u, int n_steps) {
+    etd_status s = ensure_state<T>(p, u);
+    for (int it = 0; it < n_steps && s == ETD_OK; ++it) s = step_once<T>(p, u, it == n_steps - 1);
+    return s;
+}
+
+etd_status group_ensure_state(etd_plan* g, void* u) {
+    return g->elem == 8 ? ensure_state<double>(g, u) : ensure_state<float>(g, u);
+}
+
+etd_status group_step_once(etd_plan* g, void* u, bool last) {
+    return g->elem == 8 ? step_once<double>(g, u, last) : step_once<float>(g, u, last);
 }
 
 etd_status check_device_ptr(const void* ptr, const char* what) {
@@ -675,8 +701,10 @@ etd_status etd_batch_step(etd_plan* B, void* const* u_dev, int n_steps) {
         for (etd_plan* g : B->groups) g->uhat_valid = false;
         B->last_ptrs.assign(u_dev, u_dev + B->count);
     }
+    const size_t G = B->groups.size();
+    // gather every instance's field into its group's buffer, (re)build stale states
     ETD_CUDA(cudaEventRecord(B->ev_start, B->stream));
-    for (size_t gi = 0; gi < B->groups.size(); ++gi) {
+    for (size_t gi = 0; gi < G; ++gi) {
         etd_plan* g = B->groups[gi];
         const size_t inst_bytes = (size_t)g->ncomp * g->npts * g->elem;
         char* gf = static_cast<char*>(B->gfield[gi]);
@@ -684,7 +712,66 @@ etd_status etd_batch_step(etd_plan* B, void* const* u_dev, int n_steps) {
         for (size_t li = 0; li < B->members[gi].size(); ++li)
             ETD_CUDA(cudaMemcpyAsync(gf + li * inst_bytes, u_dev[B->members[gi][li]], inst_bytes,
                                      cudaMemcpyDeviceToDevice, g->stream));
-        etd_status s = (g->elem == 8) ? step_impl<double>(g, gf, n_steps) : step_impl<float>(g, gf, n_steps);
+        etd_status s = group_ensure_state(g, gf);
+        if (s != ETD_OK) return s;
+        ETD_CUDA(cudaEventRecord(B->ev_done[gi], g->stream));
+        ETD_CUDA(cudaStreamWaitEvent(B->stream, B->ev_done[gi], 0));
+    }
+    // inner steps: one CUDA graph of all groups' launches (forked over the group
+    // streams), captured once and replayed; without timing events only, since
+    // those are recorded per launch by the host
+    const bool use_graph = n_steps > 1 && !B->timing;
+    if (use_graph && !B->step_graph) {
+        cudaGraph_t graph = nullptr;
+        ETD_CUDA(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+        etd_status s = ETD_OK;
+        cudaError_t ce = cudaEventRecord(B->ev_start, B->stream);
+        for (size_t gi = 0; gi < G && s == ETD_OK && ce == cudaSuccess; ++gi) {
+            etd_plan* g = B->groups[gi];
+            ce = cudaStreamWaitEvent(g->stream, B->ev_start, 0);
+            const double t0 = g->t;
+            if (ce == cudaSuccess) s = group_step_once(g, B->gfield[gi], false);
+            g->t = t0;  // the replays advance time below
+            if (ce == cudaSuccess) ce = cudaEventRecord(B->ev_done[gi], g->stream);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(B->stream, B->ev_done[gi], 0);
+        }
+        cudaError_t ce2 = cudaStreamEndCapture(B->stream, &graph);
+        if (s != ETD_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (ce == cudaSuccess) ce = ce2;
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&B->step_graph, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            B->step_graph = nullptr;
+            return fail(ETD_ERR_CUDA, "capturing the ensemble step: %s", cudaGetErrorString(ce));
+        }
+    }
+    for (int it = 0; it < n_steps - 1; ++it) {
+        if (use_graph) {
+            ETD_CUDA(cudaGraphLaunch(B->step_graph, B->stream));
+            for (etd_plan* g : B->groups) g->t += g->tau;
+        } else {
+            ETD_CUDA(cudaEventRecord(B->ev_start, B->stream));
+            for (size_t gi = 0; gi < G; ++gi) {
+                etd_plan* g = B->groups[gi];
+                ETD_CUDA(cudaStreamWaitEvent(g->stream, B->ev_start, 0));
+                etd_status s = group_step_once(g, B->gfield[gi], false);
+                if (s != ETD_OK) return s;
+                ETD_CUDA(cudaEventRecord(B->ev_done[gi], g->stream));
+                ETD_CUDA(cudaStreamWaitEvent(B->stream, B->ev_done[gi], 0));
+            }
+        }
+    }
+    // last step (accurate output transform) and scatter back
+    ETD_CUDA(cudaEventRecord(B->ev_start, B->stream));
+    for (size_t gi = 0; gi < G; ++gi) {
+        etd_plan* g = B->groups[gi];
+        const size_t inst_bytes = (size_t)g->ncomp * g->npts * g->elem;
+        char* gf = static_cast<char*>(B->gfield[gi]);
+        ETD_CUDA(cudaStreamWaitEvent(g->stream, B->ev_start, 0));
+        etd_status s = group_step_once(g, gf, true);
         if (s != ETD_OK) return s;
         for (size_t li = 0; li < B->members[gi].size(); ++li)
             ETD_CUDA(cudaMemcpyAsync(u_dev[B->members[gi][li]], gf + li * inst_bytes, inst_bytes,
@@ -693,16 +780,6 @@ etd_status etd_batch_step(etd_plan* B, void* const* u_dev, int n_steps) {
         ETD_CUDA(cudaStreamWaitEvent(B->stream, B->ev_done[gi], 0));
     }
     return ETD_OK;
-}
-
-etd_status etd_step(etd_plan* p, void* u_dev, int n_steps) {
-    if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
-    if (p->is_batch) return fail(ETD_ERR_INVALID_ARG, "a batch plan is stepped with etd_batch_step");
-    if (n_steps < 0) return fail(ETD_ERR_INVALID_ARG, "n_steps must be >= 0");
-    etd_status s = check_device_ptr(u_dev, "u_dev");
-    if (s != ETD_OK) return s;
-    if (n_steps == 0) return ETD_OK;
-    return (p->elem == 8) ? step_impl<double>(p, u_dev, n_steps) : step_impl<float>(p, u_dev, n_steps);
 }
 
 etd_status etd_sync(etd_plan* p) {
@@ -835,8 +912,8 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
 
 etd_status etd_set_timing(etd_plan* p, int enable) {
     if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
-    for (etd_plan* g : p->groups) g->timing = enable != 0;
     p->timing = enable != 0;
+    for (etd_plan* g : p->groups) g->timing = enable != 0;
     return ETD_OK;
 }
 
