@@ -782,6 +782,16 @@ etd_status etd_batch_step(etd_plan* B, void* const* u_dev, int n_steps) {
     return ETD_OK;
 }
 
+etd_status etd_step(etd_plan* p, void* u_dev, int n_steps) {
+    if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    if (p->is_batch) return fail(ETD_ERR_INVALID_ARG, "a batch plan is stepped with etd_batch_step");
+    if (n_steps < 0) return fail(ETD_ERR_INVALID_ARG, "n_steps must be >= 0");
+    etd_status s = check_device_ptr(u_dev, "u_dev");
+    if (s != ETD_OK) return s;
+    if (n_steps == 0) return ETD_OK;
+    return (p->elem == 8) ? step_impl<double>(p, u_dev, n_steps) : step_impl<float>(p, u_dev, n_steps);
+}
+
 etd_status etd_sync(etd_plan* p) {
     if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
     for (etd_plan* g : p->groups) {
