@@ -89,6 +89,7 @@ struct etd_plan {
     std::vector<cudaEvent_t> ev_done;
     long long count = 0;
     cudaGraphExec_t step_graph = nullptr;  // one inner step of every group (not the last of a call)
+    cudaStream_t cap_stream = nullptr;      // capture origin (the caller's stream may be the legacy one)
 };
 
 namespace {
@@ -172,6 +173,7 @@ void free_plan(etd_plan* p) {
         if (f) cudaFree(f);
     if (p->ev_start) cudaEventDestroy(p->ev_start);
     if (p->step_graph) cudaGraphExecDestroy(p->step_graph);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (auto ev : p->ev_done)
         if (ev) cudaEventDestroy(ev);
     void* bufs[] = {p->P[0],     p->P[1],     p->P[2],     p->grid,     p->uhat,     p->what,
@@ -723,9 +725,10 @@ etd_status etd_batch_step(etd_plan* B, void* const* u_dev, int n_steps) {
     const bool use_graph = n_steps > 1 && !B->timing;
     if (use_graph && !B->step_graph) {
         cudaGraph_t graph = nullptr;
-        ETD_CUDA(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
+        if (!B->cap_stream) ETD_CUDA(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
+        ETD_CUDA(cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal));
         etd_status s = ETD_OK;
-        cudaError_t ce = cudaEventRecord(B->ev_start, B->stream);
+        cudaError_t ce = cudaEventRecord(B->ev_start, B->cap_stream);
         for (size_t gi = 0; gi < G && s == ETD_OK && ce == cudaSuccess; ++gi) {
             etd_plan* g = B->groups[gi];
             ce = cudaStreamWaitEvent(g->stream, B->ev_start, 0);
@@ -733,9 +736,9 @@ etd_status etd_batch_step(etd_plan* B, void* const* u_dev, int n_steps) {
             if (ce == cudaSuccess) s = group_step_once(g, B->gfield[gi], false);
             g->t = t0;  // the replays advance time below
             if (ce == cudaSuccess) ce = cudaEventRecord(B->ev_done[gi], g->stream);
-            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(B->stream, B->ev_done[gi], 0);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(B->cap_stream, B->ev_done[gi], 0);
         }
-        cudaError_t ce2 = cudaStreamEndCapture(B->stream, &graph);
+        cudaError_t ce2 = cudaStreamEndCapture(B->cap_stream, &graph);
         if (s != ETD_OK) {
             if (graph) cudaGraphDestroy(graph);
             return s;
