@@ -166,6 +166,22 @@ etd_status etd_batch_create(etd_plan** out, int count, const int* d, const int* 
  */
 etd_status etd_batch_step(etd_plan* p, void* const* u_dev, int n_steps);
 
+/*
+ * Adjoint (reverse-mode derivative) of n_steps time steps of a single plan.
+ * The forward window starts from u_ckpt (device field, the state at its first
+ * step). On entry lambda_dev holds dL/dU at the end of the window; on exit it
+ * holds dL/dU at u_ckpt. dL/dkappa_c (c < n_comp) is ADDED to grad_kappa[c] and
+ * dL/d rx_params[i] (i < 4; FitzHugh-Nagumo: c3, eps, a, b; linear: c;
+ * singular: rho) to grad_rx[i]; either pointer may be NULL. The window's
+ * forward states are recomputed on the device (memory: n_steps fields).
+ * Per step (S = E_1(tau A_2), X_l = E_l(tau A_1), all symmetric and commuting):
+ *   Gbar = tau X3 Ubar+, Wbar = Ubar+ + J_f(W)^T Gbar,
+ *   Fbar = tau X2 S Wbar - S Gbar, Ubar = X1 S Wbar + J_f(U)^T Fbar.
+ * Synchronises. Autonomous reactions only (ETD_RX_AC_FORCED: UNSUPPORTED).
+ */
+etd_status etd_step_adjoint(etd_plan* p, const void* u_ckpt, void* lambda_dev, int n_steps, double* grad_kappa,
+                            double* grad_rx);
+
 /* Forget the carried spectral state (after the caller changed u_dev). */
 etd_status etd_plan_invalidate(etd_plan* p);
 

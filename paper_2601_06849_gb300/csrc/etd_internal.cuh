@@ -226,6 +226,66 @@ struct Rx {
 // Record the message etd_last_error() returns on this host thread (etd_plan.cu).
 void set_last_error(const char* msg);
 
+// ---- adjoint step (adjoint.cu) ----
+// out = alpha * Xa * [S] * in1 + beta * Xb * [S] * in2 over the spectral grid,
+// X* selected from {1, E1, tau E2, tau E3} at the x mode, S = E1 at the other modes.
+template <typename T>
+struct SpecCombine {
+    int ncomp, d, n;
+    long long npts;
+    const double* grid;
+    const T* in1;
+    int xsel1, s1;
+    double alpha;
+    const T* in2;
+    int xsel2, s2;
+    double beta;
+    T* out;
+};
+template <typename T>
+struct ReactVjp {  // out = base + J_f(X)^T V
+    int kind, ncomp;
+    long long npts;
+    double rp[4];
+    const T* X;
+    const T* V;
+    const T* base;
+    T* out;
+};
+template <typename T>
+struct GradKappa {
+    int ncomp, d, n;
+    long long npts;
+    const double* grid;
+    const double* dgrid;  // kappa derivatives of E1, tau E2, tau E3
+    const T* Lh;          // U+bar^
+    const T* Gbh;         // Gbar^
+    const T* Wbh;         // Wbar^
+    const T* Uh;          // U^
+    const T* Fh;          // F^
+    const T* FWh;         // F_W^
+    double* out;          // [ncomp], accumulated
+};
+template <typename T>
+struct GradRx {
+    int kind, ncomp;
+    long long npts;
+    double rp[4];
+    const T* U;
+    const T* W;
+    const T* Gb;
+    const T* Fb;
+    double* out;  // [4], accumulated
+};
+template <typename T>
+void launch_spec_combine(const SpecCombine<T>& a, cudaStream_t st);
+template <typename T>
+void launch_react_vjp(const ReactVjp<T>& a, cudaStream_t st);
+template <typename T>
+void launch_grad_kappa(const GradKappa<T>& a, cudaStream_t st);
+template <typename T>
+void launch_grad_rx(const GradRx<T>& a, cudaStream_t st);
+
 // ---- launchers (defined in the .cu files) ----
 void launch_gemm_simt_f32(const float* A, const float* P, int M, int n, int nbatch, const Epi<float>& e,
                           cudaStream_t st);

@@ -89,6 +89,11 @@ struct etd_plan {
     std::vector<cudaEvent_t> ev_done;
     long long count = 0;
     cudaGraphExec_t step_graph = nullptr;  // one inner step of every group (not the last of a call)
+    // adjoint workspace (etd_step_adjoint), allocated on first use
+    std::vector<void*> adj_traj;  // forward states of the window being differentiated
+    void* adj_work[14] = {nullptr};
+    double* adj_dgrid = nullptr;  // kappa derivatives of E1, tau E2, tau E3 per component
+    double* adj_acc = nullptr;    // [2] kappa gradients, [4] reaction-parameter gradients
     cudaStream_t cap_stream = nullptr;      // capture origin (the caller's stream may be the legacy one)
 };
 
@@ -173,6 +178,12 @@ void free_plan(etd_plan* p) {
         if (f) cudaFree(f);
     if (p->ev_start) cudaEventDestroy(p->ev_start);
     if (p->step_graph) cudaGraphExecDestroy(p->step_graph);
+    for (void* f : p->adj_traj)
+        if (f) cudaFree(f);
+    for (void* f : p->adj_work)
+        if (f) cudaFree(f);
+    if (p->adj_dgrid) cudaFree(p->adj_dgrid);
+    if (p->adj_acc) cudaFree(p->adj_acc);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (auto ev : p->ev_done)
         if (ev) cudaEventDestroy(ev);
@@ -382,6 +393,173 @@ etd_status group_ensure_state(etd_plan* g, void* u) {
 
 etd_status group_step_once(etd_plan* g, void* u, bool last) {
     return g->elem == 8 ? step_once<double>(g, u, last) : step_once<float>(g, u, last);
+}
+
+// d E_l / dx of the factor family at x >= 0 (for the kappa gradients).
+void factor_grid_derivs(int family, double x, double* de) {
+    if (family == ETD_PADE_02 || family == ETD_PADE_04) {
+        double D, dD, N[3], dN[3];
+        if (family == ETD_PADE_02) {
+            D = x * x + 2 * x + 2;
+            dD = 2 * x + 2;
+            N[0] = 2; N[1] = x + 2; N[2] = x + 1;
+            dN[0] = 0; dN[1] = 1; dN[2] = 1;
+        } else {
+            D = (((x + 4) * x + 12) * x + 24) * x + 24;
+            dD = ((4 * x + 12) * x + 24) * x + 24;
+            N[0] = 24; N[1] = ((x + 4) * x + 12) * x + 24; N[2] = ((x + 3) * x + 8) * x + 12;
+            dN[0] = 0; dN[1] = (3 * x + 8) * x + 12; dN[2] = (3 * x + 6) * x + 8;
+        }
+        for (int l = 0; l < 3; ++l) de[l] = (dN[l] * D - N[l] * dD) / (D * D);
+        return;
+    }
+    // exact exponentials: E1 = e^{-x}, E2 = sum (-x)^j/(j+1)!, E3 = sum (-x)^j/(j+2)!
+    de[0] = -std::exp(-x);
+    if (x < 0.1) {
+        double d2 = 0, d3 = 0, pw = 1.0, f2 = 2.0, f3 = 6.0;  // pw = (-1)^j x^{j-1}, j >= 1
+        for (int j = 1; j < 14; ++j) {
+            pw = (j == 1) ? -1.0 : pw * -x;
+            d2 += j * pw / f2;
+            d3 += j * pw / f3;
+            f2 *= (j + 2);
+            f3 *= (j + 3);
+        }
+        de[1] = d2;
+        de[2] = d3;
+    } else {
+        const double e = std::exp(-x);
+        de[1] = (e * (x + 1.0) - 1.0) / (x * x);
+        de[2] = ((1.0 - e) * x - 2.0 * (x - 1.0 + e)) / (x * x * x);
+    }
+}
+
+// out = T(in) (layouts of the caller, rows of n); kind >= 0 transforms f(in).
+template <typename T>
+etd_status xform(etd_plan* p, int kind, const void* in, void* out) {
+    const int sp = split_for(p, p->out_slot);
+    etd_status s = run_react<T>(p, kind, in, p->n, p->npts, p->t, sp);
+    int cur = 0;
+    if (s == ETD_OK) s = run_chain<T>(p, cur, p->out_slot, EPI_PLAIN, sp, out, p->n, p->npts);
+    return s;
+}
+
+template <typename T>
+etd_status spec(etd_plan* p, const void* in1, int x1, int s1, double a, const void* in2, int x2, int s2, double b,
+                void* out) {
+    SpecCombine<T> c{};
+    c.ncomp = p->ncomp;
+    c.d = p->d;
+    c.n = p->n;
+    c.npts = p->npts;
+    c.grid = (const double*)p->grid;
+    c.in1 = (const T*)in1;
+    c.xsel1 = x1;
+    c.s1 = s1;
+    c.alpha = a;
+    c.in2 = (const T*)in2;
+    c.xsel2 = x2;
+    c.s2 = s2;
+    c.beta = b;
+    c.out = (T*)out;
+    launch_spec_combine<T>(c, p->stream);
+    cudaError_t ce = cudaGetLastError();
+    return ce == cudaSuccess ? ETD_OK : fail(ETD_ERR_CUDA, "adjoint kernel: %s", cudaGetErrorString(ce));
+}
+
+template <typename T>
+etd_status vjp(etd_plan* p, const void* X, const void* V, const void* base, void* out) {
+    ReactVjp<T> r{};
+    r.kind = p->reaction;
+    r.ncomp = p->ncomp;
+    r.npts = p->npts;
+    for (int i = 0; i < 4; ++i) r.rp[i] = p->rp[i];
+    r.X = (const T*)X;
+    r.V = (const T*)V;
+    r.base = (const T*)base;
+    r.out = (T*)out;
+    launch_react_vjp<T>(r, p->stream);
+    cudaError_t ce = cudaGetLastError();
+    return ce == cudaSuccess ? ETD_OK : fail(ETD_ERR_CUDA, "adjoint kernel: %s", cudaGetErrorString(ce));
+}
+
+// One backward step from state U with lam = dL/dU^{n+1} on entry, dL/dU^n on exit.
+template <typename T>
+etd_status adjoint_step_impl(etd_plan* p, const void* U, void* lam) {
+    void** w = p->adj_work;
+    void *Fh = w[0], *Uh = w[1], *Wh = w[2], *W = w[3], *FWh = w[4], *Lh = w[5], *Gbh = w[6], *Gb = w[7];
+    void *Wb = w[8], *Wbh = w[9], *Fbh = w[10], *Fb = w[11], *tmp = w[12], *tmpT = w[13];
+    enum { X_ONE = 0, X_E1 = 1, X_E2 = 2, X_E3 = 3 };
+    etd_status s = ETD_OK;
+    // forward quantities of this step, in the eigenbasis
+    if (s == ETD_OK) s = xform<T>(p, p->reaction, U, Fh);                            // F^ = T f(U)
+    if (s == ETD_OK) s = xform<T>(p, -1, U, Uh);                                     // U^
+    if (s == ETD_OK) s = spec<T>(p, Uh, X_E1, 1, 1.0, Fh, X_E2, 1, 1.0, Wh);         // W^
+    if (s == ETD_OK) s = xform<T>(p, -1, Wh, W);                                     // W
+    if (s == ETD_OK) s = xform<T>(p, p->reaction, W, FWh);                           // F_W^
+    // backward
+    if (s == ETD_OK) s = xform<T>(p, -1, lam, Lh);                                   // U+bar^
+    if (s == ETD_OK) s = spec<T>(p, Lh, X_E3, 0, 1.0, nullptr, 0, 0, 0.0, Gbh);      // Gbar^ = tau E3 U+bar^
+    if (s == ETD_OK) s = xform<T>(p, -1, Gbh, Gb);                                   // Gbar
+    if (s == ETD_OK) s = vjp<T>(p, W, Gb, lam, Wb);                                  // Wbar
+    if (s == ETD_OK) s = xform<T>(p, -1, Wb, Wbh);                                   // Wbar^
+    if (s == ETD_OK) s = spec<T>(p, Wbh, X_E2, 1, 1.0, Gbh, X_ONE, 1, -1.0, Fbh);    // Fbar^
+    if (s == ETD_OK) s = xform<T>(p, -1, Fbh, Fb);                                   // Fbar
+    if (s == ETD_OK) s = spec<T>(p, Wbh, X_E1, 1, 1.0, nullptr, 0, 0, 0.0, tmp);     // X1 S Wbar^
+    if (s == ETD_OK) s = xform<T>(p, -1, tmp, tmpT);
+    if (s != ETD_OK) return s;
+    GradKappa<T> gk{};
+    gk.ncomp = p->ncomp;
+    gk.d = p->d;
+    gk.n = p->n;
+    gk.npts = p->npts;
+    gk.grid = (const double*)p->grid;
+    gk.dgrid = p->adj_dgrid;
+    gk.Lh = (const T*)Lh;
+    gk.Gbh = (const T*)Gbh;
+    gk.Wbh = (const T*)Wbh;
+    gk.Uh = (const T*)Uh;
+    gk.Fh = (const T*)Fh;
+    gk.FWh = (const T*)FWh;
+    gk.out = p->adj_acc;
+    launch_grad_kappa<T>(gk, p->stream);
+    GradRx<T> gr{};
+    gr.kind = p->reaction;
+    gr.ncomp = p->ncomp;
+    gr.npts = p->npts;
+    for (int i = 0; i < 4; ++i) gr.rp[i] = p->rp[i];
+    gr.U = (const T*)U;
+    gr.W = (const T*)W;
+    gr.Gb = (const T*)Gb;
+    gr.Fb = (const T*)Fb;
+    gr.out = p->adj_acc + 2;
+    launch_grad_rx<T>(gr, p->stream);
+    return vjp<T>(p, U, Fb, tmpT, lam);  // Ubar = X1 S Wbar + J_f(U)^T Fbar
+}
+
+template <typename T>
+etd_status adjoint_impl(etd_plan* p, const void* u_ckpt, void* lam, int n_steps) {
+    const size_t fbytes = (size_t)p->ncomp * p->npts * p->elem;
+    while ((int)p->adj_traj.size() < n_steps) {
+        void* f = nullptr;
+        etd_status s = dalloc(p, &f, fbytes);
+        if (s != ETD_OK) return s;
+        p->adj_traj.push_back(f);
+    }
+    // forward states U^0 .. U^{N-1} of the window, recomputed from the checkpoint
+    const double t0 = p->t;
+    ETD_CUDA(cudaMemcpyAsync(p->adj_traj[0], u_ckpt, fbytes, cudaMemcpyDeviceToDevice, p->stream));
+    for (int j = 1; j < n_steps; ++j) {
+        ETD_CUDA(cudaMemcpyAsync(p->adj_traj[j], p->adj_traj[j - 1], fbytes, cudaMemcpyDeviceToDevice, p->stream));
+        etd_status s = step_impl<T>(p, p->adj_traj[j], 1);
+        if (s != ETD_OK) return s;
+    }
+    p->t = t0;
+    p->uhat_valid = false;  // the carried state now belongs to the recomputed window
+    for (int j = n_steps - 1; j >= 0; --j) {
+        etd_status s = adjoint_step_impl<T>(p, p->adj_traj[j], lam);
+        if (s != ETD_OK) return s;
+    }
+    return ETD_OK;
 }
 
 etd_status check_device_ptr(const void* ptr, const char* what) {
@@ -793,6 +971,54 @@ etd_status etd_step(etd_plan* p, void* u_dev, int n_steps) {
     if (s != ETD_OK) return s;
     if (n_steps == 0) return ETD_OK;
     return (p->elem == 8) ? step_impl<double>(p, u_dev, n_steps) : step_impl<float>(p, u_dev, n_steps);
+}
+
+etd_status etd_step_adjoint(etd_plan* p, const void* u_ckpt, void* lambda_dev, int n_steps, double* grad_kappa,
+                            double* grad_rx) {
+    if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
+    if (p->is_batch) return fail(ETD_ERR_INVALID_ARG, "the adjoint works on single plans");
+    if (n_steps < 1) return fail(ETD_ERR_INVALID_ARG, "n_steps must be >= 1");
+    if (p->reaction == ETD_RX_AC_FORCED)
+        return fail(ETD_ERR_UNSUPPORTED, "the adjoint supports autonomous reactions only");
+    etd_status s = check_device_ptr(u_ckpt, "u_ckpt");
+    if (s == ETD_OK) s = check_device_ptr(lambda_dev, "lambda_dev");
+    if (s != ETD_OK) return s;
+    const size_t fbytes = (size_t)p->ncomp * p->npts * p->elem;
+    if (!p->adj_acc) {
+        for (int i = 0; i < 14 && s == ETD_OK; ++i) s = dalloc(p, &p->adj_work[i], fbytes);
+        if (s == ETD_OK) s = dalloc(p, (void**)&p->adj_acc, 8 * sizeof(double));
+        if (s == ETD_OK) s = dalloc(p, (void**)&p->adj_dgrid, (size_t)p->ncomp * 3 * p->n * sizeof(double));
+        if (s != ETD_OK) return s;
+        // d/dkappa of E1(tau lambda), tau E2, tau E3: tau mu E_l'(tau lambda), mu = dlambda/dkappa
+        const int n = p->n;
+        const double h = 1.0 / (n + 1), pi = 3.14159265358979323846;
+        std::vector<double> dg((size_t)p->ncomp * 3 * n);
+        for (int c = 0; c < p->ncomp; ++c)
+            for (int k = 0; k < n; ++k) {
+                const double sk = std::sin(pi * (k + 1) / (2.0 * (n + 1)));
+                const double mu = 4.0 / (h * h) * sk * sk;
+                const double lam = p->kappa[c] * mu + p->q / p->d;
+                double de[3];
+                factor_grid_derivs(p->pade, p->tau * lam, de);
+                dg[((size_t)c * 3 + 0) * n + k] = p->tau * mu * de[0];
+                dg[((size_t)c * 3 + 1) * n + k] = p->tau * p->tau * mu * de[1];
+                dg[((size_t)c * 3 + 2) * n + k] = p->tau * p->tau * mu * de[2];
+            }
+        ETD_CUDA(cudaMemcpy(p->adj_dgrid, dg.data(), dg.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    ETD_CUDA(cudaMemsetAsync(p->adj_acc, 0, 8 * sizeof(double), p->stream));
+    s = (p->elem == 8) ? adjoint_impl<double>(p, u_ckpt, lambda_dev, n_steps)
+                       : adjoint_impl<float>(p, u_ckpt, lambda_dev, n_steps);
+    if (s != ETD_OK) return s;
+    double acc[8];
+    ETD_CUDA(cudaMemcpyAsync(acc, p->adj_acc, sizeof acc, cudaMemcpyDeviceToHost, p->stream));
+    s = etd_sync(p);
+    if (s != ETD_OK) return s;
+    if (grad_kappa)
+        for (int c = 0; c < p->ncomp; ++c) grad_kappa[c] += acc[c];
+    if (grad_rx)
+        for (int i = 0; i < 4; ++i) grad_rx[i] += acc[2 + i];
+    return ETD_OK;
 }
 
 etd_status etd_sync(etd_plan* p) {

@@ -27,7 +27,7 @@ SYMBOLS = (
     "etd_options_default", "etd_plan_create", "etd_step", "etd_step_host", "etd_transform",
     "etd_plan_invalidate", "etd_set_time", "etd_sync", "etd_field_stats", "etd_get_plan_info",
     "etd_set_timing", "etd_kernel_times", "etd_plan_destroy", "etd_status_string", "etd_last_error",
-    "etd_transform_noalloc", "etd_batch_create", "etd_batch_step",
+    "etd_transform_noalloc", "etd_batch_create", "etd_batch_step", "etd_step_adjoint",
 )
 ETD_NOALLOC_MAX_ELEMS = 4194304
 
@@ -94,6 +94,7 @@ def lib():
             "etd_batch_create": ([ctypes.POINTER(vp), i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d),
                                   ctypes.POINTER(d), ctypes.POINTER(d), i, ctypes.POINTER(etd_options)], i),
             "etd_batch_step": ([vp, ctypes.POINTER(vp), i], i),
+            "etd_step_adjoint": ([vp, vp, vp, i, ctypes.POINTER(d), ctypes.POINTER(d)], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -195,6 +196,15 @@ def etd_batch_create(d, m, kappa, q, dt, pade_order: int, opt: Optional[etd_opti
 def etd_batch_step(plan: int, u_dev_ptrs, n_steps: int) -> None:
     ptrs = (ctypes.c_void_p * len(u_dev_ptrs))(*u_dev_ptrs)
     _check(lib().etd_batch_step(plan, ptrs, n_steps))
+
+
+def etd_step_adjoint(plan: int, u_ckpt: int, lambda_dev: int, n_steps: int):
+    """Backpropagate lambda_dev (in place) through n_steps from u_ckpt; returns
+    (dL/dkappa per component [2], dL/d rx_params [4])."""
+    gk = (ctypes.c_double * 2)()
+    gr = (ctypes.c_double * 4)()
+    _check(lib().etd_step_adjoint(plan, u_ckpt, lambda_dev, n_steps, gk, gr))
+    return list(gk), list(gr)
 
 
 def etd_plan_destroy(plan: int) -> None:
@@ -337,6 +347,12 @@ class Plan:
 
     def sync(self):
         etd_sync(self.handle)
+
+    def adjoint(self, u_ckpt, lam, n_steps: int):
+        """lam <- dL/dU at u_ckpt given dL/dU n_steps later; returns (dL/dkappa, dL/drx)."""
+        self._check_field(u_ckpt, "u_ckpt")
+        self._check_field(lam, "lam")
+        return etd_step_adjoint(self.handle, u_ckpt.data_ptr(), lam.data_ptr(), n_steps)
 
     def stats(self, u):
         self._check_field(u)
