@@ -182,6 +182,15 @@ etd_status etd_batch_step(etd_plan* p, void* const* u_dev, int n_steps);
 etd_status etd_step_adjoint(etd_plan* p, const void* u_ckpt, void* lambda_dev, int n_steps, double* grad_kappa,
                             double* grad_rx);
 
+/*
+ * Failure-path self test (no counterpart in the paper): launches, on the plan
+ * stream, a one-CTA kernel whose bounded device wait (the same routine the
+ * transform kernels use, limit limit_ms in (0, 1000]) has nothing to wait for,
+ * so it runs out, raises the plan's timeout flag and returns. The next etd_sync
+ * then returns ETD_ERR_TIMEOUT and clears the flag; the plan stays usable.
+ */
+etd_status etd_selftest_wait_timeout(etd_plan* p, double limit_ms);
+
 /* Forget the carried spectral state (after the caller changed u_dev). */
 etd_status etd_plan_invalidate(etd_plan* p);
 

@@ -319,5 +319,6 @@ void tc_maps_destroy(TcMaps* m);
 cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, int a_index, int M, int n, int nbatch,
                            const Epi<float>& e, unsigned* err, cudaStream_t st);
 const char* tc_last_driver_error();
+cudaError_t launch_wait_timeout_probe(unsigned* err, double limit_ms, cudaStream_t st);
 
 }  // namespace etd

@@ -1021,6 +1021,13 @@ etd_status etd_step_adjoint(etd_plan* p, const void* u_ckpt, void* lambda_dev, i
     return ETD_OK;
 }
 
+etd_status etd_selftest_wait_timeout(etd_plan* p, double limit_ms) {
+    if (!p || p->is_batch) return fail(ETD_ERR_INVALID_ARG, "a single plan is required");
+    if (!(limit_ms > 0) || limit_ms > 1000) return fail(ETD_ERR_INVALID_ARG, "limit_ms must be in (0, 1000]");
+    ETD_CUDA(launch_wait_timeout_probe(p->err, limit_ms, p->stream));
+    return ETD_OK;
+}
+
 etd_status etd_sync(etd_plan* p) {
     if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
     for (etd_plan* g : p->groups) {

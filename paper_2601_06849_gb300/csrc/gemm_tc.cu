@@ -89,13 +89,14 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // Wait for the phase with the given parity to complete; false on timeout/abort.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* err) {
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* err,
+                          unsigned long long limit_ns = WAIT_LIMIT_NS) {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (;;) {
         if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (globaltimer() - t0 > WAIT_LIMIT_NS) {
+        if (globaltimer() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicOr(err, ERR_TIMEOUT);
             return false;
@@ -783,6 +784,20 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     }
 }
 
+// Diagnostic: one thread waits, through mbar_wait, on an mbarrier that no one
+// arrives at, so the bounded wait runs out after limit_ns and raises ERR_TIMEOUT
+// exactly as a stalled pipeline would; the kernel then returns normally.
+__global__ void wait_timeout_probe_kernel(unsigned* err, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_wait(smem_u32(&bar), 0u, &abort_flag, err, limit_ns);
+    }
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -919,6 +934,11 @@ cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const
 }
 
 void tc_maps_destroy(TcMaps* m) { delete m; }
+
+cudaError_t launch_wait_timeout_probe(unsigned* err, double limit_ms, cudaStream_t st) {
+    wait_timeout_probe_kernel<<<1, 32, 0, st>>>(err, (unsigned long long)(limit_ms * 1e6));
+    return cudaGetLastError();
+}
 
 cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, int a_index, int M, int n, int nbatch,
                            const Epi<float>& e, unsigned* err, cudaStream_t st) {

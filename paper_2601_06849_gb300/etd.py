@@ -28,6 +28,7 @@ SYMBOLS = (
     "etd_plan_invalidate", "etd_set_time", "etd_sync", "etd_field_stats", "etd_get_plan_info",
     "etd_set_timing", "etd_kernel_times", "etd_plan_destroy", "etd_status_string", "etd_last_error",
     "etd_transform_noalloc", "etd_batch_create", "etd_batch_step", "etd_step_adjoint",
+    "etd_selftest_wait_timeout",
 )
 ETD_NOALLOC_MAX_ELEMS = 4194304
 
@@ -95,6 +96,7 @@ def lib():
                                   ctypes.POINTER(d), ctypes.POINTER(d), i, ctypes.POINTER(etd_options)], i),
             "etd_batch_step": ([vp, ctypes.POINTER(vp), i], i),
             "etd_step_adjoint": ([vp, vp, vp, i, ctypes.POINTER(d), ctypes.POINTER(d)], i),
+            "etd_selftest_wait_timeout": ([vp, d], i),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -205,6 +207,10 @@ def etd_step_adjoint(plan: int, u_ckpt: int, lambda_dev: int, n_steps: int):
     gr = (ctypes.c_double * 4)()
     _check(lib().etd_step_adjoint(plan, u_ckpt, lambda_dev, n_steps, gk, gr))
     return list(gk), list(gr)
+
+
+def etd_selftest_wait_timeout(plan: int, limit_ms: float) -> None:
+    _check(lib().etd_selftest_wait_timeout(plan, limit_ms))
 
 
 def etd_plan_destroy(plan: int) -> None:
