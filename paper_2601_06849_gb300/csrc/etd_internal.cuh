@@ -11,6 +11,7 @@
 // three passes the three mode products (3D), and the same passes invert them.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,8 +30,23 @@ enum SplitKind : int {
     SPLIT_NONE = 0,     // one plane, the value itself (CUDA-core products)
     SPLIT_TF32 = 1,     // hi = rna_tf32(v), lo = rna_tf32(v - hi)
     SPLIT_TF32_HI = 2,  // hi only, rna_tf32(v) (single TF32 product)
-    SPLIT_TF32_3 = 3    // hi, mid = rna_tf32(v - hi), lo = rna_tf32(v - hi - mid)
+    SPLIT_TF32_3 = 3,   // hi, mid = rna_tf32(v - hi), lo = rna_tf32(v - hi - mid)
+    SPLIT_BF16_2 = 4,   // BF16 planes: hi = rn_bf16(v), lo = rn_bf16(v - hi)
+    SPLIT_BF16_3 = 5    // BF16 planes: hi, mid, lo (24 significant bits)
 };
+
+// BF16 pieces of v (round to nearest even); the operand planes are then 2-byte arrays.
+__device__ __forceinline__ void split_bf16(double v, int pieces, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                           __nv_bfloat16* lo2, long long o) {
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+    hi[o] = h;
+    if (pieces < 2) return;
+    const double r1 = v - (double)__bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn((float)r1);
+    lo[o] = m;
+    if (pieces < 3) return;
+    lo2[o] = __float2bfloat16_rn((float)(r1 - (double)__bfloat162float(m)));
+}
 
 enum ErrBits : unsigned { ERR_TIMEOUT = 1u, ERR_BAD_CONFIG = 2u };
 
@@ -66,6 +82,11 @@ struct Epi {
 
     __device__ __forceinline__ void write_operand(long long o, double v) const {
         if constexpr (sizeof(T) == 4) {
+            if (split == SPLIT_BF16_2 || split == SPLIT_BF16_3) {
+                split_bf16(v, split == SPLIT_BF16_3 ? 3 : 2, reinterpret_cast<__nv_bfloat16*>(op_hi),
+                           reinterpret_cast<__nv_bfloat16*>(op_lo), reinterpret_cast<__nv_bfloat16*>(op_lo2), o);
+                return;
+            }
             if (split == SPLIT_TF32) {
                 const float h = tf32_rna((float)v);
                 op_hi[o] = h;
@@ -302,6 +323,7 @@ struct TcConfig {
     int stages;      // shared-memory pipeline depth
     int products;    // 1 (TF32), 3 (two-piece split) or 6 (three-piece split)
     int pieces;      // operand pieces read per product mode
+    bool bf16;       // BF16 pieces, kind::f16 products (else TF32 pieces, kind::tf32)
     bool accurate;   // separate correction accumulator + compensated k-block sums
     bool persistent; // one CTA per SM, epilogue overlapped with the next tile
     int tiles_m, tiles_n;
@@ -310,11 +332,11 @@ struct TcConfig {
     unsigned stage_bytes;
 };
 struct TcMaps;  // opaque holder of CUtensorMap objects (gemm_tc.cu)
-TcConfig tc_choose(int M, int n, int products, int nbatch);
+TcConfig tc_choose(int M, int n, int products, int nbatch, bool bf16);
 // a[i][j]: operand buffer i, piece j (NULL = reuse piece 0); pp[j]: pieces of P;
 // bn_slot: tile widths of the two configurations the maps serve.
-cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const float* const a[][3], int n_a,
-                           const float* const pp[3], const int bn_slot[2]);
+cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const void* const a[][3], int n_a,
+                           const void* const pp[3], const int bn_slot[2], bool bf16);
 void tc_maps_destroy(TcMaps* m);
 cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, int a_index, int M, int n, int nbatch,
                            const Epi<float>& e, unsigned* err, cudaStream_t st);

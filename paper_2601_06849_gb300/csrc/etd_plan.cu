@@ -55,6 +55,8 @@ struct etd_plan {
     long long bs = 0, npts = 0;
     size_t elem = 4;
     bool use_tc = false;
+    bool bf16 = false;  // BF16 operand pieces (ETD_PREC_BF16X3 / X6)
+    size_t op_elem = 4; // bytes per operand-plane value
     int pieces = 1;     // operand planes allocated per buffer
     int out_slot = 0;   // config slot of the transform that returns the field
     // device memory
@@ -144,6 +146,22 @@ void factor_grids(int family, double x, double* e) {
             e[2] = (x + std::expm1(-x)) / (x * x);
         }
     }
+}
+
+// Round to BF16 (7 stored mantissa bits), nearest with ties to even: add half an
+// ulp of the kept part (minus one when the kept part is even) and truncate.
+uint16_t bf16_round_host(float v) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_to_float_host(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
 }
 
 // Round to TF32 (10 stored mantissa bits), nearest with ties away from zero.
@@ -250,6 +268,7 @@ Epi<T> base_epi(const etd_plan* p) {
 int split_for(const etd_plan* p, int slot) {
     if (!p->use_tc) return SPLIT_NONE;
     const int pieces = p->tc[slot].pieces;
+    if (p->bf16) return pieces == 3 ? SPLIT_BF16_3 : SPLIT_BF16_2;
     return pieces == 3 ? SPLIT_TF32_3 : (pieces == 2 ? SPLIT_TF32 : SPLIT_TF32_HI);
 }
 
@@ -614,8 +633,6 @@ etd_status validate_options(int d, int m, int pade_order, const etd_options& opt
         return fail(ETD_ERR_INVALID_ARG, "this reaction needs n_comp = 1");
     if (opt.precision < ETD_PREC_FP64 || opt.precision > ETD_PREC_TF32X6)
         return fail(ETD_ERR_INVALID_ARG, "unknown precision");
-    if (opt.precision == ETD_PREC_BF16X3 || opt.precision == ETD_PREC_BF16X6)
-        return fail(ETD_ERR_UNSUPPORTED, "BF16 split precisions are not built yet");
     return ETD_OK;
 }
 
@@ -647,13 +664,15 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     p->tau = dtv[0];
     p->stream = (cudaStream_t)opt.stream;
     p->elem = (opt.precision == ETD_PREC_FP64) ? 8 : 4;
-    p->use_tc = (opt.precision == ETD_PREC_TF32 || opt.precision == ETD_PREC_TF32X3 ||
-                 opt.precision == ETD_PREC_TF32X6);
+    p->bf16 = (opt.precision == ETD_PREC_BF16X3 || opt.precision == ETD_PREC_BF16X6);
+    p->use_tc = p->bf16 || opt.precision == ETD_PREC_TF32 || opt.precision == ETD_PREC_TF32X3 ||
+                opt.precision == ETD_PREC_TF32X6;
+    p->op_elem = p->bf16 ? 2 : p->elem;
     const int n = m;
     const int nb = ninst * p->ncomp;
     p->M = (d == 2) ? n : n * n;
     p->mq = (d == 2) ? 1 : n;
-    p->ld = (n + 3) / 4 * 4;
+    p->ld = (n + 7) / 8 * 8;  // rows start on 16-byte boundaries for 2- and 4-byte values
     p->bs = (long long)p->M * p->ld;
     p->npts = (long long)p->M * n;
 
@@ -685,10 +704,12 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
 
     // ---- tensor-core configurations ----
     if (p->use_tc) {
-        const int prod0 = opt.precision == ETD_PREC_TF32 ? 1 : (opt.precision == ETD_PREC_TF32X6 ? 6 : 3);
-        p->tc[0] = tc_choose(p->M, n, prod0, nb);
-        if (opt.precision == ETD_PREC_TF32X3) {
-            p->tc[1] = tc_choose(p->M, n, 6, nb);
+        const int prod0 = opt.precision == ETD_PREC_TF32
+                              ? 1
+                              : ((opt.precision == ETD_PREC_TF32X6 || opt.precision == ETD_PREC_BF16X6) ? 6 : 3);
+        p->tc[0] = tc_choose(p->M, n, prod0, nb, p->bf16);
+        if (opt.precision == ETD_PREC_TF32X3 || opt.precision == ETD_PREC_BF16X3) {
+            p->tc[1] = tc_choose(p->M, n, 6, nb, p->bf16);
             p->out_slot = 1;
         } else {
             p->tc[1] = p->tc[0];
@@ -701,7 +722,8 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     const size_t E = p->elem;
     const size_t field_bytes = (size_t)nb * p->bs * E;
     const size_t state_bytes = (size_t)nb * p->bs * sizeof(double);
-    const size_t pbytes = (size_t)n * p->ld * E;
+    const size_t pbytes = (size_t)n * p->ld * p->op_elem;
+    const size_t op_bytes = (size_t)nb * p->bs * p->op_elem;
     for (int j = 0; j < p->pieces && s == ETD_OK; ++j) s = dalloc(p, &p->P[j], pbytes);
     if (s == ETD_OK) s = dalloc(p, &p->grid, (size_t)nb * 3 * n * sizeof(double));
     if (s == ETD_OK) s = dalloc(p, &p->uhat, state_bytes);
@@ -709,7 +731,7 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     if (s == ETD_OK) s = dalloc(p, &p->fq, field_bytes);
     if (s == ETD_OK) s = dalloc(p, &p->wphys, field_bytes);
     for (int i = 0; i < 2 && s == ETD_OK; ++i)
-        for (int j = 0; j < p->pieces && s == ETD_OK; ++j) s = dalloc(p, &p->op[i][j], field_bytes);
+        for (int j = 0; j < p->pieces && s == ETD_OK; ++j) s = dalloc(p, &p->op[i][j], op_bytes);
     if (s == ETD_OK) s = dalloc(p, (void**)&p->err, sizeof(unsigned) * 4);
     if (s == ETD_OK) s = dalloc(p, (void**)&p->stats, sizeof(double) * 4);
     if (s != ETD_OK) {
@@ -729,6 +751,13 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
                     ((double*)hostbuf.data())[o] = v;
                 } else if (!p->use_tc) {
                     ((float*)hostbuf.data())[o] = (float)v;
+                } else if (p->bf16) {
+                    uint16_t piece = 0;
+                    for (int q = 0; q <= j; ++q) {
+                        piece = bf16_round_host((float)v);
+                        v -= (double)bf16_to_float_host(piece);
+                    }
+                    ((uint16_t*)hostbuf.data())[o] = piece;
                 } else {
                     float piece = 0.f;
                     for (int q = 0; q <= j; ++q) {
@@ -743,19 +772,19 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     if (ce == cudaSuccess) ce = cudaMemcpy(p->grid, grid.data(), grid.size() * sizeof(double), cudaMemcpyHostToDevice);
     // zero the padded operand columns once (they are never written by the passes)
     for (int i = 0; i < 2 && ce == cudaSuccess; ++i)
-        for (int j = 0; j < p->pieces && ce == cudaSuccess; ++j) ce = cudaMemset(p->op[i][j], 0, field_bytes);
+        for (int j = 0; j < p->pieces && ce == cudaSuccess; ++j) ce = cudaMemset(p->op[i][j], 0, op_bytes);
     if (ce == cudaSuccess) ce = cudaMemset(p->err, 0, sizeof(unsigned) * 4);
     if (ce != cudaSuccess) {
         free_plan(p);
         return fail(ETD_ERR_CUDA, "plan upload: %s", cudaGetErrorString(ce));
     }
     if (p->use_tc) {
-        const float* a[2][3];
+        const void* a[2][3];
         for (int i = 0; i < 2; ++i)
-            for (int j = 0; j < 3; ++j) a[i][j] = (const float*)p->op[i][j];
-        const float* pp[3] = {(const float*)p->P[0], (const float*)p->P[1], (const float*)p->P[2]};
+            for (int j = 0; j < 3; ++j) a[i][j] = p->op[i][j];
+        const void* pp[3] = {p->P[0], p->P[1], p->P[2]};
         const int bn_slot[2] = {p->tc[0].bn, p->tc[1].bn};
-        ce = tc_maps_create(&p->maps, p->M, n, nb, p->ld, a, 2, pp, bn_slot);
+        ce = tc_maps_create(&p->maps, p->M, n, nb, p->ld, a, 2, pp, bn_slot, p->bf16);
         if (ce != cudaSuccess) {
             std::string why = tc_last_driver_error();
             free_plan(p);

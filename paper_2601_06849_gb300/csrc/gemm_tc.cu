@@ -38,7 +38,7 @@ struct TcMaps {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BKF = 32;                  // FP32 elements per k-block = one 128-byte row
+constexpr int BKF = 32;                  // TF32 values per k-block = one 128-byte row (64 for BF16)
 constexpr int A_BYTES = BM * BKF * 4;    // 16 KiB per operand plane
 constexpr int NUM_EPI_WARPS = 8;         // two per TMEM lane quarter, one per column half
 constexpr int WARP_TMA = 8;
@@ -53,6 +53,8 @@ struct KParams {
     int M, n, bn, stages, products, pieces, tiles_m, tiles_n, tmem_cols;
     int acc_cols;  // columns of one accumulator region (power of two >= bn)
     int nbatch;
+    int bf16;      // BF16 pieces and kind::f16 products (else TF32, kind::tf32)
+    int kvals;     // operand values per k-block: 32 (TF32) or 64 (BF16), 128 bytes per row
     unsigned stage_bytes, b_bytes, tx_bytes;
     unsigned* err;
     Epi<float> e;
@@ -171,6 +173,31 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
         : "memory");
 }
 
+// Instruction descriptor of kind::f16 with BF16 operands: D = F32, A = B = BF16
+// (format 1 at bits 7-9 and 10-12), both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// One product of 32-byte K slices (8 TF32 or 16 BF16 values) of the two operands.
+__device__ __forceinline__ void mma_op(int bf16, uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    if (bf16)
+        mma_bf16(tmem_d, adesc, bdesc, idesc, accumulate);
+    else
+        mma_tf32(tmem_d, adesc, bdesc, idesc, accumulate);
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -275,7 +302,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
     int b, tm, tn;
     tile_coords(blockIdx.x, p.tiles_m, p.tiles_n, 16, b, tm, tn);
-    const int nk = (p.n + BKF - 1) / BKF;
+    const int nk = (p.n + p.kvals - 1) / p.kvals;
     // TMEM columns: [0, acc) and [acc, 2 acc) k-block buffers, [2 acc, 3 acc) corrections (ACCURATE)
     const uint32_t acc_cols = (uint32_t)p.acc_cols;
 
@@ -318,7 +345,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const uint32_t st = smem_u32(smem + (size_t)s * p.stage_bytes);
             const uint32_t fb = bar_full + 8 * s;
             mbar_expect_tx(fb, p.tx_bytes);
-            const int k0 = kb * BKF;
+            const int k0 = kb * p.kvals;
             const uint32_t sb = st + (uint32_t)p.pieces * A_BYTES;  // first P piece
             tma_load_2d(st, &mA0, fb, k0, arow);
             tma_load_2d(sb, &mP0, fb, k0, prow);
@@ -335,7 +362,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         s_issued = issued;
     } else if (warp == WARP_MMA && lane == 0) {
         // ---------------- MMA issuer: one k-block per accumulator buffer ----------------
-        const uint32_t idesc = idesc_tf32(BM, p.bn);
+        const uint32_t idesc = p.bf16 ? idesc_bf16(BM, p.bn) : idesc_tf32(BM, p.bn);
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % S;
             const int a = kb & 1;
@@ -350,19 +377,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const uint32_t b0 = a0 + (uint32_t)p.pieces * A_BYTES;
             const uint32_t b1 = b0 + p.b_bytes, b2 = b0 + 2 * p.b_bytes;
 #pragma unroll
-            for (int kk = 0; kk < BKF / 8; ++kk) {
+            for (int kk = 0; kk < 4; ++kk) {
                 const uint32_t off = kk * 32;  // 8 TF32 values = 32 bytes per MMA
                 // terms of (a0 + a1 + a2)(b0 + b1 + b2) down to the 2^-22 level
-                mma_tf32(d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
+                mma_op(p.bf16, d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
                 const uint32_t cacc = ACCURATE ? ((kb > 0 || kk > 0) ? 1u : 0u) : 1u;
                 if (p.products >= 3) {
-                    mma_tf32(dc, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, cacc);
-                    mma_tf32(dc, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                    mma_op(p.bf16, dc, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, cacc);
+                    mma_op(p.bf16, dc, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
                 }
                 if (p.products == 6) {
-                    mma_tf32(dc, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), idesc, 1u);
-                    mma_tf32(dc, sdesc_sw128(a2 + off), sdesc_sw128(b0 + off), idesc, 1u);
-                    mma_tf32(dc, sdesc_sw128(a0 + off), sdesc_sw128(b2 + off), idesc, 1u);
+                    mma_op(p.bf16, dc, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                    mma_op(p.bf16, dc, sdesc_sw128(a2 + off), sdesc_sw128(b0 + off), idesc, 1u);
+                    mma_op(p.bf16, dc, sdesc_sw128(a0 + off), sdesc_sw128(b2 + off), idesc, 1u);
                 }
             }
             mma_commit(bar_empty + 8 * s);     // stage s may be refilled once these products finish
@@ -563,7 +590,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     const uint32_t bar_st_full = smem_u32(&s_bar[22]);
     const uint32_t bar_st_empty = smem_u32(&s_bar[24]);
     const uint32_t bar_done = smem_u32(&s_bar[26]);
-    const int nk = (p.n + BKF - 1) / BKF;
+    const int nk = (p.n + p.kvals - 1) / p.kvals;
     const int nkb = 2;                 // k-block buffers (3 + 1 measured slower than 2 + 2)
     const int nsb = 4 - nkb;           // staging buffers
     const uint32_t staging0 = (uint32_t)nkb * pk::KB_COLS;
@@ -618,7 +645,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                 const uint32_t st = smem_u32(smem + (size_t)s * p.stage_bytes);
                 const uint32_t fb = bar_full + 8 * s;
                 mbar_expect_tx(fb, p.tx_bytes);
-                const int k0 = kb * BKF;
+                const int k0 = kb * p.kvals;
                 const uint32_t sb = st + (uint32_t)p.pieces * A_BYTES;
                 tma_load_2d(st, &mA0, fb, k0, arow);
                 tma_load_2d(sb, &mP0, fb, k0, prow);
@@ -631,7 +658,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
         }
     } else if (warp == pk::WARP_MMA && lane == 0) {
         // ---------------- MMA issuer ----------------
-        const uint32_t idesc = idesc_tf32(BM, p.bn);
+        const uint32_t idesc = p.bf16 ? idesc_bf16(BM, p.bn) : idesc_tf32(BM, p.bn);
         int g = 0;
         bool stop = false;
         for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
@@ -651,12 +678,12 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                 const uint32_t b0 = a0 + (uint32_t)p.pieces * A_BYTES;
                 const uint32_t b1 = b0 + p.b_bytes;
 #pragma unroll
-                for (int kk = 0; kk < BKF / 8; ++kk) {
+                for (int kk = 0; kk < 4; ++kk) {
                     const uint32_t off = kk * 32;
-                    mma_tf32(d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
+                    mma_op(p.bf16, d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
                     if (p.products >= 3) {
-                        mma_tf32(d, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, 1u);
-                        mma_tf32(d, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                        mma_op(p.bf16, d, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, 1u);
+                        mma_op(p.bf16, d, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
                     }
                 }
                 mma_commit(bar_empty + 8 * s);
@@ -817,17 +844,18 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap* map, const float* base, int inner, long long rows, int ld, int box_rows) {
+bool make_map(CUtensorMap* map, const void* base, int inner, long long rows, int ld, int box_rows, bool bf16) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) {
         snprintf(g_driver_error, sizeof g_driver_error, "cuTensorMapEncodeTiled entry point not found");
         return false;
     }
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-    cuuint32_t box[2] = {(cuuint32_t)BKF, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * (bf16 ? 2 : 4)};
+    cuuint32_t box[2] = {(cuuint32_t)(bf16 ? 2 * BKF : BKF), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+    CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                    const_cast<void*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -842,18 +870,20 @@ bool make_map(CUtensorMap* map, const float* base, int inner, long long rows, in
 
 const char* tc_last_driver_error() { return g_driver_error; }
 
-TcConfig tc_choose(int M, int n, int products, int nbatch) {
+TcConfig tc_choose(int M, int n, int products, int nbatch, bool bf16) {
     TcConfig c{};
     c.products = products;
+    c.bf16 = bf16;
     c.pieces = products == 6 ? 3 : (products == 3 ? 2 : 1);
     c.accurate = (c.pieces == 3);
     // The 128 x 256 one-tile-per-CTA kernel wins when each tile has a long K loop
     // and there are enough tiles to fill the SMs several times over (2D at large
     // n); otherwise (3D: K = n is short, the epilogue dominates; mid-size 2D:
     // few tiles) the persistent 128 x 128 kernel overlaps epilogue and products.
-    const int nk = (n + BKF - 1) / BKF;
+    const int kv = bf16 ? 2 * BKF : BKF;
+    const int nk = (n + kv - 1) / kv;
     const long long tiles256 = (long long)nbatch * ((M + BM - 1) / BM) * ((n + 255) / 256);
-    c.persistent = !c.accurate && !(nk >= 64 && tiles256 >= 4 * 152);
+    c.persistent = !c.accurate && !(nk * kv >= 2048 && tiles256 >= 4 * 152);
     // tile width: the multiple of 32 up to bn_max that wastes the fewest columns
     // (each of the two column halves is a whole number of 16-column TMEM loads)
     const int bn_max = (c.accurate || c.persistent) ? 128 : 256;
@@ -892,8 +922,8 @@ TcConfig tc_choose(int M, int n, int products, int nbatch) {
     return c;
 }
 
-cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const float* const a[][3], int n_a,
-                           const float* const pp[3], const int bn_slot[2]) {
+cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const void* const a[][3], int n_a,
+                           const void* const pp[3], const int bn_slot[2], bool bf16) {
     *out = nullptr;
     if (n_a > 4) return cudaErrorInvalidValue;
     TcMaps* m = new TcMaps();
@@ -901,13 +931,13 @@ cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const
     bool ok = true;
     for (int i = 0; i < n_a && ok; ++i)
         for (int j = 0; j < 3 && ok; ++j) {
-            const float* base = a[i][j] ? a[i][j] : a[i][0];
-            ok = make_map(&m->a[i][j], base, n, (long long)nbatch * M, ld, BM);
+            const void* base = a[i][j] ? a[i][j] : a[i][0];
+            ok = make_map(&m->a[i][j], base, n, (long long)nbatch * M, ld, BM, bf16);
         }
     for (int slot = 0; slot < 2 && ok; ++slot)
         for (int j = 0; j < 3 && ok; ++j) {
-            const float* base = pp[j] ? pp[j] : pp[0];
-            ok = make_map(&m->p[slot][j], base, n, n, ld, bn_slot[slot] > 0 ? bn_slot[slot] : 32);
+            const void* base = pp[j] ? pp[j] : pp[0];
+            ok = make_map(&m->p[slot][j], base, n, n, ld, bn_slot[slot] > 0 ? bn_slot[slot] : 32, bf16);
         }
     if (!ok) {
         delete m;
@@ -960,6 +990,8 @@ cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, in
     p.err = err;
     p.e = e;
     p.nbatch = nbatch;
+    p.bf16 = cfg.bf16 ? 1 : 0;
+    p.kvals = cfg.bf16 ? 2 * BKF : BKF;
     const long long ntiles = (long long)nbatch * cfg.tiles_m * cfg.tiles_n;
     const CUtensorMap* A = maps->a[a_index];
     const CUtensorMap* P = maps->p[slot];

@@ -13,6 +13,11 @@ namespace etd {
 template <typename T>
 __device__ __forceinline__ void store_split(T* hi, T* lo, T* lo2, long long o, T v, int split) {
     if constexpr (sizeof(T) == 4) {
+        if (split == SPLIT_BF16_2 || split == SPLIT_BF16_3) {
+            split_bf16((double)v, split == SPLIT_BF16_3 ? 3 : 2, reinterpret_cast<__nv_bfloat16*>(hi),
+                       reinterpret_cast<__nv_bfloat16*>(lo), reinterpret_cast<__nv_bfloat16*>(lo2), o);
+            return;
+        }
         if (split == SPLIT_TF32_3) {  // three TF32 pieces hold all 24 bits of v
             const float h = tf32_rna(v);
             const float m = tf32_rna(v - h);

@@ -7,7 +7,7 @@ from gpu_util import need_gpu, rel_err, sine_basis
 from paper_2601_06849_gb300 import etd, inputs
 
 # bound on max|T_gpu - T| / max|T| for one transform (2 or 3 chained passes)
-TOL = {"fp64": 1e-13, "fp32": 1e-5, "tf32x3": 2e-6, "tf32x6": 2e-6, "tf32": 5e-3}
+TOL = {"fp64": 1e-13, "fp32": 1e-5, "tf32x3": 2e-6, "tf32x6": 2e-6, "tf32": 5e-3, "bf16x3": 2e-6, "bf16x6": 2e-6}
 
 
 def reference(x, d):
@@ -30,7 +30,7 @@ def test_sine_basis_diagonalises_operator():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32x3", "tf32x6", "tf32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32x3", "tf32x6", "tf32", "bf16x3", "bf16x6"])
 @pytest.mark.parametrize("d,n,ncomp", [(2, 64, 1), (2, 200, 2), (2, 37, 1), (3, 24, 1), (3, 45, 2), (2, 520, 1),
                                        (2, 2, 1)])
 def test_transform_matches_definition(precision, d, n, ncomp):
