@@ -55,9 +55,11 @@ __global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
             case ETD_RX_FHN: {
                 // f_u = u - c3 u^3 - v,  f_v = eps (u - a v - b)
                 const T u = r.in[oi], v = r.in[r.bs_in + oi];
+                // component offsets go into the element index, never into pointer
+                // arithmetic: the operand planes hold 4-byte or 2-byte values
                 store_split(r.out_hi, r.out_lo, r.out_lo2, oo, u - r.rp[0] * u * u * u - v, r.split);
-                store_split(r.out_hi + r.bs_out, r.out_lo + r.bs_out, r.out_lo2 + r.bs_out, oo,
-                            r.rp[1] * (u - r.rp[2] * v - r.rp[3]), r.split);
+                store_split(r.out_hi, r.out_lo, r.out_lo2, oo + r.bs_out, r.rp[1] * (u - r.rp[2] * v - r.rp[3]),
+                            r.split);
                 break;
             }
             case ETD_RX_ALLEN_CAHN: {
@@ -89,8 +91,7 @@ __global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
                     T f = (T)0;
                     if (r.kind == ETD_RX_LINEAR) f = r.rp[0] * u;
                     else if (r.kind < 0) f = u;  // identity: split the field itself
-                    store_split(r.out_hi + c * r.bs_out, r.out_lo + c * r.bs_out, r.out_lo2 + c * r.bs_out, oo, f,
-                                r.split);
+                    store_split(r.out_hi, r.out_lo, r.out_lo2, oo + c * r.bs_out, f, r.split);
                 }
                 break;
         }
