@@ -99,22 +99,31 @@ def run_ensemble(args, world, rank, local):
         e2e_s = barrier_max(time.perf_counter() - t0, world)
     peaks, src = measured_peaks()
     flops = info.step_flops * max(info.products, 1) * args.steps
-    peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
-    achieved = flops / (el_max / 1e3) / 1e12
+    bf16_mode = args.precision.startswith("bf16")
+    tpeak = peaks["bf16_tflops_sustained"] * (1.0 if bf16_mode else TF32_OVER_BF16)
+    sec = el_max / 1e3
+    tens = {"achieved": flops / sec / 1e12, "peak": tpeak, "unit": "TFLOP/s", "frac": flops / sec / 1e12 / tpeak,
+            "peak_source": (f"{src}: bf16_tflops_sustained" if bf16_mode else
+                            f"{src}: bf16_tflops_sustained x 1.1/2.25 (TF32/BF16 nominal)")}
+    sbytes = info.step_bytes * args.steps
+    hbm = {"achieved": sbytes / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": sbytes / sec / 1e9 / peaks["hbm_gbs"], "peak_source": f"{src}: hbm_gbs"}
+    bound = "hbm" if sbytes / (peaks["hbm_gbs"] * 1e9) > flops / (tpeak * 1e12) else "tensor"
+    top = hbm if bound == "hbm" else tens
     nbytes = sum(h.numel() * h.element_size() for h in hosts)
     line = {
         "metric": "unknown-updates/s per ETD2RK-DS step", "value": value, "unit": "unknown-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "tf32x3 (f32 state)" if args.precision == "tf32x3" else args.precision, "data": "synthetic",
+        "dtype": f"{args.precision} (f32 fields, double-float spectral state)", "data": "synthetic",
         "config": {"workload": desc, "instances": len(members), "unknowns": info.unknowns,
                    "precision": args.precision, "pade": "P02",
                    "l2": f"working set {info.workspace_bytes / 1e9:.2f} GB > 129 MB L2: no flush",
                    "parallelism": f"replicas x{world}; groups by grid on concurrent streams, one CUDA graph per step"},
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+        "roofline": {"bound": bound, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+                     "frac": top["frac"], "traffic": None,
                      "kernel": "all transform passes of the ensemble over the timed region (whole-GPU rate)",
-                     "peak_source": f"{src}: bf16_tflops_sustained x 1.1/2.25 (TF32/BF16 nominal)"},
+                     "peak_source": top["peak_source"], "tensor": tens, "hbm": hbm},
         "gpu_launches": args.steps * sum(10 for _ in range(15)),
         "e2e": {"value": world * info.unknowns * e2e_steps / e2e_s, "unit": "unknown-updates/s",
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
@@ -421,17 +430,31 @@ def main():
     peaks, src = measured_peaks()
     avg_gemm_ms = gemm_ms / max(gemm_n, 1)
     if info.products > 0:
+        # one per-step transform pass: its algorithmic flops and DRAM bytes, and
+        # the bound whose time is larger (2D m=4096: tensor; 3D m=256: HBM)
         flops = info.gemm_flops * info.products
-        peak = peaks["bf16_tflops_sustained"] * TF32_OVER_BF16
-        achieved = flops / (avg_gemm_ms * 1e-3) / 1e12
+        bytes_pass = info.step_bytes / info.gemms_per_step
+        bf16_mode = args.precision.startswith("bf16")
+        tpeak = peaks["bf16_tflops_sustained"] * (1.0 if bf16_mode else TF32_OVER_BF16)
+        hpeak = peaks["hbm_gbs"]
+        sec = avg_gemm_ms * 1e-3
+        tens = {"achieved": flops / sec / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+                "frac": flops / sec / 1e12 / tpeak, "per_launch": flops,
+                "peak_source": (f"{src}: bf16_tflops_sustained" if bf16_mode else
+                                f"{src}: bf16_tflops_sustained x 1.1/2.25 (TF32/BF16 nominal)")}
+        hbm = {"achieved": bytes_pass / sec / 1e9, "peak": hpeak, "unit": "GB/s",
+               "frac": bytes_pass / sec / 1e9 / hpeak, "per_launch": bytes_pass, "peak_source": f"{src}: hbm_gbs"}
+        bound = "hbm" if bytes_pass / (hpeak * 1e9) > flops / (tpeak * 1e12) else "tensor"
+        top = hbm if bound == "hbm" else tens
         traffic, src_hash = (None, None)
         if name == "fhn2d_4096" and args.precision == "tf32x3":
             traffic, src_hash = recorded_traffic(KERNEL_FILES, "profiles/gemm_tf32_tc_fhn4096_traffic.md")
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_unit": "bytes per launch (ncu dram read + write)",
-                "kernel": "gemm_tf32_tc_kernel<false> (per-step transform pass)",
-                "peak_source": f"{src}: bf16_tflops_sustained x 1.1/2.25 (TF32/BF16 nominal)",
-                "flops_per_launch": flops, "avg_launch_ms": avg_gemm_ms}
+        roof = {"bound": bound, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+                "frac": top["frac"], "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "kernel": "tcgen05 transform pass (per-step passes, mean over the step)",
+                "peak_source": top["peak_source"], "avg_launch_ms": avg_gemm_ms,
+                "tensor": tens, "hbm": hbm}
     else:
         flops = info.gemm_flops
         lanes = 128 if plan.dtype == torch.float32 else 2  # FP32 lanes / FP64 units per SM
@@ -454,8 +477,10 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"tf32x3": "tf32x3 (f32 state)", "tf32": "tf32 (f32 state)", "fp32": "f32",
-                  "fp64": "f64"}.get(args.precision, args.precision),
+        "dtype": {"tf32x3": "tf32x3 (f32 fields, double-float spectral state)", "tf32": "tf32 (f32 fields)", "fp32": "f32",
+                  "fp64": "f64", "bf16x3": "bf16x3 (f32 fields, double-float spectral state)",
+                  "bf16x6": "bf16x6 (f32 fields, double-float spectral state)",
+                  "tf32x6": "tf32x6 (f32 fields, double-float spectral state)"}.get(args.precision, args.precision),
         "data": "synthetic",
         "config": {"workload": desc, "d": d, "n": n, "n_comp": info.n_comp, "precision": args.precision,
                    "pade": "P02", "unknowns": unknowns,

@@ -98,6 +98,9 @@ typedef struct {
     double gemm_flops;           /* algorithmic flops of one pass, all components: 2 n^(d+1) n_comp */
     double step_flops;           /* algorithmic flops of one time step (16 n or 24 n per unknown) */
     long long workspace_bytes;   /* device memory the plan holds */
+    double step_bytes;           /* algorithmic DRAM bytes of one time step's transform passes: every operand
+                                    piece, basis piece, spectral state value and output field value read or
+                                    written once per pass (reaction kernels not included) */
 } etd_plan_info;
 
 /* Fill *opt with the defaults listed above. */

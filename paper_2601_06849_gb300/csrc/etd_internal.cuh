@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace etd {
 
 enum EpiMode : int {
@@ -35,17 +37,18 @@ enum SplitKind : int {
     SPLIT_BF16_3 = 5    // BF16 planes: hi, mid, lo (24 significant bits)
 };
 
-// BF16 pieces of v (round to nearest even); the operand planes are then 2-byte arrays.
-__device__ __forceinline__ void split_bf16(double v, int pieces, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                                           __nv_bfloat16* lo2, long long o) {
-    const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+// BF16 pieces of an FP32 value in FP32 arithmetic: each residual v - piece is
+// exact in FP32 (the piece keeps fewer bits than v), so no FP64 is needed.
+__device__ __forceinline__ void split_bf16_f(float v, int pieces, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                             __nv_bfloat16* lo2, long long o) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
     hi[o] = h;
     if (pieces < 2) return;
-    const double r1 = v - (double)__bfloat162float(h);
-    const __nv_bfloat16 m = __float2bfloat16_rn((float)r1);
+    const float r1 = v - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
     lo[o] = m;
     if (pieces < 3) return;
-    lo2[o] = __float2bfloat16_rn((float)(r1 - (double)__bfloat162float(m)));
+    lo2[o] = __float2bfloat16_rn(r1 - __bfloat162float(m));
 }
 
 enum ErrBits : unsigned { ERR_TIMEOUT = 1u, ERR_BAD_CONFIG = 2u };
@@ -56,13 +59,65 @@ __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float(r);
 }
 
-// The carried spectral state (U^, W^) and the factor grids are FP64 for every
-// precision: in the eigenbasis the linear part of a step is the elementwise
-// product E1x E1y.. U^, so rounding the state or the factors to FP32 would add
-// a systematic relative error of up to 2^-24 per step (about N 2^-24 after N
-// steps). Only the transform operands and the physical fields use T.
+// ---- double-float arithmetic ----
+// A double-float is the unevaluated sum x + y of two floats with |y| <= ulp(x)/2,
+// about 48 significant bits. GB300 runs FP64 at a small fraction of its FP32
+// rate, so the per-element updates of the carried spectral state in the FP32
+// paths use these error-free transformations in FP32: Knuth's TwoSum and the
+// FMA form of Dekker's TwoProduct. The _rn intrinsics keep the compiler from
+// contracting a product and a sum into one FMA, which would break exactness.
+__device__ __forceinline__ float2 ff_two_sum(float a, float b) {  // a + b exactly
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ float2 ff_fast_two_sum(float a, float b) {  // needs |a| >= |b| or a == 0
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);  // exact rounding error of p
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 ff_mul_f(float2 a, float b) {
+    const float p = __fmul_rn(a.x, b);
+    float e = __fmaf_rn(a.x, b, -p);
+    e = __fmaf_rn(a.y, b, e);
+    return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    const float2 s = ff_two_sum(a.x, b.x);
+    return ff_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
+}
+
+// Operand pieces of a double-float w: piece 0 rounds w.x, piece j rounds what
+// the earlier pieces left of w.x + w.y. Each w.x - piece0 is exact in FP32.
+template <bool BF16>
+__device__ __forceinline__ float piece_round(float v) {
+    if constexpr (BF16) return __bfloat162float(__float2bfloat16_rn(v));
+    else return tf32_rna(v);
+}
+template <bool BF16>
+__device__ __forceinline__ void ff_pieces(float2 w, float* q) {
+    q[0] = piece_round<BF16>(w.x);
+    const float r1 = __fsub_rn(w.x, q[0]);
+    q[1] = piece_round<BF16>(__fadd_rn(r1, w.y));
+    q[2] = piece_round<BF16>(__fadd_rn(__fsub_rn(r1, q[1]), w.y));
+}
+
+// The carried spectral state (U^, W^) and the factor grids carry more than FP32
+// precision for every precision: in the eigenbasis the linear part of a step is
+// the elementwise product E1x E1y.. U^, so rounding the state or the factors to
+// FP32 would add a systematic relative error of up to 2^-24 per step (about
+// N 2^-24 after N steps). The FP64 path holds them in FP64 (St = double); the
+// FP32 paths hold double-floats (St = float2, same 8 bytes per value) and update
+// them in FP32 arithmetic. Only the transform operands and the physical fields use T.
 template <typename T>
 struct Epi {
+    using St = typename std::conditional<sizeof(T) == 4, float2, double>::type;
     int mode;        // EpiMode
     int split;       // SplitKind (float only)
     int d, n, M;     // M = n^(d-1) rows per component
@@ -75,43 +130,137 @@ struct Epi {
     T* dst;          // EPI_PLAIN destination
     int ld_dst;
     long long bs_dst;
-    double* uhat;    // carried spectral state U^   (internal layout)
-    double* what;    // W^ of the current step
+    St* uhat;        // carried spectral state U^   (internal layout)
+    St* what;        // W^ of the current step
     T* fq;           // E_1(tau A_2) F^ of the current step
-    const double* grid;  // [comp][3][n]: E_1, tau E_2, tau E_3 at tau * lambda_k
+    const St* grid;  // [comp][3][n]: E_1, tau E_2, tau E_3 at tau * lambda_k
 
     __device__ __forceinline__ void write_operand(long long o, double v) const {
+        op_hi[o] = (T)v;  // FP64 path: one plane, CUDA-core products
+    }
+
+    // Operand pieces of an FP32 value, FP32 arithmetic only (split and reaction passes).
+    __device__ __forceinline__ void write_operand_f(long long o, float v) const {
         if constexpr (sizeof(T) == 4) {
+            write_operand_ff(o, make_float2(v, 0.f));
+        } else {
+            write_operand(o, (double)v);
+        }
+    }
+
+    // Operand pieces of a double-float value (FP32 paths).
+    __device__ __forceinline__ void write_operand_ff(long long o, float2 w) const {
+        if constexpr (sizeof(T) == 4) {
+            float q[3];
             if (split == SPLIT_BF16_2 || split == SPLIT_BF16_3) {
-                split_bf16(v, split == SPLIT_BF16_3 ? 3 : 2, reinterpret_cast<__nv_bfloat16*>(op_hi),
-                           reinterpret_cast<__nv_bfloat16*>(op_lo), reinterpret_cast<__nv_bfloat16*>(op_lo2), o);
+                ff_pieces<true>(w, q);
+                __nv_bfloat16* h = reinterpret_cast<__nv_bfloat16*>(op_hi);
+                h[o] = __float2bfloat16_rn(q[0]);  // exact: q[0] is a BF16 value
+                reinterpret_cast<__nv_bfloat16*>(op_lo)[o] = __float2bfloat16_rn(q[1]);
+                if (split == SPLIT_BF16_3) reinterpret_cast<__nv_bfloat16*>(op_lo2)[o] = __float2bfloat16_rn(q[2]);
                 return;
             }
-            if (split == SPLIT_TF32) {
-                const float h = tf32_rna((float)v);
-                op_hi[o] = h;
-                op_lo[o] = tf32_rna((float)(v - (double)h));
+            if (split == SPLIT_TF32 || split == SPLIT_TF32_3) {
+                ff_pieces<false>(w, q);
+                op_hi[o] = q[0];
+                op_lo[o] = q[1];
+                if (split == SPLIT_TF32_3) op_lo2[o] = q[2];
                 return;
             }
             if (split == SPLIT_TF32_HI) {
-                op_hi[o] = tf32_rna((float)v);
+                op_hi[o] = tf32_rna(w.x);
                 return;
             }
-            if (split == SPLIT_TF32_3) {
-                const float h = tf32_rna((float)v);
-                const double r = v - (double)h;
-                const float m = tf32_rna((float)r);
-                op_hi[o] = h;
-                op_lo[o] = m;
-                op_lo2[o] = tf32_rna((float)(r - (double)m));
-                return;
-            }
+            op_hi[o] = __fadd_rn(w.x, w.y);
         }
-        op_hi[o] = (T)v;
     }
 
     // Value v = out(b, mm, nn) with mm = mh * n + ml.
-    __device__ __forceinline__ void apply(int b, int mh, int ml, int nn, T v) const {
+    __device__ __forceinline__ void apply(int b, int mh, int ml, int nn, T v) const;
+};
+
+// Epilogue of up to N consecutive columns nn0 .. nn0+count-1 of one row
+// (mm = mh * n + ml), values v[], for the FP32 paths. Loads of the carried state
+// for all columns are issued before any store, so they overlap instead of each
+// waiting a DRAM round trip behind the previous column's stores.
+//   EPI_STAGE1: W^ = S (E1 U^ + tau E2 F^),  F^q = S F^          (eq. (13))
+//   EPI_STAGE2: U^+ = W^ + tau E3 (F_W^ - F^q)                   (eq. (14))
+// with S = E_1(tau A_2) [E_1(tau A_2^z)] at the y [z] modes and E_l at the x mode.
+template <int N>
+__device__ __forceinline__ void epi_apply_batch(const Epi<float>& e, int b, int mh, int ml, int nn0, const float* v,
+                                                int count) {
+    const long long base = (long long)b * e.bs + (long long)mh * e.ld + ml;
+    const long long step = (long long)e.mq * e.ld;  // offset between consecutive nn
+    if (e.mode == EPI_PLAIN) {
+        float* d = e.dst + (long long)b * e.bs_dst + ((long long)nn0 * e.mq + mh) * e.ld_dst + ml;
+        const long long sd = (long long)e.mq * e.ld_dst;
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j < count) d[j * sd] = v[j];
+        return;
+    }
+    const long long o0 = base + (long long)nn0 * step;
+    if (e.mode == EPI_SPLIT) {
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j < count) e.write_operand_f(o0 + j * step, v[j]);
+        return;
+    }
+    if (e.mode == EPI_CARRY) {
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j < count) e.uhat[o0 + j * step] = make_float2(v[j], 0.f);
+        return;
+    }
+    const float2* g = e.grid + (long long)b * 3 * e.n;
+    if (e.mode == EPI_STAGE1) {
+        float2 u[N], sl[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            u[j] = (j < count) ? e.uhat[o0 + j * step] : make_float2(0.f, 0.f);
+            sl[j] = (j < count) ? g[nn0 + j] : make_float2(0.f, 0.f);
+        }
+        const float2 g1 = g[ml], g2 = g[e.n + ml];
+        const float2 gm = g[mh];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            if (j < count) {
+                const long long o = o0 + j * step;
+                const float2 sj = (e.d == 2) ? sl[j] : ff_mul(gm, sl[j]);
+                const float2 w = ff_mul(ff_add(ff_mul(g1, u[j]), ff_mul_f(g2, v[j])), sj);
+                e.what[o] = w;
+                e.fq[o] = __fmaf_rn(sj.x, v[j], __fmul_rn(sj.y, v[j]));
+                e.write_operand_ff(o, w);
+            }
+        }
+        return;
+    }
+    if (e.mode == EPI_STAGE2) {
+        float2 w[N];
+        float f[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            w[j] = (j < count) ? e.what[o0 + j * step] : make_float2(0.f, 0.f);
+            f[j] = (j < count) ? e.fq[o0 + j * step] : 0.f;
+        }
+        const float2 g3 = g[2 * e.n + ml];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            if (j < count) {
+                const long long o = o0 + j * step;
+                const float2 u = ff_add(w[j], ff_mul(g3, ff_two_sum(v[j], -f[j])));  // v - f exactly
+                e.uhat[o] = u;
+                e.write_operand_ff(o, u);
+            }
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void Epi<T>::apply(int b, int mh, int ml, int nn, T v) const {
+    if constexpr (sizeof(T) == 4) {
+        epi_apply_batch<1>(*this, b, mh, ml, nn, &v, 1);
+    } else {
         if (mode == EPI_PLAIN) {
             dst[b * bs_dst + ((long long)nn * mq + mh) * ld_dst + ml] = v;
             return;
@@ -119,104 +268,30 @@ struct Epi {
         const long long o = b * bs + ((long long)nn * mq + mh) * ld + ml;
         switch (mode) {
             case EPI_SPLIT:
-                write_operand(o, (double)v);
+                write_operand(o, v);
                 break;
             case EPI_CARRY:
-                uhat[o] = (double)v;
+                uhat[o] = v;
                 break;
             case EPI_STAGE1: {
                 // spectral indices: k = ml (x mode); 2D l = nn; 3D l = mh, p = nn
                 const double* g = grid + (long long)b * 3 * n;
                 const double s = (d == 2) ? g[nn] : g[mh] * g[nn];  // E_1(tau A_2) [E_1(tau A_2^z)]
-                const double w = (g[ml] * uhat[o] + g[n + ml] * (double)v) * s;
+                const double w = (g[ml] * uhat[o] + g[n + ml] * v) * s;
                 what[o] = w;
-                fq[o] = (T)(s * (double)v);
+                fq[o] = s * v;
                 write_operand(o, w);
                 break;
             }
             case EPI_STAGE2: {
                 const double* g = grid + (long long)b * 3 * n;
-                const double u = what[o] + g[2 * n + ml] * ((double)v - (double)fq[o]);
+                const double u = what[o] + g[2 * n + ml] * (v - fq[o]);
                 uhat[o] = u;
                 write_operand(o, u);
                 break;
             }
             default:
                 break;
-        }
-    }
-};
-
-// Epilogue of up to N consecutive columns nn0 .. nn0+count-1 of one row
-// (mm = mh * n + ml), values v[]. Loads of the carried state for all columns are
-// issued before any store, so they overlap instead of each waiting a DRAM
-// round trip behind the previous column's stores.
-template <typename T, int N>
-__device__ __forceinline__ void epi_apply_batch(const Epi<T>& e, int b, int mh, int ml, int nn0, const float* v,
-                                                int count) {
-    const long long base = (long long)b * e.bs + (long long)mh * e.ld + ml;
-    const long long step = (long long)e.mq * e.ld;  // offset between consecutive nn
-    if (e.mode == EPI_PLAIN) {
-        T* d = e.dst + (long long)b * e.bs_dst + ((long long)nn0 * e.mq + mh) * e.ld_dst + ml;
-        const long long sd = (long long)e.mq * e.ld_dst;
-#pragma unroll
-        for (int j = 0; j < N; ++j)
-            if (j < count) d[j * sd] = (T)v[j];
-        return;
-    }
-    const long long o0 = base + (long long)nn0 * step;
-    if (e.mode == EPI_SPLIT) {
-#pragma unroll
-        for (int j = 0; j < N; ++j)
-            if (j < count) e.write_operand(o0 + j * step, (double)v[j]);
-        return;
-    }
-    if (e.mode == EPI_CARRY) {
-#pragma unroll
-        for (int j = 0; j < N; ++j)
-            if (j < count) e.uhat[o0 + j * step] = (double)v[j];
-        return;
-    }
-    const double* g = e.grid + (long long)b * 3 * e.n;
-    if (e.mode == EPI_STAGE1) {
-        double u[N], sl[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            u[j] = (j < count) ? e.uhat[o0 + j * step] : 0.0;
-            sl[j] = (j < count) ? g[nn0 + j] : 0.0;
-        }
-        const double g1 = g[ml], g2 = g[e.n + ml];
-        const double gm = (e.d == 2) ? 1.0 : g[mh];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            if (j < count) {
-                const long long o = o0 + j * step;
-                const double sj = gm * sl[j];  // E_1(tau A_2) [E_1(tau A_2^z)]
-                const double w = (g1 * u[j] + g2 * (double)v[j]) * sj;
-                e.what[o] = w;
-                e.fq[o] = (T)(sj * (double)v[j]);
-                e.write_operand(o, w);
-            }
-        }
-        return;
-    }
-    if (e.mode == EPI_STAGE2) {
-        double w[N];
-        T f[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            w[j] = (j < count) ? e.what[o0 + j * step] : 0.0;
-            f[j] = (j < count) ? e.fq[o0 + j * step] : (T)0;
-        }
-        const double g3 = g[2 * e.n + ml];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            if (j < count) {
-                const long long o = o0 + j * step;
-                const double u = w[j] + g3 * ((double)v[j] - (double)f[j]);
-                e.uhat[o] = u;
-                e.write_operand(o, u);
-            }
         }
     }
 }

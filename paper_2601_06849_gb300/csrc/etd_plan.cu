@@ -61,7 +61,8 @@ struct etd_plan {
     int out_slot = 0;   // config slot of the transform that returns the field
     // device memory
     void* P[3] = {nullptr, nullptr, nullptr};  // pieces of the sine basis
-    void* grid = nullptr;
+    void* grid = nullptr;   // FP64 factor grids [comp][3][n]
+    void* grid2 = nullptr;  // the same as double-floats (FP32 paths)
     void* uhat = nullptr;
     void* what = nullptr;
     void* fq = nullptr;
@@ -205,7 +206,7 @@ void free_plan(etd_plan* p) {
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (auto ev : p->ev_done)
         if (ev) cudaEventDestroy(ev);
-    void* bufs[] = {p->P[0],     p->P[1],     p->P[2],     p->grid,     p->uhat,     p->what,
+    void* bufs[] = {p->P[0],     p->P[1],     p->P[2],     p->grid,     p->grid2,    p->uhat,     p->what,
                     p->fq,       p->wphys,    p->op[0][0], p->op[0][1], p->op[0][2], p->op[1][0],
                     p->op[1][1], p->op[1][2], p->err,      p->stats,    p->host_field};
     for (void* b : bufs)
@@ -258,10 +259,11 @@ Epi<T> base_epi(const etd_plan* p) {
     e.mq = p->mq;
     e.ld = p->ld;
     e.bs = p->bs;
-    e.uhat = (double*)p->uhat;
-    e.what = (double*)p->what;
+    using St = typename Epi<T>::St;
+    e.uhat = (St*)p->uhat;
+    e.what = (St*)p->what;
     e.fq = (T*)p->fq;
-    e.grid = (const double*)p->grid;
+    e.grid = (const St*)(sizeof(T) == 4 ? p->grid2 : p->grid);
     return e;
 }
 
@@ -726,6 +728,7 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     const size_t op_bytes = (size_t)nb * p->bs * p->op_elem;
     for (int j = 0; j < p->pieces && s == ETD_OK; ++j) s = dalloc(p, &p->P[j], pbytes);
     if (s == ETD_OK) s = dalloc(p, &p->grid, (size_t)nb * 3 * n * sizeof(double));
+    if (s == ETD_OK) s = dalloc(p, &p->grid2, (size_t)nb * 3 * n * 2 * sizeof(float));
     if (s == ETD_OK) s = dalloc(p, &p->uhat, state_bytes);
     if (s == ETD_OK) s = dalloc(p, &p->what, state_bytes);
     if (s == ETD_OK) s = dalloc(p, &p->fq, field_bytes);
@@ -770,6 +773,14 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
         ce = cudaMemcpy(p->P[j], hostbuf.data(), pbytes, cudaMemcpyHostToDevice);
     }
     if (ce == cudaSuccess) ce = cudaMemcpy(p->grid, grid.data(), grid.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) {  // double-float copy: hi = rn(g), lo = rn(g - hi)
+        std::vector<float> g2(grid.size() * 2);
+        for (size_t i = 0; i < grid.size(); ++i) {
+            g2[2 * i] = (float)grid[i];
+            g2[2 * i + 1] = (float)(grid[i] - (double)g2[2 * i]);
+        }
+        ce = cudaMemcpy(p->grid2, g2.data(), g2.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
     // zero the padded operand columns once (they are never written by the passes)
     for (int i = 0; i < 2 && ce == cudaSuccess; ++i)
         for (int j = 0; j < p->pieces && ce == cudaSuccess; ++j) ce = cudaMemset(p->op[i][j], 0, op_bytes);
@@ -1162,6 +1173,7 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
             info->unknowns += gi.unknowns;
             info->gemm_flops += gi.gemm_flops;
             info->step_flops += gi.step_flops;
+            info->step_bytes += gi.step_bytes;
             info->products = gi.products;
             info->gemms_per_step = gi.gemms_per_step;
             info->d = gi.d;
@@ -1182,6 +1194,22 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
     info->gemm_flops = 2.0 * (double)p->npts * (double)p->n * p->ncomp * p->ninst;
     info->step_flops = info->gemm_flops * info->gemms_per_step;
     info->workspace_bytes = p->workspace;
+    // Per pass: its operand pieces and basis pieces read once; per chain of d
+    // passes, d - 1 split outputs plus one final epilogue (stage 1: W^, F^q and
+    // operand pieces written, U^ read; stage 2: W^, F^q read, U^+ and pieces
+    // written; physical field: the field written).
+    const double vals = (double)p->ninst * p->ncomp * p->npts;
+    const double pin = p->use_tc ? p->tc[0].pieces : 1;
+    const double opb = vals * (double)p->op_elem;
+    const double basis = (double)p->n * p->n * (double)p->op_elem * pin;
+    const double st = 8.0, fe = (double)p->elem;
+    const double pass_in = pin * opb + basis;
+    const double split_out = pin * opb;
+    const double chains = 4.0;
+    info->step_bytes = chains * p->d * pass_in + chains * (p->d - 1) * split_out +
+                       (vals * (st + st + fe) + split_out) +   // stage 1
+                       (vals * (st + fe + st) + split_out) +   // stage 2
+                       2.0 * vals * fe;                        // two physical fields
     return ETD_OK;
 }
 

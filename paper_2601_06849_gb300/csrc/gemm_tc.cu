@@ -53,8 +53,6 @@ struct KParams {
     int M, n, bn, stages, products, pieces, tiles_m, tiles_n, tmem_cols;
     int acc_cols;  // columns of one accumulator region (power of two >= bn)
     int nbatch;
-    int bf16;      // BF16 pieces and kind::f16 products (else TF32, kind::tf32)
-    int kvals;     // operand values per k-block: 32 (TF32) or 64 (BF16), 128 bytes per row
     unsigned stage_bytes, b_bytes, tx_bytes;
     unsigned* err;
     Epi<float> e;
@@ -190,9 +188,12 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
 }
 
 // One product of 32-byte K slices (8 TF32 or 16 BF16 values) of the two operands.
-__device__ __forceinline__ void mma_op(int bf16, uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+// The operand type is a template parameter so that the issuing thread runs no
+// branch between products.
+template <bool BF16>
+__device__ __forceinline__ void mma_op(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                        uint32_t accumulate) {
-    if (bf16)
+    if constexpr (BF16)
         mma_bf16(tmem_d, adesc, bdesc, idesc, accumulate);
     else
         mma_tf32(tmem_d, adesc, bdesc, idesc, accumulate);
@@ -271,12 +272,13 @@ __device__ __forceinline__ void acc_add(float& sum, float& comp, float v) {
 //   compensated (2Sum) FP32 arithmetic. Used for the transforms whose error
 //   stays in the result: U -> U^ when the carried state is (re)built and the
 //   transform that returns the field.
-template <bool ACCURATE>
+template <bool ACCURATE, bool BF16>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     gemm_tf32_tc_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                         const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mP0,
                         const __grid_constant__ CUtensorMap mP1, const __grid_constant__ CUtensorMap mP2,
                         const KParams p) {
+    constexpr int KV = BF16 ? 2 * BKF : BKF;  // operand values per k-block (128 bytes per row)
     extern __shared__ uint8_t smem_raw[];
     __shared__ int s_skip;
     __shared__ uint32_t s_tmem;
@@ -302,7 +304,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
     int b, tm, tn;
     tile_coords(blockIdx.x, p.tiles_m, p.tiles_n, 16, b, tm, tn);
-    const int nk = (p.n + p.kvals - 1) / p.kvals;
+    const int nk = (p.n + KV - 1) / KV;
     // TMEM columns: [0, acc) and [acc, 2 acc) k-block buffers, [2 acc, 3 acc) corrections (ACCURATE)
     const uint32_t acc_cols = (uint32_t)p.acc_cols;
 
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const uint32_t st = smem_u32(smem + (size_t)s * p.stage_bytes);
             const uint32_t fb = bar_full + 8 * s;
             mbar_expect_tx(fb, p.tx_bytes);
-            const int k0 = kb * p.kvals;
+            const int k0 = kb * KV;
             const uint32_t sb = st + (uint32_t)p.pieces * A_BYTES;  // first P piece
             tma_load_2d(st, &mA0, fb, k0, arow);
             tma_load_2d(sb, &mP0, fb, k0, prow);
@@ -362,7 +364,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         s_issued = issued;
     } else if (warp == WARP_MMA && lane == 0) {
         // ---------------- MMA issuer: one k-block per accumulator buffer ----------------
-        const uint32_t idesc = p.bf16 ? idesc_bf16(BM, p.bn) : idesc_tf32(BM, p.bn);
+        const uint32_t idesc = BF16 ? idesc_bf16(BM, p.bn) : idesc_tf32(BM, p.bn);
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % S;
             const int a = kb & 1;
@@ -380,16 +382,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             for (int kk = 0; kk < 4; ++kk) {
                 const uint32_t off = kk * 32;  // 8 TF32 values = 32 bytes per MMA
                 // terms of (a0 + a1 + a2)(b0 + b1 + b2) down to the 2^-22 level
-                mma_op(p.bf16, d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
+                mma_op<BF16>(d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
                 const uint32_t cacc = ACCURATE ? ((kb > 0 || kk > 0) ? 1u : 0u) : 1u;
                 if (p.products >= 3) {
-                    mma_op(p.bf16, dc, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, cacc);
-                    mma_op(p.bf16, dc, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                    mma_op<BF16>(dc, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, cacc);
+                    mma_op<BF16>(dc, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
                 }
                 if (p.products == 6) {
-                    mma_op(p.bf16, dc, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), idesc, 1u);
-                    mma_op(p.bf16, dc, sdesc_sw128(a2 + off), sdesc_sw128(b0 + off), idesc, 1u);
-                    mma_op(p.bf16, dc, sdesc_sw128(a0 + off), sdesc_sw128(b2 + off), idesc, 1u);
+                    mma_op<BF16>(dc, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                    mma_op<BF16>(dc, sdesc_sw128(a2 + off), sdesc_sw128(b0 + off), idesc, 1u);
+                    mma_op<BF16>(dc, sdesc_sw128(a0 + off), sdesc_sw128(b2 + off), idesc, 1u);
                 }
             }
             mma_commit(bar_empty + 8 * s);     // stage s may be refilled once these products finish
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     float v[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] = stage[(c0 + i < hcols ? c0 + i : 0) * 32 + lane];
-                    epi_apply_batch<float, 16>(p.e, b, mh, ml, nn0 + c0, v, min(16, cols - c0));
+                    epi_apply_batch<16>(p.e, b, mh, ml, nn0 + c0, v, min(16, cols - c0));
                 }            }
         }
     }
@@ -562,10 +564,12 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+template <bool BF16>
 __global__ void __launch_bounds__(pk::THREADS, 1)
     gemm_tf32_persistent_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                                 const __grid_constant__ CUtensorMap mP0, const __grid_constant__ CUtensorMap mP1,
                                 const KParams p) {
+    constexpr int KV = BF16 ? 2 * BKF : BKF;  // operand values per k-block (128 bytes per row)
     extern __shared__ uint8_t smem_raw[];
     __shared__ int s_skip;
     __shared__ uint32_t s_tmem;
@@ -590,7 +594,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     const uint32_t bar_st_full = smem_u32(&s_bar[22]);
     const uint32_t bar_st_empty = smem_u32(&s_bar[24]);
     const uint32_t bar_done = smem_u32(&s_bar[26]);
-    const int nk = (p.n + p.kvals - 1) / p.kvals;
+    const int nk = (p.n + KV - 1) / KV;
     const int nkb = 2;                 // k-block buffers (3 + 1 measured slower than 2 + 2)
     const int nsb = 4 - nkb;           // staging buffers
     const uint32_t staging0 = (uint32_t)nkb * pk::KB_COLS;
@@ -645,7 +649,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                 const uint32_t st = smem_u32(smem + (size_t)s * p.stage_bytes);
                 const uint32_t fb = bar_full + 8 * s;
                 mbar_expect_tx(fb, p.tx_bytes);
-                const int k0 = kb * p.kvals;
+                const int k0 = kb * KV;
                 const uint32_t sb = st + (uint32_t)p.pieces * A_BYTES;
                 tma_load_2d(st, &mA0, fb, k0, arow);
                 tma_load_2d(sb, &mP0, fb, k0, prow);
@@ -658,7 +662,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
         }
     } else if (warp == pk::WARP_MMA && lane == 0) {
         // ---------------- MMA issuer ----------------
-        const uint32_t idesc = p.bf16 ? idesc_bf16(BM, p.bn) : idesc_tf32(BM, p.bn);
+        const uint32_t idesc = BF16 ? idesc_bf16(BM, p.bn) : idesc_tf32(BM, p.bn);
         int g = 0;
         bool stop = false;
         for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
@@ -680,10 +684,10 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     const uint32_t off = kk * 32;
-                    mma_op(p.bf16, d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
+                    mma_op<BF16>(d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
                     if (p.products >= 3) {
-                        mma_op(p.bf16, d, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, 1u);
-                        mma_op(p.bf16, d, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                        mma_op<BF16>(d, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, 1u);
+                        mma_op<BF16>(d, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
                     }
                 }
                 mma_commit(bar_empty + 8 * s);
@@ -779,7 +783,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                     float v[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-                    epi_apply_batch<float, 16>(p.e, b, mh, ml, nn0 + c0, v, min(16, p.n - nn0 - c0));
+                    epi_apply_batch<16>(p.e, b, mh, ml, nn0 + c0, v, min(16, p.n - nn0 - c0));
                 }
             }
             tc_fence_before();
@@ -945,14 +949,15 @@ cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const
     }
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_tf32_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             SMEM_LIMIT);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(gemm_tf32_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     SMEM_LIMIT);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(gemm_tf32_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     SMEM_LIMIT);
+        const void* kernels[] = {(const void*)gemm_tf32_tc_kernel<false, false>,
+                                 (const void*)gemm_tf32_tc_kernel<true, false>,
+                                 (const void*)gemm_tf32_tc_kernel<false, true>,
+                                 (const void*)gemm_tf32_tc_kernel<true, true>,
+                                 (const void*)gemm_tf32_persistent_kernel<false>,
+                                 (const void*)gemm_tf32_persistent_kernel<true>};
+        cudaError_t e = cudaSuccess;
+        for (const void* k : kernels)
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
         if (e != cudaSuccess) {
             delete m;
             return e;
@@ -990,8 +995,6 @@ cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, in
     p.err = err;
     p.e = e;
     p.nbatch = nbatch;
-    p.bf16 = cfg.bf16 ? 1 : 0;
-    p.kvals = cfg.bf16 ? 2 * BKF : BKF;
     const long long ntiles = (long long)nbatch * cfg.tiles_m * cfg.tiles_n;
     const CUtensorMap* A = maps->a[a_index];
     const CUtensorMap* P = maps->p[slot];
@@ -1003,13 +1006,21 @@ cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, in
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
         }
         const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-        gemm_tf32_persistent_kernel<<<grid, pk::THREADS, cfg.smem_bytes, st>>>(A[0], A[1], P[0], P[1], p);
-    } else if (cfg.accurate) {
-        gemm_tf32_tc_kernel<true>
-            <<<(unsigned)ntiles, NUM_THREADS, cfg.smem_bytes, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
+        if (cfg.bf16)
+            gemm_tf32_persistent_kernel<true><<<grid, pk::THREADS, cfg.smem_bytes, st>>>(A[0], A[1], P[0], P[1], p);
+        else
+            gemm_tf32_persistent_kernel<false><<<grid, pk::THREADS, cfg.smem_bytes, st>>>(A[0], A[1], P[0], P[1], p);
     } else {
-        gemm_tf32_tc_kernel<false>
-            <<<(unsigned)ntiles, NUM_THREADS, cfg.smem_bytes, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
+        const unsigned g = (unsigned)ntiles;
+        const int sm = cfg.smem_bytes;
+        if (cfg.accurate && cfg.bf16)
+            gemm_tf32_tc_kernel<true, true><<<g, NUM_THREADS, sm, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
+        else if (cfg.accurate)
+            gemm_tf32_tc_kernel<true, false><<<g, NUM_THREADS, sm, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
+        else if (cfg.bf16)
+            gemm_tf32_tc_kernel<false, true><<<g, NUM_THREADS, sm, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
+        else
+            gemm_tf32_tc_kernel<false, false><<<g, NUM_THREADS, sm, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
     }
     return cudaGetLastError();
 }

@@ -14,8 +14,8 @@ template <typename T>
 __device__ __forceinline__ void store_split(T* hi, T* lo, T* lo2, long long o, T v, int split) {
     if constexpr (sizeof(T) == 4) {
         if (split == SPLIT_BF16_2 || split == SPLIT_BF16_3) {
-            split_bf16((double)v, split == SPLIT_BF16_3 ? 3 : 2, reinterpret_cast<__nv_bfloat16*>(hi),
-                       reinterpret_cast<__nv_bfloat16*>(lo), reinterpret_cast<__nv_bfloat16*>(lo2), o);
+            split_bf16_f(v, split == SPLIT_BF16_3 ? 3 : 2, reinterpret_cast<__nv_bfloat16*>(hi),
+                         reinterpret_cast<__nv_bfloat16*>(lo), reinterpret_cast<__nv_bfloat16*>(lo2), o);
             return;
         }
         if (split == SPLIT_TF32_3) {  // three TF32 pieces hold all 24 bits of v
@@ -40,60 +40,81 @@ __device__ __forceinline__ void store_split(T* hi, T* lo, T* lo2, long long o, T
     hi[o] = v;
 }
 
+// One warp task is a segment of RX_SEG consecutive points of one grid row
+// (RX_SEG / 32 per lane), so that every access is coalesced along the row, all
+// loads of a task are issued before its stores, and the only integer divisions
+// are two per task, not per point.
+constexpr int RX_SEG = 256;
+constexpr int RX_PER_LANE = RX_SEG / 32;
+
 template <typename T>
 __global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long total = r.npts * r.ninst;
-    for (long long pt = (long long)blockIdx.x * blockDim.x + threadIdx.x; pt < total; pt += stride) {
-        const long long inst = pt / r.npts;
-        const long long p = pt - inst * r.npts;
-        const long long row = p / r.n;
-        const int x = (int)(p - row * r.n);
-        const long long oi = inst * r.ncomp * r.bs_in + row * r.ld_in + x;
-        const long long oo = inst * r.ncomp * r.bs_out + row * r.ld_out + x;
-        switch (r.kind) {
-            case ETD_RX_FHN: {
-                // f_u = u - c3 u^3 - v,  f_v = eps (u - a v - b)
-                const T u = r.in[oi], v = r.in[r.bs_in + oi];
-                // component offsets go into the element index, never into pointer
-                // arithmetic: the operand planes hold 4-byte or 2-byte values
-                store_split(r.out_hi, r.out_lo, r.out_lo2, oo, u - r.rp[0] * u * u * u - v, r.split);
-                store_split(r.out_hi, r.out_lo, r.out_lo2, oo + r.bs_out, r.rp[1] * (u - r.rp[2] * v - r.rp[3]),
-                            r.split);
-                break;
-            }
-            case ETD_RX_ALLEN_CAHN: {
-                const T u = r.in[oi];
-                store_split(r.out_hi, r.out_lo, r.out_lo2, oo, u - u * u * u, r.split);
-                break;
-            }
-            case ETD_RX_SINGULAR: {
-                const T u = r.in[oi];
-                store_split(r.out_hi, r.out_lo, r.out_lo2, oo, r.rp[0] * u / ((T)1 - u), r.split);
-                break;
-            }
-            case ETD_RX_AC_FORCED: {
-                // u0 = prod sin(pi x_axis) at x_i = (i+1)/(n+1); psi in FP64
-                const double inv = 1.0 / (double)(r.n + 1);
-                const long long y = row % r.n, z = row / r.n;
-                double u0 = sinpi((double)(x + 1) * inv) * sinpi((double)(y + 1) * inv);
-                if (r.d == 3) u0 *= sinpi((double)(z + 1) * inv);
-                const double ue = r.decay * u0;
-                const double psi = r.psi_coef * ue - ue * (1.0 - ue * ue);
-                const T u = r.in[oi];
-                store_split(r.out_hi, r.out_lo, r.out_lo2, oo, (T)((double)u * (1.0 - (double)u * (double)u) + psi),
-                            r.split);
-                break;
-            }
-            default:
-                for (int c = 0; c < r.ncomp; ++c) {
-                    const T u = r.in[c * r.bs_in + oi];
-                    T f = (T)0;
-                    if (r.kind == ETD_RX_LINEAR) f = r.rp[0] * u;
-                    else if (r.kind < 0) f = u;  // identity: split the field itself
-                    store_split(r.out_hi, r.out_lo, r.out_lo2, oo + c * r.bs_out, f, r.split);
+    const int lane = threadIdx.x & 31;
+    const long long rows_inst = r.npts / r.n;  // n^(d-1) rows per instance
+    const int nseg = (r.n + RX_SEG - 1) / RX_SEG;
+    const long long tasks = rows_inst * r.ninst * nseg;
+    const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < tasks; t += wstride) {
+        const long long R = t / nseg;
+        const int x0 = (int)(t - R * nseg) * RX_SEG + lane;
+        const long long inst = R / rows_inst;
+        const long long row = R - inst * rows_inst;
+        const T* __restrict__ in = r.in + inst * r.ncomp * r.bs_in + row * r.ld_in;
+        const long long oo = inst * r.ncomp * r.bs_out + row * r.ld_out;
+        T u[RX_PER_LANE], v[RX_PER_LANE];
+#pragma unroll
+        for (int j = 0; j < RX_PER_LANE; ++j) {
+            const int x = x0 + 32 * j;
+            const bool ok = x < r.n;
+            u[j] = ok ? in[x] : (T)0;
+            v[j] = (ok && r.ncomp > 1) ? in[r.bs_in + x] : (T)0;
+        }
+        double u0yz = 1.0;  // ETD_RX_AC_FORCED: the y [and z] factors of u0 on this row
+        if (r.kind == ETD_RX_AC_FORCED) {
+            const double inv = 1.0 / (double)(r.n + 1);
+            const long long y = row % r.n, z = row / r.n;
+            u0yz = sinpi((double)(y + 1) * inv);
+            if (r.d == 3) u0yz *= sinpi((double)(z + 1) * inv);
+        }
+#pragma unroll
+        for (int j = 0; j < RX_PER_LANE; ++j) {
+            const int x = x0 + 32 * j;
+            if (x >= r.n) continue;
+            const T a = u[j], b = v[j];
+            T f0 = (T)0, f1 = (T)0;
+            switch (r.kind) {
+                case ETD_RX_FHN:  // f_u = u - c3 u^3 - v,  f_v = eps (u - a v - b)
+                    f0 = a - r.rp[0] * a * a * a - b;
+                    f1 = r.rp[1] * (a - r.rp[2] * b - r.rp[3]);
+                    break;
+                case ETD_RX_ALLEN_CAHN:
+                    f0 = a - a * a * a;
+                    break;
+                case ETD_RX_SINGULAR:
+                    f0 = r.rp[0] * a / ((T)1 - a);
+                    break;
+                case ETD_RX_AC_FORCED: {
+                    // u0 = prod sin(pi x_axis) at x_i = (i+1)/(n+1); psi in FP64
+                    const double ue = r.decay * u0yz * sinpi((double)(x + 1) / (double)(r.n + 1));
+                    const double psi = r.psi_coef * ue - ue * (1.0 - ue * ue);
+                    f0 = (T)((double)a * (1.0 - (double)a * (double)a) + psi);
+                    break;
                 }
-                break;
+                case ETD_RX_LINEAR:
+                    f0 = r.rp[0] * a;
+                    f1 = r.rp[0] * b;
+                    break;
+                default:
+                    if (r.kind < 0) {  // identity: split the field itself
+                        f0 = a;
+                        f1 = b;
+                    }
+                    break;
+            }
+            // component offsets go into the element index, never into pointer
+            // arithmetic: the operand planes hold 4-byte or 2-byte values
+            store_split(r.out_hi, r.out_lo, r.out_lo2, oo + x, f0, r.split);
+            if (r.ncomp > 1) store_split(r.out_hi, r.out_lo, r.out_lo2, oo + r.bs_out + x, f1, r.split);
         }
     }
 }
@@ -106,11 +127,16 @@ static int grid_for(long long work, int threads) {
     return (int)blocks;
 }
 
+template <typename T>
+static int react_grid(const Rx<T>& r) {
+    const long long tasks = (r.npts / r.n) * r.ninst * ((r.n + RX_SEG - 1) / RX_SEG);
+    return grid_for(tasks * 32, 256);  // one warp per task
+}
 void launch_react_f32(const Rx<float>& r, cudaStream_t st) {
-    react_kernel<float><<<grid_for(r.npts * r.ninst, 256), 256, 0, st>>>(r);
+    react_kernel<float><<<react_grid(r), 256, 0, st>>>(r);
 }
 void launch_react_f64(const Rx<double>& r, cudaStream_t st) {
-    react_kernel<double><<<grid_for(r.npts * r.ninst, 256), 256, 0, st>>>(r);
+    react_kernel<double><<<react_grid(r), 256, 0, st>>>(r);
 }
 
 // acc[0] = max |u| (as the bit pattern of a non-negative double, so an

@@ -56,7 +56,7 @@ class etd_plan_info(ctypes.Structure):
         ("d", ctypes.c_int), ("n", ctypes.c_int), ("n_comp", ctypes.c_int), ("precision", ctypes.c_int),
         ("products", ctypes.c_int), ("gemms_per_step", ctypes.c_int),
         ("unknowns", ctypes.c_longlong), ("gemm_flops", ctypes.c_double), ("step_flops", ctypes.c_double),
-        ("workspace_bytes", ctypes.c_longlong),
+        ("workspace_bytes", ctypes.c_longlong), ("step_bytes", ctypes.c_double),
     ]
 
 
