@@ -108,13 +108,20 @@ __device__ __forceinline__ void ff_pieces(float2 w, float* q) {
     q[2] = piece_round<BF16>(__fadd_rn(__fsub_rn(r1, q[1]), w.y));
 }
 
-// The carried spectral state (U^, W^) and the factor grids carry more than FP32
+// The carried spectral state and the factor grids carry more than FP32
 // precision for every precision: in the eigenbasis the linear part of a step is
 // the elementwise product E1x E1y.. U^, so rounding the state or the factors to
 // FP32 would add a systematic relative error of up to 2^-24 per step (about
 // N 2^-24 after N steps). The FP64 path holds them in FP64 (St = double); the
 // FP32 paths hold double-floats (St = float2, same 8 bytes per value) and update
 // them in FP32 arithmetic. Only the transform operands and the physical fields use T.
+//
+// The two Hadamard stages of a step (eq. (13)-(14) in the eigenbasis, with
+// S = E_1(tau A_2) [E_1(tau A_2^z)] at the y [z] modes and E_l at the x mode):
+//   stage 1, value F^ = T f(U):   W^ = S (E1 U^ + tau E2 F^),  Z = W^ - tau E3 S F^
+//   stage 2, value F_W^ = T f(W): U^+ = Z + tau E3 F_W^
+// Z is eq. (14)'s W^ + tau E3 (F_W^ - S F^) with its F_W^-free part formed in
+// stage 1, so stage 2 reads one state value per point instead of W^ and S F^.
 template <typename T>
 struct Epi {
     using St = typename std::conditional<sizeof(T) == 4, float2, double>::type;
@@ -131,8 +138,7 @@ struct Epi {
     int ld_dst;
     long long bs_dst;
     St* uhat;        // carried spectral state U^   (internal layout)
-    St* what;        // W^ of the current step
-    T* fq;           // E_1(tau A_2) F^ of the current step
+    St* zhat;        // Z of the current step (stage 1 -> stage 2)
     const St* grid;  // [comp][3][n]: E_1, tau E_2, tau E_3 at tau * lambda_k
 
     __device__ __forceinline__ void write_operand(long long o, double v) const {
@@ -175,20 +181,33 @@ struct Epi {
         }
     }
 
+    // Does this epilogue read carried state (U^ in stage 1, Z in stage 2)?
+    __device__ __forceinline__ bool reads_state() const { return mode == EPI_STAGE1 || mode == EPI_STAGE2; }
+    __device__ __forceinline__ const St* state_in() const { return mode == EPI_STAGE1 ? uhat : zhat; }
+
     // Value v = out(b, mm, nn) with mm = mh * n + ml.
     __device__ __forceinline__ void apply(int b, int mh, int ml, int nn, T v) const;
 };
 
-// Epilogue of up to N consecutive columns nn0 .. nn0+count-1 of one row
-// (mm = mh * n + ml), values v[], for the FP32 paths. Loads of the carried state
-// for all columns are issued before any store, so they overlap instead of each
-// waiting a DRAM round trip behind the previous column's stores.
-//   EPI_STAGE1: W^ = S (E1 U^ + tau E2 F^),  F^q = S F^          (eq. (13))
-//   EPI_STAGE2: U^+ = W^ + tau E3 (F_W^ - F^q)                   (eq. (14))
-// with S = E_1(tau A_2) [E_1(tau A_2^z)] at the y [z] modes and E_l at the x mode.
+// State values of up to N consecutive columns nn0 .. nn0+count-1 of one row
+// (mm = mh * n + ml) for the epilogue below. Callers issue this for the next
+// batch of columns before they apply the current one, so the loads overlap the
+// arithmetic and stores of the current batch.
+template <int N>
+__device__ __forceinline__ void epi_load_state(const Epi<float>& e, int b, int mh, int ml, int nn0, int count,
+                                               float2 (&st)[N]) {
+    if (!e.reads_state()) return;
+    const float2* src = e.state_in() + (long long)b * e.bs + ((long long)nn0 * e.mq + mh) * e.ld + ml;
+    const long long step = (long long)e.mq * e.ld;  // offset between consecutive nn
+#pragma unroll
+    for (int j = 0; j < N; ++j) st[j] = (j < count) ? src[j * step] : make_float2(0.f, 0.f);
+}
+
+// Epilogue of up to N consecutive columns of one row, values v[], state st[]
+// from epi_load_state (FP32 paths).
 template <int N>
 __device__ __forceinline__ void epi_apply_batch(const Epi<float>& e, int b, int mh, int ml, int nn0, const float* v,
-                                                int count) {
+                                                int count, const float2 (&st)[N]) {
     const long long base = (long long)b * e.bs + (long long)mh * e.ld + ml;
     const long long step = (long long)e.mq * e.ld;  // offset between consecutive nn
     if (e.mode == EPI_PLAIN) {
@@ -213,42 +232,31 @@ __device__ __forceinline__ void epi_apply_batch(const Epi<float>& e, int b, int 
         return;
     }
     const float2* g = e.grid + (long long)b * 3 * e.n;
+    const float2 g3 = g[2 * e.n + ml];
     if (e.mode == EPI_STAGE1) {
-        float2 u[N], sl[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            u[j] = (j < count) ? e.uhat[o0 + j * step] : make_float2(0.f, 0.f);
-            sl[j] = (j < count) ? g[nn0 + j] : make_float2(0.f, 0.f);
-        }
         const float2 g1 = g[ml], g2 = g[e.n + ml];
         const float2 gm = g[mh];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             if (j < count) {
                 const long long o = o0 + j * step;
-                const float2 sj = (e.d == 2) ? sl[j] : ff_mul(gm, sl[j]);
-                const float2 w = ff_mul(ff_add(ff_mul(g1, u[j]), ff_mul_f(g2, v[j])), sj);
-                e.what[o] = w;
-                e.fq[o] = __fmaf_rn(sj.x, v[j], __fmul_rn(sj.y, v[j]));
+                const float2 sl = g[nn0 + j];
+                const float2 sj = (e.d == 2) ? sl : ff_mul(gm, sl);
+                const float2 w = ff_mul(ff_add(ff_mul(g1, st[j]), ff_mul_f(g2, v[j])), sj);
+                const float2 sf = ff_mul_f(sj, v[j]);  // S F^
+                const float2 t = ff_mul(g3, sf);
+                e.zhat[o] = ff_add(w, make_float2(-t.x, -t.y));
                 e.write_operand_ff(o, w);
             }
         }
         return;
     }
     if (e.mode == EPI_STAGE2) {
-        float2 w[N];
-        float f[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            w[j] = (j < count) ? e.what[o0 + j * step] : make_float2(0.f, 0.f);
-            f[j] = (j < count) ? e.fq[o0 + j * step] : 0.f;
-        }
-        const float2 g3 = g[2 * e.n + ml];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             if (j < count) {
                 const long long o = o0 + j * step;
-                const float2 u = ff_add(w[j], ff_mul(g3, ff_two_sum(v[j], -f[j])));  // v - f exactly
+                const float2 u = ff_add(st[j], ff_mul_f(g3, v[j]));
                 e.uhat[o] = u;
                 e.write_operand_ff(o, u);
             }
@@ -259,13 +267,16 @@ __device__ __forceinline__ void epi_apply_batch(const Epi<float>& e, int b, int 
 template <typename T>
 __device__ __forceinline__ void Epi<T>::apply(int b, int mh, int ml, int nn, T v) const {
     if constexpr (sizeof(T) == 4) {
-        epi_apply_batch<1>(*this, b, mh, ml, nn, &v, 1);
+        float2 st[1];
+        epi_load_state<1>(*this, b, mh, ml, nn, 1, st);
+        epi_apply_batch<1>(*this, b, mh, ml, nn, &v, 1, st);
     } else {
         if (mode == EPI_PLAIN) {
             dst[b * bs_dst + ((long long)nn * mq + mh) * ld_dst + ml] = v;
             return;
         }
         const long long o = b * bs + ((long long)nn * mq + mh) * ld + ml;
+        const double* g = grid + (long long)b * 3 * n;
         switch (mode) {
             case EPI_SPLIT:
                 write_operand(o, v);
@@ -275,17 +286,14 @@ __device__ __forceinline__ void Epi<T>::apply(int b, int mh, int ml, int nn, T v
                 break;
             case EPI_STAGE1: {
                 // spectral indices: k = ml (x mode); 2D l = nn; 3D l = mh, p = nn
-                const double* g = grid + (long long)b * 3 * n;
                 const double s = (d == 2) ? g[nn] : g[mh] * g[nn];  // E_1(tau A_2) [E_1(tau A_2^z)]
                 const double w = (g[ml] * uhat[o] + g[n + ml] * v) * s;
-                what[o] = w;
-                fq[o] = s * v;
+                zhat[o] = w - g[2 * n + ml] * (s * v);
                 write_operand(o, w);
                 break;
             }
             case EPI_STAGE2: {
-                const double* g = grid + (long long)b * 3 * n;
-                const double u = what[o] + g[2 * n + ml] * (v - fq[o]);
+                const double u = zhat[o] + g[2 * n + ml] * v;
                 uhat[o] = u;
                 write_operand(o, u);
                 break;

@@ -64,8 +64,7 @@ struct etd_plan {
     void* grid = nullptr;   // FP64 factor grids [comp][3][n]
     void* grid2 = nullptr;  // the same as double-floats (FP32 paths)
     void* uhat = nullptr;
-    void* what = nullptr;
-    void* fq = nullptr;
+    void* zhat = nullptr;  // Z between the two stages of a step
     void* wphys = nullptr;
     void* op[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // operand buffers x pieces
     unsigned* err = nullptr;
@@ -206,8 +205,8 @@ void free_plan(etd_plan* p) {
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (auto ev : p->ev_done)
         if (ev) cudaEventDestroy(ev);
-    void* bufs[] = {p->P[0],     p->P[1],     p->P[2],     p->grid,     p->grid2,    p->uhat,     p->what,
-                    p->fq,       p->wphys,    p->op[0][0], p->op[0][1], p->op[0][2], p->op[1][0],
+    void* bufs[] = {p->P[0],     p->P[1],     p->P[2],     p->grid,     p->grid2,    p->uhat,     p->zhat,
+                    p->wphys,    p->op[0][0], p->op[0][1], p->op[0][2], p->op[1][0],
                     p->op[1][1], p->op[1][2], p->err,      p->stats,    p->host_field};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -261,8 +260,7 @@ Epi<T> base_epi(const etd_plan* p) {
     e.bs = p->bs;
     using St = typename Epi<T>::St;
     e.uhat = (St*)p->uhat;
-    e.what = (St*)p->what;
-    e.fq = (T*)p->fq;
+    e.zhat = (St*)p->zhat;
     e.grid = (const St*)(sizeof(T) == 4 ? p->grid2 : p->grid);
     return e;
 }
@@ -730,8 +728,7 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     if (s == ETD_OK) s = dalloc(p, &p->grid, (size_t)nb * 3 * n * sizeof(double));
     if (s == ETD_OK) s = dalloc(p, &p->grid2, (size_t)nb * 3 * n * 2 * sizeof(float));
     if (s == ETD_OK) s = dalloc(p, &p->uhat, state_bytes);
-    if (s == ETD_OK) s = dalloc(p, &p->what, state_bytes);
-    if (s == ETD_OK) s = dalloc(p, &p->fq, field_bytes);
+    if (s == ETD_OK) s = dalloc(p, &p->zhat, state_bytes);
     if (s == ETD_OK) s = dalloc(p, &p->wphys, field_bytes);
     for (int i = 0; i < 2 && s == ETD_OK; ++i)
         for (int j = 0; j < p->pieces && s == ETD_OK; ++j) s = dalloc(p, &p->op[i][j], op_bytes);
@@ -1195,9 +1192,9 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
     info->step_flops = info->gemm_flops * info->gemms_per_step;
     info->workspace_bytes = p->workspace;
     // Per pass: its operand pieces and basis pieces read once; per chain of d
-    // passes, d - 1 split outputs plus one final epilogue (stage 1: W^, F^q and
-    // operand pieces written, U^ read; stage 2: W^, F^q read, U^+ and pieces
-    // written; physical field: the field written).
+    // passes, d - 1 split outputs plus one final epilogue (stage 1: U^ read, Z
+    // and operand pieces written; stage 2: Z read, U^+ and pieces written;
+    // physical field: the field written).
     const double vals = (double)p->ninst * p->ncomp * p->npts;
     const double pin = p->use_tc ? p->tc[0].pieces : 1;
     const double opb = vals * (double)p->op_elem;
@@ -1207,9 +1204,9 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
     const double split_out = pin * opb;
     const double chains = 4.0;
     info->step_bytes = chains * p->d * pass_in + chains * (p->d - 1) * split_out +
-                       (vals * (st + st + fe) + split_out) +   // stage 1
-                       (vals * (st + fe + st) + split_out) +   // stage 2
-                       2.0 * vals * fe;                        // two physical fields
+                       (vals * (st + st) + split_out) +   // stage 1: U^ read, Z written
+                       (vals * (st + st) + split_out) +   // stage 2: Z read, U^+ written
+                       2.0 * vals * fe;                   // two physical fields
     return ETD_OK;
 }
 

@@ -208,6 +208,19 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 
 // tcgen05.ld of 16 consecutive accumulator columns of this warp's 32 lanes;
 // asynchronous until tmem_wait16 on the same registers.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait8(uint32_t (&r)[8]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7])
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -479,12 +492,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const int mh = mm / p.n, ml = mm - mh * p.n;
                 const int nn0 = tn * p.bn + half * hcols;
                 const int cols = min(hcols, p.n - nn0);
+                // state loads of the next 16 columns go out before this batch's stores
+                float2 cur[16], nxt[16];
+                epi_load_state<16>(p.e, b, mh, ml, nn0, min(16, cols), cur);
                 for (int c0 = 0; c0 < cols; c0 += 16) {
+                    if (c0 + 16 < cols) epi_load_state<16>(p.e, b, mh, ml, nn0 + c0 + 16, min(16, cols - c0 - 16), nxt);
                     float v[16];
 #pragma unroll
                     for (int i = 0; i < 16; ++i) v[i] = stage[(c0 + i < hcols ? c0 + i : 0) * 32 + lane];
-                    epi_apply_batch<16>(p.e, b, mh, ml, nn0 + c0, v, min(16, cols - c0));
-                }            }
+                    epi_apply_batch<16>(p.e, b, mh, ml, nn0 + c0, v, min(16, cols - c0), cur);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
+                }
+            }
         }
     }
 
@@ -529,10 +549,11 @@ namespace pk {
 constexpr int BN = 128;
 constexpr int HALF = BN / 2;
 constexpr int NUM_DRAIN = 8;
-constexpr int NUM_STORE = 4;
-constexpr int WARP_TMA = 12;
-constexpr int WARP_MMA = 13;
-constexpr int THREADS = 14 * 32;
+constexpr int NUM_STORE = 8;            // two per TMEM lane quarter, one per column half
+constexpr int WARP_TMA = 16;
+constexpr int WARP_MMA = 17;
+constexpr int THREADS = 18 * 32;        // <= 112 registers per thread
+constexpr int EPI_COLS = 8;             // columns per epilogue batch of a store thread
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t KB_COLS = 128;        // one TMEM region (k-block or staging buffer)
 }  // namespace pk
@@ -716,19 +737,13 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                 tc_fence_after();
                 const uint32_t src = tmem + lane_off + (uint32_t)a * pk::KB_COLS;
 #pragma unroll
-                for (int c = 0; c < pk::HALF / 32; ++c) {
-                    if ((c + 1) * 32 <= hcols) {
-                        uint32_t r[32];
-                        tmem_ld32(src + (uint32_t)(c * 32), r);
-                        tmem_wait32(r);
-#pragma unroll
-                        for (int i = 0; i < 32; ++i) sum[c * 32 + i] += __uint_as_float(r[i]);
-                    } else if (c * 32 + 16 <= hcols) {
+                for (int c = 0; c < pk::HALF / 16; ++c) {
+                    if (c * 16 < hcols) {
                         uint32_t r[16];
-                        tmem_ld16(src + (uint32_t)(c * 32), r);
+                        tmem_ld16(src + (uint32_t)(c * 16), r);
                         tmem_wait16(r);
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) sum[c * 32 + i] += __uint_as_float(r[i]);
+                        for (int i = 0; i < 16; ++i) sum[c * 16 + i] += __uint_as_float(r[i]);
                     }
                 }
                 tc_fence_before();
@@ -762,7 +777,10 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
         }
     } else if (warp < pk::NUM_DRAIN + pk::NUM_STORE) {
         // ---------------- store warps: staging -> fused epilogue -> global ----------------
-        const int quarter = warp & 3;
+        // warp (quarter, half): TMEM lanes 32 quarter .. +31, columns half * bn/2 .. +bn/2
+        const int quarter = warp & 3, half = (warp - pk::NUM_DRAIN) >> 2;
+        const int hcols = p.bn / 2;
+        constexpr int EC = pk::EPI_COLS;
         int j = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
             int b, tm, tn;
@@ -770,21 +788,30 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
             const int sb = j % nsb;
             if (!warp_wait(bar_st_full + 8 * sb, (uint32_t)((j / nsb) & 1), abort_flag, p.err)) break;
             tc_fence_after();
-            const uint32_t src = tmem + ((uint32_t)(quarter * 32) << 16) + staging0 + (uint32_t)sb * pk::KB_COLS;
+            const uint32_t src =
+                tmem + ((uint32_t)(quarter * 32) << 16) + staging0 + (uint32_t)sb * pk::KB_COLS + (uint32_t)(half * hcols);
             const int mm = tm * BM + quarter * 32 + lane;
             const bool row_ok = mm < p.M;
             const int mh = mm / p.n, ml = mm - mh * p.n;
-            const int nn0 = tn * p.bn;
-            for (int c0 = 0; c0 < p.bn; c0 += 16) {
-                uint32_t r[16];
-                tmem_ld16(src + (uint32_t)c0, r);
-                tmem_wait16(r);
-                if (row_ok) {
-                    float v[16];
+            const int nn0 = tn * p.bn + half * hcols;
+            const int cols = min(hcols, p.n - nn0);  // may be <= 0 for the last column tile
+            // state loads of the next EC columns go out before this batch's stores
+            float2 cur[EC], nxt[EC];
+            if (row_ok && cols > 0) epi_load_state<EC>(p.e, b, mh, ml, nn0, min(EC, cols), cur);
+            for (int c0 = 0; c0 < hcols; c0 += EC) {
+                uint32_t r[EC];
+                tmem_ld8(src + (uint32_t)c0, r);
+                if (row_ok && c0 + EC < cols)
+                    epi_load_state<EC>(p.e, b, mh, ml, nn0 + c0 + EC, min(EC, cols - c0 - EC), nxt);
+                tmem_wait8(r);
+                if (row_ok && c0 < cols) {
+                    float v[EC];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-                    epi_apply_batch<16>(p.e, b, mh, ml, nn0 + c0, v, min(16, p.n - nn0 - c0));
+                    for (int i = 0; i < EC; ++i) v[i] = __uint_as_float(r[i]);
+                    epi_apply_batch<EC>(p.e, b, mh, ml, nn0 + c0, v, min(EC, cols - c0), cur);
                 }
+#pragma unroll
+                for (int i = 0; i < EC; ++i) cur[i] = nxt[i];
             }
             tc_fence_before();
             __syncwarp();
