@@ -46,16 +46,22 @@ typedef enum {
 
 /* Arithmetic of the eigen-transforms (the dense products with P). */
 enum {
-    ETD_PREC_FP64 = 0,   /* double state, FP64 CUDA-core products */
-    ETD_PREC_FP32 = 1,   /* float state, FP32 CUDA-core products */
-    ETD_PREC_TF32 = 2,   /* float state, one TF32 tensor-core product */
-    ETD_PREC_TF32X3 = 3, /* float fields, split TF32: hi*hi + hi*lo + lo*hi; the transform
-                            that returns the field uses the six-product split (default) */
+    ETD_PREC_FP64 = 0,   /* double fields and state, FP64 CUDA-core products */
+    ETD_PREC_FP32 = 1,   /* float fields, FP32 CUDA-core products */
+    ETD_PREC_TF32 = 2,   /* float fields, one TF32 tensor-core product */
+    ETD_PREC_TF32X3 = 3, /* float fields, split TF32: hi*hi + hi*lo + lo*hi (default) */
     ETD_PREC_BF16X3 = 4, /* float fields, BF16 hi/lo split, three products */
-    ETD_PREC_BF16X6 = 5, /* float fields, BF16 hi/mid/lo split, six products */
-    ETD_PREC_TF32X6 = 6  /* float fields, three-piece TF32 split, six products in every pass */
+    ETD_PREC_BF16X6 = 5, /* float fields, BF16 hi/mid/lo split, six products in every pass,
+                            correction products in their own accumulator (most accurate) */
+    ETD_PREC_TF32X6 = 6  /* float fields, TF32 hi/mid/lo split, six products, as BF16X6 */
 };
-/* Every precision keeps the carried spectral state and the factor grids in FP64. */
+/* In every split mode (X3, X6) the two transforms whose error stays in the
+ * result, U -> U^ when the carried spectral state is (re)built and the
+ * transform that returns the field, use three pieces, six products, a separate
+ * accumulator for the five correction products and compensated sums.
+ * The carried spectral state and the factor grids hold more than FP32
+ * precision: FP64 for ETD_PREC_FP64, double-float pairs (hi + lo, about 48
+ * bits) for every other precision. */
 
 /* Reaction f(t, u), evaluated pointwise. */
 enum {
@@ -218,7 +224,7 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info);
  * events on the plan stream. etd_kernel_times (after etd_sync) returns, for
  * kind 0 = transform passes of the time steps, 1 = pointwise reaction/split
  * kernels, 2 = the accurate transform passes (state rebuild and returned field,
- * ETD_PREC_TF32X3 only), the summed milliseconds and launch count since the
+ * the split modes only), the summed milliseconds and launch count since the
  * last call for that kind.
  */
 etd_status etd_set_timing(etd_plan* p, int enable);

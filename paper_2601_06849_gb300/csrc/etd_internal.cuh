@@ -92,6 +92,10 @@ __device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
     const float2 s = ff_two_sum(a.x, b.x);
     return ff_two_sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
 }
+__device__ __forceinline__ float2 ff_add_f(float2 a, float b) {  // a + b for a float b
+    const float2 s = ff_two_sum(a.x, b);
+    return ff_fast_two_sum(s.x, __fadd_rn(s.y, a.y));
+}
 
 // Operand pieces of a double-float w: piece 0 rounds w.x, piece j rounds what
 // the earlier pieces left of w.x + w.y. Each w.x - piece0 is exact in FP32.
@@ -231,10 +235,16 @@ __device__ __forceinline__ void epi_apply_batch(const Epi<float>& e, int b, int 
             if (j < count) e.uhat[o0 + j * step] = make_float2(v[j], 0.f);
         return;
     }
+    // The transformed reaction v carries the transform's relative error (about
+    // 2^-22 for split TF32), so its products with tau E2 and tau E3 are formed
+    // in FP32 (relative error 2^-24) and added to the double-float terms;
+    // E1 U^ and the products with S keep double-float precision.
     const float2* g = e.grid + (long long)b * 3 * e.n;
-    const float2 g3 = g[2 * e.n + ml];
+    const float g3 = g[2 * e.n + ml].x;
     if (e.mode == EPI_STAGE1) {
+        // W^ = S (E1 U^ + tau E2 F^),  Z = W^ - tau E3 S F^ = S (E1 U^ + (tau E2 - tau E3) F^)
         const float2 g1 = g[ml], g2 = g[e.n + ml];
+        const float g23 = __fsub_rn(g2.x, g3) + g2.y - g[2 * e.n + ml].y;
         const float2 gm = g[mh];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
@@ -242,21 +252,20 @@ __device__ __forceinline__ void epi_apply_batch(const Epi<float>& e, int b, int 
                 const long long o = o0 + j * step;
                 const float2 sl = g[nn0 + j];
                 const float2 sj = (e.d == 2) ? sl : ff_mul(gm, sl);
-                const float2 w = ff_mul(ff_add(ff_mul(g1, st[j]), ff_mul_f(g2, v[j])), sj);
-                const float2 sf = ff_mul_f(sj, v[j]);  // S F^
-                const float2 t = ff_mul(g3, sf);
-                e.zhat[o] = ff_add(w, make_float2(-t.x, -t.y));
+                const float2 t = ff_mul(g1, st[j]);
+                const float2 w = ff_mul(ff_add_f(t, __fmul_rn(g2.x, v[j])), sj);
+                e.zhat[o] = ff_mul(ff_add_f(t, __fmul_rn(g23, v[j])), sj);
                 e.write_operand_ff(o, w);
             }
         }
         return;
     }
-    if (e.mode == EPI_STAGE2) {
+    if (e.mode == EPI_STAGE2) {  // U^+ = Z + tau E3 F_W^
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             if (j < count) {
                 const long long o = o0 + j * step;
-                const float2 u = ff_add(st[j], ff_mul_f(g3, v[j]));
+                const float2 u = ff_add_f(st[j], __fmul_rn(g3, v[j]));
                 e.uhat[o] = u;
                 e.write_operand_ff(o, u);
             }
@@ -415,7 +424,9 @@ struct TcConfig {
     unsigned stage_bytes;
 };
 struct TcMaps;  // opaque holder of CUtensorMap objects (gemm_tc.cu)
-TcConfig tc_choose(int M, int n, int products, int nbatch, bool bf16);
+// accurate: the ACCURATE variant (three pieces only): correction products in
+// their own accumulator, compensated sums across k-blocks
+TcConfig tc_choose(int M, int n, int products, int nbatch, bool bf16, bool accurate);
 // a[i][j]: operand buffer i, piece j (NULL = reuse piece 0); pp[j]: pieces of P;
 // bn_slot: tile widths of the two configurations the maps serve.
 cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const void* const a[][3], int n_a,

@@ -707,9 +707,15 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
         const int prod0 = opt.precision == ETD_PREC_TF32
                               ? 1
                               : ((opt.precision == ETD_PREC_TF32X6 || opt.precision == ETD_PREC_BF16X6) ? 6 : 3);
-        p->tc[0] = tc_choose(p->M, n, prod0, nb, p->bf16);
-        if (opt.precision == ETD_PREC_TF32X3 || opt.precision == ETD_PREC_BF16X3) {
-            p->tc[1] = tc_choose(p->M, n, 6, nb, p->bf16);
+        // slot 0: every per-step pass; slot 1: the transforms whose error stays in
+        // the result (state rebuild, returned field), the ACCURATE six-product kernel.
+        // The six-product modes run every pass ACCURATE: with all six products in
+        // one k-block accumulator a pass is about as slow and no more accurate than
+        // the three-product split (the tensor cores' truncating accumulation, not
+        // the dropped lo*lo term, sets the error).
+        p->tc[0] = tc_choose(p->M, n, prod0, nb, p->bf16, prod0 == 6);
+        if (prod0 > 1) {
+            p->tc[1] = tc_choose(p->M, n, 6, nb, p->bf16, true);
             p->out_slot = 1;
         } else {
             p->tc[1] = p->tc[0];

@@ -901,12 +901,12 @@ bool make_map(CUtensorMap* map, const void* base, int inner, long long rows, int
 
 const char* tc_last_driver_error() { return g_driver_error; }
 
-TcConfig tc_choose(int M, int n, int products, int nbatch, bool bf16) {
+TcConfig tc_choose(int M, int n, int products, int nbatch, bool bf16, bool accurate) {
     TcConfig c{};
     c.products = products;
     c.bf16 = bf16;
     c.pieces = products == 6 ? 3 : (products == 3 ? 2 : 1);
-    c.accurate = (c.pieces == 3);
+    c.accurate = accurate && c.pieces == 3;
     // The 128 x 256 one-tile-per-CTA kernel wins when each tile has a long K loop
     // and there are enough tiles to fill the SMs several times over (2D at large
     // n); otherwise (3D: K = n is short, the epilogue dominates; mid-size 2D:
@@ -914,10 +914,12 @@ TcConfig tc_choose(int M, int n, int products, int nbatch, bool bf16) {
     const int kv = bf16 ? 2 * BKF : BKF;
     const int nk = (n + kv - 1) / kv;
     const long long tiles256 = (long long)nbatch * ((M + BM - 1) / BM) * ((n + 255) / 256);
-    c.persistent = !c.accurate && !(nk * kv >= 2048 && tiles256 >= 4 * 152);
+    // (the persistent kernel reads at most two operand pieces)
+    c.persistent = !c.accurate && c.pieces <= 2 && !(nk * kv >= 2048 && tiles256 >= 4 * 152);
     // tile width: the multiple of 32 up to bn_max that wastes the fewest columns
-    // (each of the two column halves is a whole number of 16-column TMEM loads)
-    const int bn_max = (c.accurate || c.persistent) ? 128 : 256;
+    // (each of the two column halves is a whole number of 16-column TMEM loads);
+    // three pieces of a 128 x 256 tile would leave room for one pipeline stage
+    const int bn_max = (c.accurate || c.persistent || c.pieces == 3) ? 128 : 256;
     int best = bn_max, best_waste = 1 << 30;
     if (n <= bn_max) {
         best = ((n + 31) / 32) * 32;
