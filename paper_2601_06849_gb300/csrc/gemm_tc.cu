@@ -585,10 +585,15 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-template <bool BF16>
+// ACC (short K only, no compensated sums): hi*hi into the k-block buffers, the
+// correction products into a fourth TMEM region that spans the tile's whole K
+// range; the drain warps add it to their sums once the tile's last k-block is
+// in, then free it for the next tile (one staging buffer instead of two).
+template <bool BF16, bool ACC>
 __global__ void __launch_bounds__(pk::THREADS, 1)
     gemm_tf32_persistent_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
-                                const __grid_constant__ CUtensorMap mP0, const __grid_constant__ CUtensorMap mP1,
+                                const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mP0,
+                                const __grid_constant__ CUtensorMap mP1, const __grid_constant__ CUtensorMap mP2,
                                 const KParams p) {
     constexpr int KV = BF16 ? 2 * BKF : BKF;  // operand values per k-block (128 bytes per row)
     extern __shared__ uint8_t smem_raw[];
@@ -597,8 +602,8 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     __shared__ int s_abort;
     __shared__ int s_consumed;
     __shared__ int s_issued;
-    // full[8], empty[8], kb_full[3], kb_empty[3], stage_full[2], stage_empty[2], done
-    __shared__ __align__(8) uint64_t s_bar[8 + 8 + 3 + 3 + 2 + 2 + 1];
+    // full[8], empty[8], kb_full[3], kb_empty[3], stage_full[2], stage_empty[2], done, corr_empty
+    __shared__ __align__(8) uint64_t s_bar[8 + 8 + 3 + 3 + 2 + 2 + 1 + 1];
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) s_skip = (*(volatile unsigned*)p.err != 0u);
@@ -615,10 +620,12 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     const uint32_t bar_st_full = smem_u32(&s_bar[22]);
     const uint32_t bar_st_empty = smem_u32(&s_bar[24]);
     const uint32_t bar_done = smem_u32(&s_bar[26]);
+    const uint32_t bar_corr_empty = smem_u32(&s_bar[27]);
     const int nk = (p.n + KV - 1) / KV;
     const int nkb = 2;                 // k-block buffers (3 + 1 measured slower than 2 + 2)
-    const int nsb = 4 - nkb;           // staging buffers
-    const uint32_t staging0 = (uint32_t)nkb * pk::KB_COLS;
+    const int nsb = ACC ? 1 : 2;       // staging buffers
+    const uint32_t corr0 = (uint32_t)nkb * pk::KB_COLS;  // ACC: correction accumulator
+    const uint32_t staging0 = (uint32_t)(nkb + (ACC ? 1 : 0)) * pk::KB_COLS;
     const int ntiles = p.nbatch * p.tiles_m * p.tiles_n;
 
     if (threadIdx.x == 0) {
@@ -635,6 +642,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
             mbar_init(bar_st_empty + 8 * a, pk::NUM_STORE);
         }
         mbar_init(bar_done, 1);
+        mbar_init(bar_corr_empty, pk::NUM_DRAIN);
         s_abort = 0;
         s_consumed = 0;
         s_issued = 0;
@@ -678,15 +686,19 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                     tma_load_2d(st + A_BYTES, &mA1, fb, k0, arow);
                     tma_load_2d(sb + p.b_bytes, &mP1, fb, k0, prow);
                 }
+                if (p.pieces > 2) {
+                    tma_load_2d(st + 2 * A_BYTES, &mA2, fb, k0, arow);
+                    tma_load_2d(sb + 2 * p.b_bytes, &mP2, fb, k0, prow);
+                }
                 s_issued = g + 1;
             }
         }
     } else if (warp == pk::WARP_MMA && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = BF16 ? idesc_bf16(BM, p.bn) : idesc_tf32(BM, p.bn);
-        int g = 0;
+        int g = 0, j = 0;
         bool stop = false;
-        for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+        for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x, ++j) {
             for (int kb = 0; kb < nk; ++kb, ++g) {
                 const int s = g % S;
                 const int a = g % nkb;
@@ -698,19 +710,33 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)a * pk::KB_COLS;
+                const uint32_t dc = ACC ? tmem + corr0 : d;  // correction products
                 const uint32_t a0 = smem_u32(smem + (size_t)s * p.stage_bytes);
-                const uint32_t a1 = a0 + A_BYTES;
+                const uint32_t a1 = a0 + A_BYTES, a2 = a0 + 2 * A_BYTES;
                 const uint32_t b0 = a0 + (uint32_t)p.pieces * A_BYTES;
-                const uint32_t b1 = b0 + p.b_bytes;
+                const uint32_t b1 = b0 + p.b_bytes, b2 = b0 + 2 * p.b_bytes;
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {
                     const uint32_t off = kk * 32;
                     mma_op<BF16>(d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
+                    if (ACC && kb == 0 && kk == 0 && j > 0 &&
+                        !mbar_wait(bar_corr_empty, (uint32_t)((j - 1) & 1), abort_flag, p.err)) {
+                        stop = true;  // the previous tile's corrections were never read
+                        break;
+                    }
+                    // ACC: the tile's first correction product overwrites the region
+                    const uint32_t cacc = ACC ? ((kb > 0 || kk > 0) ? 1u : 0u) : 1u;
                     if (p.products >= 3) {
-                        mma_op<BF16>(d, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, 1u);
-                        mma_op<BF16>(d, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                        mma_op<BF16>(dc, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, cacc);
+                        mma_op<BF16>(dc, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                    }
+                    if (p.products == 6) {
+                        mma_op<BF16>(dc, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                        mma_op<BF16>(dc, sdesc_sw128(a2 + off), sdesc_sw128(b0 + off), idesc, 1u);
+                        mma_op<BF16>(dc, sdesc_sw128(a0 + off), sdesc_sw128(b2 + off), idesc, 1u);
                     }
                 }
+                if (stop) break;
                 mma_commit(bar_empty + 8 * s);
                 mma_commit(bar_kb_full + 8 * a);
                 s_consumed = g + 1;
@@ -751,6 +777,24 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                 if (lane == 0) mbar_arrive(bar_kb_empty + 8 * a);
             }
             if (stop) break;
+            if constexpr (ACC) {
+                // every product of the tile has completed (the last k-block's commit
+                // covers all earlier products): add the corrections, free the region
+                tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < pk::HALF / 16; ++c) {
+                    if (c * 16 < hcols) {
+                        uint32_t r[16];
+                        tmem_ld16(tmem + lane_off + corr0 + (uint32_t)(c * 16), r);
+                        tmem_wait16(r);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) sum[c * 16 + i] += __uint_as_float(r[i]);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_corr_empty);
+            }
             const int sb = j % nsb;
             if (j >= nsb && !warp_wait(bar_st_empty + 8 * sb, (uint32_t)(((j / nsb) - 1) & 1), abort_flag, p.err))
                 break;
@@ -914,8 +958,11 @@ TcConfig tc_choose(int M, int n, int products, int nbatch, bool bf16, bool accur
     const int kv = bf16 ? 2 * BKF : BKF;
     const int nk = (n + kv - 1) / kv;
     const long long tiles256 = (long long)nbatch * ((M + BM - 1) / BM) * ((n + 255) / 256);
-    // (the persistent kernel reads at most two operand pieces)
-    c.persistent = !c.accurate && c.pieces <= 2 && !(nk * kv >= 2048 && tiles256 >= 4 * 152);
+    // The persistent kernel's accurate variant has no compensated sums across
+    // k-blocks, so it takes short K ranges only (at most 16 k-blocks); its fast
+    // variant reads at most two operand pieces.
+    const bool long_k = nk * kv >= 2048 && tiles256 >= 4 * 152;
+    c.persistent = !long_k && (c.accurate ? nk <= 16 : c.pieces <= 2);
     // tile width: the multiple of 32 up to bn_max that wastes the fewest columns
     // (each of the two column halves is a whole number of 16-column TMEM loads);
     // three pieces of a 128 x 256 tile would leave room for one pipeline stage
@@ -982,8 +1029,10 @@ cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const
                                  (const void*)gemm_tf32_tc_kernel<true, false>,
                                  (const void*)gemm_tf32_tc_kernel<false, true>,
                                  (const void*)gemm_tf32_tc_kernel<true, true>,
-                                 (const void*)gemm_tf32_persistent_kernel<false>,
-                                 (const void*)gemm_tf32_persistent_kernel<true>};
+                                 (const void*)gemm_tf32_persistent_kernel<false, false>,
+                                 (const void*)gemm_tf32_persistent_kernel<true, false>,
+                                 (const void*)gemm_tf32_persistent_kernel<false, true>,
+                                 (const void*)gemm_tf32_persistent_kernel<true, true>};
         cudaError_t e = cudaSuccess;
         for (const void* k : kernels)
             if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
@@ -1035,10 +1084,16 @@ cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, in
             if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
         }
         const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
-        if (cfg.bf16)
-            gemm_tf32_persistent_kernel<true><<<grid, pk::THREADS, cfg.smem_bytes, st>>>(A[0], A[1], P[0], P[1], p);
+        const int sm = cfg.smem_bytes;
+        const int th = pk::THREADS;
+        if (cfg.accurate && cfg.bf16)
+            gemm_tf32_persistent_kernel<true, true><<<grid, th, sm, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
+        else if (cfg.accurate)
+            gemm_tf32_persistent_kernel<false, true><<<grid, th, sm, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
+        else if (cfg.bf16)
+            gemm_tf32_persistent_kernel<true, false><<<grid, th, sm, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
         else
-            gemm_tf32_persistent_kernel<false><<<grid, pk::THREADS, cfg.smem_bytes, st>>>(A[0], A[1], P[0], P[1], p);
+            gemm_tf32_persistent_kernel<false, false><<<grid, th, sm, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
     } else {
         const unsigned g = (unsigned)ntiles;
         const int sm = cfg.smem_bytes;
