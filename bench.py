@@ -449,8 +449,8 @@ def main():
         bound = "hbm" if bytes_pass / (hpeak * 1e9) > flops / (tpeak * 1e12) else "tensor"
         top = hbm if bound == "hbm" else tens
         traffic, src_hash = (None, None)
-        if name == "fhn2d_4096" and args.precision == "tf32x3":
-            traffic, src_hash = recorded_traffic(KERNEL_FILES, "profiles/gemm_tf32_tc_fhn4096_traffic.md")
+        if name == "fhn2d_4096" and args.precision == "bf16x6":
+            traffic, src_hash = recorded_traffic(KERNEL_FILES, "profiles/gemm_tc_accurate_bf16x6_fhn4096_traffic.md")
         roof = {"bound": bound, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
                 "frac": top["frac"], "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
