@@ -64,7 +64,7 @@ def run_ensemble(args, world, rank, local):
     stream = torch.cuda.Stream()
     batch = etd.Batch(2, [m.n for m in members], [m.kappa_u for m in members], [q] * len(members),
                       [m.tau for m in members], precision=args.precision, reaction="fhn", rx_params=FHN, n_comp=2,
-                      kappa_v=kv, stream=stream)
+                      kappa_v=kv, stream=stream, autotune=args.autotune)
     info = batch.info()
     with torch.cuda.stream(stream):
         fields = [torch.tensor(m.u0, dtype=batch.dtype, device="cuda") for m in members]
@@ -119,6 +119,7 @@ def run_ensemble(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": f"{args.precision} (f32 fields, double-float spectral state)", "data": "synthetic",
         "config": {"workload": desc, "instances": len(members), "unknowns": info.unknowns,
+                   "autotuned": bool(args.autotune),
                    "precision": args.precision, "pade": "P02",
                    "l2": f"working set {info.workspace_bytes / 1e9:.2f} GB > 129 MB L2: no flush",
                    "parallelism": f"replicas x{world}; groups by grid on concurrent streams, one CUDA graph per step"},
@@ -150,14 +151,15 @@ def initial_field(name):
     return inputs.allen_cahn_2d(n, workload=0)
 
 
-def make_plan(name, precision, stream=None):
+def make_plan(name, precision, stream=None, autotune=False):
     from paper_2601_06849_gb300 import etd
 
     d, n, ku, kv, q, tau, rx, _ = WORKLOADS[name]
     if rx == "fhn":
         return etd.Plan(d, n, ku, q, tau, pade=2, precision=precision, reaction="fhn", rx_params=FHN, n_comp=2,
-                        kappa_comp=(ku, kv), stream=stream)
-    return etd.Plan(d, n, ku, q, tau, pade=2, precision=precision, reaction=rx, n_comp=1, stream=stream)
+                        kappa_comp=(ku, kv), stream=stream, autotune=autotune)
+    return etd.Plan(d, n, ku, q, tau, pade=2, precision=precision, reaction=rx, n_comp=1, stream=stream,
+                    autotune=autotune)
 
 
 def measured_peaks():
@@ -363,6 +365,7 @@ def main():
     ap.add_argument("--precision", default="bf16x6")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="time the pass kernel candidates at plan creation")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -384,7 +387,7 @@ def main():
     name = args.workload
     d, n, ku, kv, q, tau, rx, desc = WORKLOADS[name]
     stream = torch.cuda.Stream()
-    plan = make_plan(name, args.precision, stream=stream)
+    plan = make_plan(name, args.precision, stream=stream, autotune=args.autotune)
     info = plan.info()
     u0 = initial_field(name)
     u = torch.tensor(u0, dtype=plan.dtype, device="cuda")
@@ -485,6 +488,8 @@ def main():
                   "tf32x6": "tf32x6 (f32 fields, double-float spectral state)"}.get(args.precision, args.precision),
         "data": "synthetic",
         "config": {"workload": desc, "d": d, "n": n, "n_comp": info.n_comp, "precision": args.precision,
+                   "pass_kernel": {"persistent": list(info.pass_persistent), "tile_n": list(info.pass_tile_n),
+                                   "autotuned": bool(args.autotune)},
                    "pade": "P02", "unknowns": unknowns,
                    "l2": f"working set {info.workspace_bytes / 1e9:.2f} GB > 129 MB L2: inputs larger than L2, no flush",
                    "parallelism": f"replicas x{world}"},

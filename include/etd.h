@@ -92,8 +92,19 @@ typedef struct {
     int n_comp;            /* 1 or 2; default 1 */
     double kappa_comp[2];  /* per-component diffusivity; <= 0 means "use kappa" */
     void* stream;          /* cudaStream_t the plan launches on; NULL = legacy default */
-    int flags;             /* reserved, must be 0 */
+    int flags;             /* ETD_FLAG_* bits, default 0 */
 } etd_options;
+
+/*
+ * ETD_FLAG_AUTOTUNE: at plan creation (and for each group of an ensemble),
+ * time every candidate configuration of the tensor-core pass (one-tile-per-CTA
+ * kernel at its tile widths, persistent kernel) on the plan's own buffers, a
+ * few launches each with CUDA events on the plan stream, and keep the fastest.
+ * Choices are cached per (grid, batch, precision) within the process, so later
+ * plans of the same shape reuse them. Without the flag a fixed rule chooses.
+ * Plan creation then launches kernels and synchronises its stream.
+ */
+#define ETD_FLAG_AUTOTUNE 1
 
 /* Performance-relevant facts of a plan (for benchmarks and roofline figures). */
 typedef struct {
@@ -104,6 +115,10 @@ typedef struct {
     double gemm_flops;           /* algorithmic flops of one pass, all components: 2 n^(d+1) n_comp */
     double step_flops;           /* algorithmic flops of one time step (16 n or 24 n per unknown) */
     long long workspace_bytes;   /* device memory the plan holds */
+    int pass_persistent[2];      /* tensor-core pass configuration of the per-step passes [0] and of
+                                    the state-building / returned-field transforms [1]: 1 = the
+                                    persistent kernel, 0 = one tile per CTA */
+    int pass_tile_n[2];          /* tile width (columns) of those configurations; 0 without tensor cores */
     double step_bytes;           /* algorithmic DRAM bytes of one time step's transform passes: every operand
                                     piece, basis piece, spectral state value and output field value read or
                                     written once per pass (reaction kernels not included) */

@@ -427,6 +427,10 @@ struct TcMaps;  // opaque holder of CUtensorMap objects (gemm_tc.cu)
 // accurate: the ACCURATE variant (three pieces only): correction products in
 // their own accumulator, compensated sums across k-blocks
 TcConfig tc_choose(int M, int n, int products, int nbatch, bool bf16, bool accurate);
+// The configurations an autotuner may time for one pass (the tc_choose rule's
+// choice first, then the other kernel / tile widths that can run it); returns
+// how many were written to out (at most max_out).
+int tc_candidates(int M, int n, int products, int nbatch, bool bf16, bool accurate, TcConfig* out, int max_out);
 // a[i][j]: operand buffer i, piece j (NULL = reuse piece 0); pp[j]: pieces of P;
 // bn_slot: tile widths of the two configurations the maps serve.
 cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const void* const a[][3], int n_a,

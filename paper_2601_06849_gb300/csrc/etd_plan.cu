@@ -30,7 +30,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -623,7 +626,7 @@ etd_status validate_options(int d, int m, int pade_order, const etd_options& opt
     if (pade_order != ETD_PADE_02 && pade_order != ETD_PADE_04 && pade_order != ETD_EXACT_EXP)
         return fail(ETD_ERR_INVALID_ARG, "pade_order must be 2, 4 or 0 (exact exponential)");
     if (opt.n_comp < 1 || opt.n_comp > 2) return fail(ETD_ERR_INVALID_ARG, "n_comp must be 1 or 2");
-    if (opt.flags != 0) return fail(ETD_ERR_INVALID_ARG, "flags must be 0");
+    if (opt.flags & ~ETD_FLAG_AUTOTUNE) return fail(ETD_ERR_INVALID_ARG, "unknown bits in flags (0x%x)", opt.flags);
     if (opt.reaction < ETD_RX_NONE || opt.reaction > ETD_RX_AC_FORCED)
         return fail(ETD_ERR_INVALID_ARG, "unknown reaction");
     if (opt.reaction == ETD_RX_FHN && opt.n_comp != 2)
@@ -640,6 +643,87 @@ etd_status validate_scalars(double kappa, double q, double dt) {
     if (!(kappa > 0) || !std::isfinite(kappa)) return fail(ETD_ERR_INVALID_ARG, "kappa must be > 0");
     if (!(q >= 0) || !std::isfinite(q)) return fail(ETD_ERR_INVALID_ARG, "q must be >= 0");
     if (!(dt > 0) || !std::isfinite(dt)) return fail(ETD_ERR_INVALID_ARG, "dt must be > 0");
+    return ETD_OK;
+}
+
+// ---- autotuner (ETD_FLAG_AUTOTUNE) ----
+// Key: (M, n, nbatch, products, bf16, accurate); value: the chosen configuration.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int, int>, TcConfig> g_tune_cache;
+
+// Time the candidate configurations of config slot `slot` on the plan's own
+// operand buffers (a split pass from buffer 0 into buffer 1: the buffers hold
+// zeros at this point, and nothing in them is needed afterwards) and keep the
+// fastest in p->tc[slot].
+etd_status autotune_slot(etd_plan* p, int slot) {
+    const TcConfig& cur = p->tc[slot];
+    const auto key = std::make_tuple(p->M, p->n, p->ninst * p->ncomp, cur.products, cur.bf16 ? 1 : 0,
+                                     cur.accurate ? 1 : 0);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            p->tc[slot] = it->second;
+            return ETD_OK;
+        }
+    }
+    const int nb = p->ninst * p->ncomp;
+    TcConfig cand[4];
+    const int nc = tc_candidates(p->M, p->n, cur.products, nb, cur.bf16, cur.accurate, cand, 4);
+    int best = 0;
+    if (nc > 1) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ETD_CUDA(cudaEventCreate(&e0));
+        ETD_CUDA(cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        etd_status st = ETD_OK;
+        for (int i = 0; i < nc && st == ETD_OK; ++i) {
+            const void* a[2][3];
+            for (int x = 0; x < 2; ++x)
+                for (int y = 0; y < 3; ++y) a[x][y] = p->op[x][y];
+            const void* pp[3] = {p->P[0], p->P[1], p->P[2]};
+            const int bn_slot[2] = {cand[i].bn, cand[i].bn};
+            TcMaps* maps = nullptr;
+            cudaError_t ce = tc_maps_create(&maps, p->M, p->n, nb, p->ld, a, 2, pp, bn_slot, p->bf16);
+            if (ce != cudaSuccess) {
+                st = fail(ETD_ERR_CUDA, "autotune tensor maps: %s %s", cudaGetErrorString(ce), tc_last_driver_error());
+                break;
+            }
+            Epi<float> e = base_epi<float>(p);
+            e.mode = EPI_SPLIT;
+            e.split = split_for(p, slot);
+            e.op_hi = (float*)p->op[1][0];
+            e.op_lo = (float*)p->op[1][1];
+            e.op_lo2 = (float*)p->op[1][2];
+            const int reps = 3;
+            ce = launch_gemm_tc(cand[i], slot, maps, 0, p->M, p->n, nb, e, p->err, p->stream);  // warm-up
+            if (ce == cudaSuccess) ce = cudaEventRecord(e0, p->stream);
+            for (int r = 0; r < reps && ce == cudaSuccess; ++r)
+                ce = launch_gemm_tc(cand[i], slot, maps, 0, p->M, p->n, nb, e, p->err, p->stream);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e1, p->stream);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+            tc_maps_destroy(maps);
+            unsigned flags = 0;
+            if (ce == cudaSuccess) ce = cudaMemcpy(&flags, p->err, sizeof flags, cudaMemcpyDeviceToHost);
+            if (ce != cudaSuccess) {
+                st = fail(ETD_ERR_CUDA, "autotune launch: %s", cudaGetErrorString(ce));
+            } else if (flags) {
+                st = fail(flags & ERR_TIMEOUT ? ETD_ERR_TIMEOUT : ETD_ERR_CUDA, "autotune: device error flags 0x%x",
+                          flags);
+            } else if (ms < best_ms) {
+                best_ms = ms;
+                best = i;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st != ETD_OK) return st;
+    }
+    p->tc[slot] = cand[best];
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = cand[best];
     return ETD_OK;
 }
 
@@ -791,6 +875,14 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     if (ce != cudaSuccess) {
         free_plan(p);
         return fail(ETD_ERR_CUDA, "plan upload: %s", cudaGetErrorString(ce));
+    }
+    if (p->use_tc && (opt.flags & ETD_FLAG_AUTOTUNE)) {
+        etd_status st = autotune_slot(p, 0);
+        if (st == ETD_OK && p->out_slot != 0) st = autotune_slot(p, p->out_slot);
+        if (st != ETD_OK) {
+            free_plan(p);
+            return st;
+        }
     }
     if (p->use_tc) {
         const void* a[2][3];
@@ -1197,6 +1289,10 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
     info->gemm_flops = 2.0 * (double)p->npts * (double)p->n * p->ncomp * p->ninst;
     info->step_flops = info->gemm_flops * info->gemms_per_step;
     info->workspace_bytes = p->workspace;
+    for (int slot = 0; slot < 2; ++slot) {
+        info->pass_persistent[slot] = p->use_tc && p->tc[slot].persistent ? 1 : 0;
+        info->pass_tile_n[slot] = p->use_tc ? p->tc[slot].bn : 0;
+    }
     // Per pass: its operand pieces and basis pieces read once; per chain of d
     // passes, d - 1 split outputs plus one final epilogue (stage 1: U^ read, Z
     // and operand pieces written; stage 2: Z read, U^+ and pieces written;

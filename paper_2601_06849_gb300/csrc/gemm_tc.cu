@@ -104,14 +104,14 @@ __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_fla
     }
 }
 
-// Tile t -> (component b, row tile tm, column tile tn). Tiles walk down groups of
-// gm row tiles before moving to the next column tile, so the tiles running at
-// the same time share a few A panels and a few P panels (working set of a wave
-// of 152 tiles ~100-140 MB, about the 129 MB L2) instead of all of P.
-__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int gm_max, int& b, int& tm, int& tn) {
-    const int per_b = tiles_m * tiles_n;
-    b = t / per_b;
-    const int r = t - b * per_b;
+// Tile t -> (row tile tm, column tile tn). Row tiles run over the rows of all
+// components / instances stacked (nbatch * M rows; they share P), so a tile may
+// hold rows of two of them and no tile is padded when M is not a multiple of
+// 128. Tiles walk down groups of gm row tiles before moving to the next column
+// tile, so the tiles running at the same time share a few A panels and a few P
+// panels (working set of a wave of 152 tiles about the 129 MB L2) instead of all of P.
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int gm_max, int& tm, int& tn) {
+    const int r = t;
     const int group = r / (gm_max * tiles_n);
     const int first_m = group * gm_max;
     const int gm = min(gm_max, tiles_m - first_m);
@@ -315,8 +315,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const uint32_t bar_acc_empty = smem_u32(&s_bar[18]);
     const uint32_t bar_done = smem_u32(&s_bar[20]);
 
-    int b, tm, tn;
-    tile_coords(blockIdx.x, p.tiles_m, p.tiles_n, 16, b, tm, tn);
+    int tm, tn;
+    tile_coords(blockIdx.x, p.tiles_m, p.tiles_n, 16, tm, tn);
     const int nk = (p.n + KV - 1) / KV;
     // TMEM columns: [0, acc) and [acc, 2 acc) k-block buffers, [2 acc, 3 acc) corrections (ACCURATE)
     const uint32_t acc_cols = (uint32_t)p.acc_cols;
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
     if (warp == WARP_TMA && lane == 0) {
         // ---------------- TMA producer ----------------
-        const int arow = b * p.M + tm * BM;
+        const int arow = tm * BM;
         const int prow = tn * p.bn;
         int issued = 0;
         for (int kb = 0; kb < nk; ++kb) {
@@ -487,8 +487,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             for (int c = 0; c < HALF; ++c)
                 if (c < hcols) stage[c * 32 + lane] = sum[c];
             __syncwarp();
-            const int mm = tm * BM + quarter * 32 + lane;
-            if (mm < p.M) {
+            const int grow = tm * BM + quarter * 32 + lane;  // row of the stacked components
+            if (grow < p.nbatch * p.M) {
+                const int b = grow / p.M, mm = grow - b * p.M;
                 const int mh = mm / p.n, ml = mm - mh * p.n;
                 const int nn0 = tn * p.bn + half * hcols;
                 const int cols = min(hcols, p.n - nn0);
@@ -626,7 +627,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     const int nsb = ACC ? 1 : 2;       // staging buffers
     const uint32_t corr0 = (uint32_t)nkb * pk::KB_COLS;  // ACC: correction accumulator
     const uint32_t staging0 = (uint32_t)(nkb + (ACC ? 1 : 0)) * pk::KB_COLS;
-    const int ntiles = p.nbatch * p.tiles_m * p.tiles_n;
+    const int ntiles = p.tiles_m * p.tiles_n;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -665,9 +666,9 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
         int g = 0;
         bool stop = false;
         for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-            int b, tm, tn;
-            tile_coords(t, p.tiles_m, p.tiles_n, 12, b, tm, tn);
-            const int arow = b * p.M + tm * BM;
+            int tm, tn;
+            tile_coords(t, p.tiles_m, p.tiles_n, 12, tm, tn);
+            const int arow = tm * BM;
             const int prow = tn * p.bn;
             for (int kb = 0; kb < nk; ++kb, ++g) {
                 const int s = g % S;
@@ -827,15 +828,16 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
         constexpr int EC = pk::EPI_COLS;
         int j = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
-            int b, tm, tn;
-            tile_coords(t, p.tiles_m, p.tiles_n, 12, b, tm, tn);
+            int tm, tn;
+            tile_coords(t, p.tiles_m, p.tiles_n, 12, tm, tn);
             const int sb = j % nsb;
             if (!warp_wait(bar_st_full + 8 * sb, (uint32_t)((j / nsb) & 1), abort_flag, p.err)) break;
             tc_fence_after();
             const uint32_t src =
                 tmem + ((uint32_t)(quarter * 32) << 16) + staging0 + (uint32_t)sb * pk::KB_COLS + (uint32_t)(half * hcols);
-            const int mm = tm * BM + quarter * 32 + lane;
-            const bool row_ok = mm < p.M;
+            const int grow = tm * BM + quarter * 32 + lane;  // row of the stacked components
+            const bool row_ok = grow < p.nbatch * p.M;
+            const int b = grow / p.M, mm = grow - b * p.M;
             const int mh = mm / p.n, ml = mm - mh * p.n;
             const int nn0 = tn * p.bn + half * hcols;
             const int cols = min(hcols, p.n - nn0);  // may be <= 0 for the last column tile
@@ -945,49 +947,56 @@ bool make_map(CUtensorMap* map, const void* base, int inner, long long rows, int
 
 const char* tc_last_driver_error() { return g_driver_error; }
 
-TcConfig tc_choose(int M, int n, int products, int nbatch, bool bf16, bool accurate) {
+namespace {
+
+// Tile width: the multiple of 32 up to bn_max that wastes the fewest columns
+// (each of the two column halves is a whole number of 16-column TMEM loads).
+int pick_bn(int n, int bn_max) {
+    if (n <= bn_max) return ((n + 31) / 32) * 32;
+    int best = bn_max, best_waste = 1 << 30;
+    for (int bn = bn_max; bn >= (bn_max > 128 ? 128 : 64); bn -= 32) {
+        const int waste = ((n + bn - 1) / bn) * bn - n;
+        if (waste < best_waste) {
+            best_waste = waste;
+            best = bn;
+        }
+    }
+    return best;
+}
+
+int pieces_of(int products) { return products == 6 ? 3 : (products == 3 ? 2 : 1); }
+
+// Can the persistent kernel run this pass? Its accurate variant has no
+// compensated sums across k-blocks, so it takes short K ranges only (at most
+// 16 k-blocks); its fast variant reads at most two operand pieces.
+bool persistent_ok(int n, int pieces, bool accurate, bool bf16) {
+    const int kv = bf16 ? 2 * BKF : BKF;
+    const int nk = (n + kv - 1) / kv;
+    return accurate ? nk <= 16 : pieces <= 2;
+}
+
+// The largest tile width the one-tile kernel takes: 128 for the accurate
+// variant (its epilogue holds two sums per column) and for three pieces (a
+// 128 x 256 tile of three pieces leaves room for one pipeline stage).
+int onetile_bn_max(int pieces, bool accurate) { return (accurate || pieces == 3) ? 128 : 256; }
+
+TcConfig tc_make(int M, int n, int products, int nbatch, bool bf16, bool accurate, bool persistent, int bn) {
     TcConfig c{};
     c.products = products;
     c.bf16 = bf16;
-    c.pieces = products == 6 ? 3 : (products == 3 ? 2 : 1);
-    c.accurate = accurate && c.pieces == 3;
-    // The 128 x 256 one-tile-per-CTA kernel wins when each tile has a long K loop
-    // and there are enough tiles to fill the SMs several times over (2D at large
-    // n); otherwise (3D: K = n is short, the epilogue dominates; mid-size 2D:
-    // few tiles) the persistent 128 x 128 kernel overlaps epilogue and products.
-    const int kv = bf16 ? 2 * BKF : BKF;
-    const int nk = (n + kv - 1) / kv;
-    const long long tiles256 = (long long)nbatch * ((M + BM - 1) / BM) * ((n + 255) / 256);
-    // The persistent kernel's accurate variant has no compensated sums across
-    // k-blocks, so it takes short K ranges only (at most 16 k-blocks); its fast
-    // variant reads at most two operand pieces.
-    const bool long_k = nk * kv >= 2048 && tiles256 >= 4 * 152;
-    c.persistent = !long_k && (c.accurate ? nk <= 16 : c.pieces <= 2);
-    // tile width: the multiple of 32 up to bn_max that wastes the fewest columns
-    // (each of the two column halves is a whole number of 16-column TMEM loads);
-    // three pieces of a 128 x 256 tile would leave room for one pipeline stage
-    const int bn_max = (c.accurate || c.persistent || c.pieces == 3) ? 128 : 256;
-    int best = bn_max, best_waste = 1 << 30;
-    if (n <= bn_max) {
-        best = ((n + 31) / 32) * 32;
-    } else {
-        for (int bn = bn_max; bn >= (bn_max > 128 ? 128 : 64); bn -= 32) {
-            const int waste = ((n + bn - 1) / bn) * bn - n;
-            if (waste < best_waste) {
-                best_waste = waste;
-                best = bn;
-            }
-        }
-    }
-    c.bn = best;
+    c.pieces = pieces_of(products);
+    c.accurate = accurate && c.pieces >= 2;
+    c.persistent = persistent;
+    const long long rows = (long long)nbatch * M;  // components / instances stacked
+    c.bn = bn;
     c.tiles_n = (n + c.bn - 1) / c.bn;
-    c.tiles_m = (M + BM - 1) / BM;
+    c.tiles_m = (int)((rows + BM - 1) / BM);
     const unsigned b_bytes = (unsigned)c.bn * BKF * 4;
     c.stage_bytes = (unsigned)c.pieces * ((unsigned)A_BYTES + b_bytes);
     int s = (SMEM_LIMIT - 1024) / (int)c.stage_bytes;
     if (s > 8) s = 8;
     if (c.persistent) {
-        c.tmem_cols = (int)pk::TMEM_COLS;  // two k-block buffers + two staging buffers of 128 columns
+        c.tmem_cols = (int)pk::TMEM_COLS;  // k-block buffers, corrections / staging buffers of 128 columns
     } else {
         int acc = 32;
         while (acc < c.bn) acc *= 2;
@@ -1000,6 +1009,45 @@ TcConfig tc_choose(int M, int n, int products, int nbatch, bool bf16, bool accur
     c.stages = s;
     c.smem_bytes = s * (int)c.stage_bytes + 1024;
     return c;
+}
+
+}  // namespace
+
+TcConfig tc_choose(int M, int n, int products, int nbatch, bool bf16, bool accurate) {
+    const int pieces = pieces_of(products);
+    accurate = accurate && pieces >= 2;
+    // The 128 x 256 one-tile-per-CTA kernel wins when each tile has a long K loop
+    // and there are enough tiles to fill the SMs several times over (2D at large
+    // n); otherwise (3D: K = n is short, the epilogue dominates; mid-size 2D:
+    // few tiles) the persistent 128 x 128 kernel overlaps epilogue and products.
+    const int kv = bf16 ? 2 * BKF : BKF;
+    const int nk = (n + kv - 1) / kv;
+    const long long rows = (long long)nbatch * M;
+    const long long tiles256 = ((rows + BM - 1) / BM) * ((n + 255) / 256);
+    const bool long_k = nk * kv >= 2048 && tiles256 >= 4 * 152;
+    const bool persistent = !long_k && persistent_ok(n, pieces, accurate, bf16);
+    const int bn = pick_bn(n, persistent ? 128 : onetile_bn_max(pieces, accurate));
+    return tc_make(M, n, products, nbatch, bf16, accurate, persistent, bn);
+}
+
+int tc_candidates(int M, int n, int products, int nbatch, bool bf16, bool accurate, TcConfig* out, int max_out) {
+    const int pieces = pieces_of(products);
+    accurate = accurate && pieces >= 2;
+    TcConfig c[4];
+    int k = 0;
+    c[k++] = tc_choose(M, n, products, nbatch, bf16, accurate);
+    const int bmax = onetile_bn_max(pieces, accurate);
+    c[k++] = tc_make(M, n, products, nbatch, bf16, accurate, false, pick_bn(n, bmax));
+    if (bmax > 128) c[k++] = tc_make(M, n, products, nbatch, bf16, accurate, false, pick_bn(n, 128));
+    if (persistent_ok(n, pieces, accurate, bf16))
+        c[k++] = tc_make(M, n, products, nbatch, bf16, accurate, true, pick_bn(n, 128));
+    int m = 0;
+    for (int i = 0; i < k && m < max_out; ++i) {
+        bool dup = false;
+        for (int j = 0; j < m; ++j) dup = dup || (out[j].persistent == c[i].persistent && out[j].bn == c[i].bn);
+        if (!dup) out[m++] = c[i];
+    }
+    return m;
 }
 
 cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const void* const a[][3], int n_a,
@@ -1073,7 +1121,7 @@ cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, in
     p.err = err;
     p.e = e;
     p.nbatch = nbatch;
-    const long long ntiles = (long long)nbatch * cfg.tiles_m * cfg.tiles_n;
+    const long long ntiles = (long long)cfg.tiles_m * cfg.tiles_n;
     const CUtensorMap* A = maps->a[a_index];
     const CUtensorMap* P = maps->p[slot];
     if (cfg.persistent) {

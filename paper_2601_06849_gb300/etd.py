@@ -31,6 +31,7 @@ SYMBOLS = (
     "etd_selftest_wait_timeout",
 )
 ETD_NOALLOC_MAX_ELEMS = 4194304
+ETD_FLAG_AUTOTUNE = 1
 
 
 class EtdError(RuntimeError):
@@ -56,7 +57,8 @@ class etd_plan_info(ctypes.Structure):
         ("d", ctypes.c_int), ("n", ctypes.c_int), ("n_comp", ctypes.c_int), ("precision", ctypes.c_int),
         ("products", ctypes.c_int), ("gemms_per_step", ctypes.c_int),
         ("unknowns", ctypes.c_longlong), ("gemm_flops", ctypes.c_double), ("step_flops", ctypes.c_double),
-        ("workspace_bytes", ctypes.c_longlong), ("step_bytes", ctypes.c_double),
+        ("workspace_bytes", ctypes.c_longlong), ("pass_persistent", ctypes.c_int * 2),
+        ("pass_tile_n", ctypes.c_int * 2), ("step_bytes", ctypes.c_double),
     ]
 
 
@@ -226,7 +228,7 @@ class Batch:
     precision, Pade order and component count are shared."""
 
     def __init__(self, d, n, kappa, q, dt, pade=2, precision="tf32x3", reaction="fhn", rx_params=(), n_comp=2,
-                 kappa_v=None, stream=None):
+                 kappa_v=None, stream=None, autotune=False):
         import torch
 
         count = len(n)
@@ -241,6 +243,8 @@ class Batch:
         opt.n_comp = n_comp
         if kappa_v is not None:
             opt.kappa_comp[1] = float(kappa_v)
+        if autotune:
+            opt.flags |= ETD_FLAG_AUTOTUNE
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -292,7 +296,7 @@ class Plan:
 
     def __init__(self, d: int, n: int, kappa: float, q: float, dt: float, pade=2, precision: str = "tf32x3",
                  reaction: str = "allen_cahn", rx_params: Sequence[float] = (), n_comp: int = 1,
-                 kappa_comp: Optional[Sequence[float]] = None, stream=None):
+                 kappa_comp: Optional[Sequence[float]] = None, stream=None, autotune: bool = False):
         import torch
 
         self.d, self.n, self.dt, self.n_comp = d, n, dt, n_comp
@@ -307,6 +311,8 @@ class Plan:
         if kappa_comp is not None:
             for i, v in enumerate(kappa_comp):
                 opt.kappa_comp[i] = float(v)
+        if autotune:
+            opt.flags |= ETD_FLAG_AUTOTUNE
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -63,3 +63,33 @@ def test_null_plan_calls_fail_cleanly(lib):
             call()
     etd.etd_plan_destroy(0)  # NULL-safe
     assert lib.etd_status_string(0) == b"ok"
+
+
+def test_unknown_flags_rejected(lib):
+    o = etd.etd_options_default()
+    o.flags = 2  # not a defined ETD_FLAG_* bit
+    with pytest.raises(etd.EtdError) as ei:
+        etd.etd_plan_create(2, 64, 0.1, 0.0, 1e-3, 2, o)
+    assert ei.value.status == etd.ETD_ERR_INVALID_ARG
+
+
+def test_header_flag_and_binding_agree():
+    src = open(os.path.join(ROOT, "include", "etd.h")).read()
+    m = re.search(r"#define\s+ETD_FLAG_AUTOTUNE\s+(\d+)", src)
+    assert m and int(m.group(1)) == etd.ETD_FLAG_AUTOTUNE
+
+
+def test_plan_info_layout_matches_header():
+    # the ctypes mirror must list the header's fields in order
+    src = open(os.path.join(ROOT, "include", "etd.h")).read()
+    body = re.search(r"typedef struct \{([^{}]*)\} etd_plan_info;", src).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        for part in decl.split(",") if "(" not in decl else [decl]:
+            tok = re.findall(r"([A-Za-z_]\w*)\s*(?:\[\d+\])?\s*$", part.strip())
+            names.append(tok[-1])
+    assert names == [f[0] for f in etd.etd_plan_info._fields_]

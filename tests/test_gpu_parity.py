@@ -1,8 +1,9 @@
 """Full ETD2RK-DS steps through the C ABI against the FP64 CPU oracle.
 
 Error metric (relative, whole field): max |U_gpu - U_oracle| / max |U_oracle|,
-per component. Every precision carries the spectral state in FP64, so the
-error of the returned field is set by the transform that produces it:
+per component. Every precision carries the spectral state with more than FP32
+precision (FP64, or double-float pairs in the FP32 paths), so the error of the
+returned field is set by the transforms:
   fp64    1e-10                 the FP64 bar
   tf32x3  1e-6                  the split-precision bar (output transform: 3-piece split)
   tf32x6  1e-6                  same, three-piece split in every pass
