@@ -38,8 +38,12 @@ struct TcMaps {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BKF = 32;                  // TF32 values per k-block = one 128-byte row (64 for BF16)
-constexpr int A_BYTES = BM * BKF * 4;    // 16 KiB per operand plane
+constexpr int BKF = 32;                  // TF32 values per k-block (64 for BF16): 128 bytes of K, the
+                                         // span one TMEM accumulator buffer takes before it is drained
+constexpr int ROW = 128;                 // bytes of K per operand row in one pipeline stage (64 measured slower)
+constexpr int SPD = 128 / ROW;           // pipeline stages per k-block
+constexpr int KK = ROW / 32;             // MMAs per stage (each takes 32 bytes of K)
+constexpr int A_BYTES = BM * ROW;        // one operand piece of a stage
 constexpr int NUM_EPI_WARPS = 8;         // two per TMEM lane quarter, one per column half
 constexpr int WARP_TMA = 8;
 constexpr int WARP_MMA = 9;
@@ -147,12 +151,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 }
 
 // Shared-memory matrix descriptor, K-major operand, 128-byte swizzle:
-// start address >> 4 (bits 0-13), leading byte offset (unused with this
-// swizzle, 16 B), stride byte offset 1024 B between 8-row groups (bits 32-45),
-// descriptor version 1 (bit 46), swizzle mode 2 = 128 B (bits 61-63).
+// start address >> 4 (bits 0-13), leading byte offset (unused with a swizzled
+// K-major layout, 16 B), stride byte offset between 8-row groups (bits 32-45:
+// 8 rows x ROW bytes), descriptor version 1 (bit 46), swizzle mode at bits
+// 61-63 (2 = 128-byte rows, 4 = 64-byte rows), matching the tensor maps' swizzle.
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+    constexpr uint64_t mode = ROW == 128 ? 2 : 4;
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)((8 * ROW) >> 4) << 32) |
+           ((uint64_t)1 << 46) | (mode << 61);
 }
 
 // Instruction descriptor of kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32
@@ -291,7 +297,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mP0,
                         const __grid_constant__ CUtensorMap mP1, const __grid_constant__ CUtensorMap mP2,
                         const KParams p) {
-    constexpr int KV = BF16 ? 2 * BKF : BKF;  // operand values per k-block (128 bytes per row)
+    constexpr int KV = BF16 ? 2 * BKF : BKF;  // operand values per k-block
+    constexpr int KVS = KV / SPD;             // operand values per pipeline stage
     extern __shared__ uint8_t smem_raw[];
     __shared__ int s_skip;
     __shared__ uint32_t s_tmem;
@@ -317,7 +324,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
     int tm, tn;
     tile_coords(blockIdx.x, p.tiles_m, p.tiles_n, 16, tm, tn);
-    const int nk = (p.n + KV - 1) / KV;
+    const int nst = (p.n + KVS - 1) / KVS;  // pipeline stages of the K range
+    const int nk = (nst + SPD - 1) / SPD;   // k-blocks (accumulator buffers drained)
     // TMEM columns: [0, acc) and [acc, 2 acc) k-block buffers, [2 acc, 3 acc) corrections (ACCURATE)
     const uint32_t acc_cols = (uint32_t)p.acc_cols;
 
@@ -353,14 +361,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int arow = tm * BM;
         const int prow = tn * p.bn;
         int issued = 0;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % S;
-            const uint32_t ph = (uint32_t)((kb / S) & 1);
+        for (int q = 0; q < nst; ++q) {
+            const int s = q % S;
+            const uint32_t ph = (uint32_t)((q / S) & 1);
             if (!mbar_wait(bar_empty + 8 * s, ph ^ 1u, abort_flag, p.err)) break;
             const uint32_t st = smem_u32(smem + (size_t)s * p.stage_bytes);
             const uint32_t fb = bar_full + 8 * s;
             mbar_expect_tx(fb, p.tx_bytes);
-            const int k0 = kb * KV;
+            const int k0 = q * KVS;
             const uint32_t sb = st + (uint32_t)p.pieces * A_BYTES;  // first P piece
             tma_load_2d(st, &mA0, fb, k0, arow);
             tma_load_2d(sb, &mP0, fb, k0, prow);
@@ -372,44 +380,50 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 tma_load_2d(st + 2 * A_BYTES, &mA2, fb, k0, arow);
                 tma_load_2d(sb + 2 * p.b_bytes, &mP2, fb, k0, prow);
             }
-            issued = kb + 1;
+            issued = q + 1;
         }
         s_issued = issued;
     } else if (warp == WARP_MMA && lane == 0) {
         // ---------------- MMA issuer: one k-block per accumulator buffer ----------------
         const uint32_t idesc = BF16 ? idesc_bf16(BM, p.bn) : idesc_tf32(BM, p.bn);
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % S;
-            const int a = kb & 1;
-            if (!mbar_wait(bar_full + 8 * s, (uint32_t)((kb / S) & 1), abort_flag, p.err)) break;
-            if (kb >= 2 && !mbar_wait(bar_acc_empty + 8 * a, (uint32_t)(((kb >> 1) - 1) & 1), abort_flag, p.err))
+        const uint64_t desc0 = sdesc_sw128(smem_u32(smem));  // stage 0, piece 0
+        for (int q = 0; q < nst; ++q) {
+            const int s = q % S;
+            const int kb = q / SPD, a = kb & 1;
+            const bool first = q % SPD == 0, last = q % SPD == SPD - 1 || q == nst - 1;  // of the k-block
+            if (!mbar_wait(bar_full + 8 * s, (uint32_t)((q / S) & 1), abort_flag, p.err)) break;
+            if (first && kb >= 2 &&
+                !mbar_wait(bar_acc_empty + 8 * a, (uint32_t)(((kb >> 1) - 1) & 1), abort_flag, p.err))
                 break;
             tc_fence_after();
             const uint32_t d = tmem + (uint32_t)a * acc_cols;
             const uint32_t dc = ACCURATE ? tmem + 2u * acc_cols : d;  // correction products
-            const uint32_t a0 = smem_u32(smem + (size_t)s * p.stage_bytes);
-            const uint32_t a1 = a0 + A_BYTES, a2 = a0 + 2 * A_BYTES;
-            const uint32_t b0 = a0 + (uint32_t)p.pieces * A_BYTES;
-            const uint32_t b1 = b0 + p.b_bytes, b2 = b0 + 2 * p.b_bytes;
+            // operand descriptors by offset from the stage's first one (the start
+            // address field is address / 16): the issuing thread keeps up with
+            // 128 x 128 x 16 BF16 products only without rebuilding descriptors
+            const uint64_t dA0 = desc0 + (uint64_t)(s * (p.stage_bytes >> 4));
+            const uint64_t dA1 = dA0 + (A_BYTES >> 4), dA2 = dA0 + 2 * (A_BYTES >> 4);
+            const uint64_t dB0 = dA0 + (uint64_t)(p.pieces * (A_BYTES >> 4));
+            const uint64_t dB1 = dB0 + (p.b_bytes >> 4), dB2 = dB0 + 2 * (p.b_bytes >> 4);
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint32_t off = kk * 32;  // 8 TF32 values = 32 bytes per MMA
+            for (int kk = 0; kk < KK; ++kk) {
+                const uint64_t o = 2 * kk;  // 8 TF32 or 16 BF16 values = 32 bytes per MMA
                 // terms of (a0 + a1 + a2)(b0 + b1 + b2) down to the 2^-22 level
-                mma_op<BF16>(d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
-                const uint32_t cacc = ACCURATE ? ((kb > 0 || kk > 0) ? 1u : 0u) : 1u;
+                mma_op<BF16>(d, dA0 + o, dB0 + o, idesc, (first && kk == 0) ? 0u : 1u);
+                const uint32_t cacc = ACCURATE ? ((q > 0 || kk > 0) ? 1u : 0u) : 1u;
                 if (p.products >= 3) {
-                    mma_op<BF16>(dc, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, cacc);
-                    mma_op<BF16>(dc, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                    mma_op<BF16>(dc, dA1 + o, dB0 + o, idesc, cacc);
+                    mma_op<BF16>(dc, dA0 + o, dB1 + o, idesc, 1u);
                 }
                 if (p.products == 6) {
-                    mma_op<BF16>(dc, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), idesc, 1u);
-                    mma_op<BF16>(dc, sdesc_sw128(a2 + off), sdesc_sw128(b0 + off), idesc, 1u);
-                    mma_op<BF16>(dc, sdesc_sw128(a0 + off), sdesc_sw128(b2 + off), idesc, 1u);
+                    mma_op<BF16>(dc, dA1 + o, dB1 + o, idesc, 1u);
+                    mma_op<BF16>(dc, dA2 + o, dB0 + o, idesc, 1u);
+                    mma_op<BF16>(dc, dA0 + o, dB2 + o, idesc, 1u);
                 }
             }
-            mma_commit(bar_empty + 8 * s);     // stage s may be refilled once these products finish
-            mma_commit(bar_acc_full + 8 * a);  // the k-block sum is ready for the epilogue
-            s_consumed = kb + 1;
+            mma_commit(bar_empty + 8 * s);                 // stage s may be refilled once these products finish
+            if (last) mma_commit(bar_acc_full + 8 * a);  // the k-block sum is ready for the epilogue
+            s_consumed = q + 1;
         }
         mma_commit(bar_done);  // arrives when every product issued above has completed
     } else if (warp < NUM_EPI_WARPS) {
@@ -596,7 +610,8 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                                 const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mP0,
                                 const __grid_constant__ CUtensorMap mP1, const __grid_constant__ CUtensorMap mP2,
                                 const KParams p) {
-    constexpr int KV = BF16 ? 2 * BKF : BKF;  // operand values per k-block (128 bytes per row)
+    constexpr int KV = BF16 ? 2 * BKF : BKF;  // operand values per k-block
+    constexpr int KVS = KV / SPD;             // operand values per pipeline stage
     extern __shared__ uint8_t smem_raw[];
     __shared__ int s_skip;
     __shared__ uint32_t s_tmem;
@@ -622,7 +637,8 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     const uint32_t bar_st_empty = smem_u32(&s_bar[24]);
     const uint32_t bar_done = smem_u32(&s_bar[26]);
     const uint32_t bar_corr_empty = smem_u32(&s_bar[27]);
-    const int nk = (p.n + KV - 1) / KV;
+    const int nst = (p.n + KVS - 1) / KVS;  // pipeline stages of a tile's K range
+    const int nk = (nst + SPD - 1) / SPD;   // k-blocks of a tile (accumulator buffers drained)
     const int nkb = 2;                 // k-block buffers (3 + 1 measured slower than 2 + 2)
     const int nsb = ACC ? 1 : 2;       // staging buffers
     const uint32_t corr0 = (uint32_t)nkb * pk::KB_COLS;  // ACC: correction accumulator
@@ -670,7 +686,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
             tile_coords(t, p.tiles_m, p.tiles_n, 12, tm, tn);
             const int arow = tm * BM;
             const int prow = tn * p.bn;
-            for (int kb = 0; kb < nk; ++kb, ++g) {
+            for (int q = 0; q < nst; ++q, ++g) {
                 const int s = g % S;
                 if (!mbar_wait(bar_empty + 8 * s, (uint32_t)(((g / S) & 1) ^ 1), abort_flag, p.err)) {
                     stop = true;
@@ -679,7 +695,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                 const uint32_t st = smem_u32(smem + (size_t)s * p.stage_bytes);
                 const uint32_t fb = bar_full + 8 * s;
                 mbar_expect_tx(fb, p.tx_bytes);
-                const int k0 = kb * KV;
+                const int k0 = q * KVS;
                 const uint32_t sb = st + (uint32_t)p.pieces * A_BYTES;
                 tma_load_2d(st, &mA0, fb, k0, arow);
                 tma_load_2d(sb, &mP0, fb, k0, prow);
@@ -697,49 +713,55 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     } else if (warp == pk::WARP_MMA && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t idesc = BF16 ? idesc_bf16(BM, p.bn) : idesc_tf32(BM, p.bn);
-        int g = 0, j = 0;
+        const uint64_t desc0 = sdesc_sw128(smem_u32(smem));  // stage 0, piece 0
+        int g = 0, gk = 0, j = 0;  // stages, k-blocks, tiles of this CTA so far
         bool stop = false;
         for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x, ++j) {
-            for (int kb = 0; kb < nk; ++kb, ++g) {
+            for (int q = 0; q < nst; ++q, ++g) {
                 const int s = g % S;
-                const int a = g % nkb;
+                const bool first = q % SPD == 0, last = q % SPD == SPD - 1 || q == nst - 1;  // of the k-block
+                const int a = gk % nkb;
                 if (!mbar_wait(bar_full + 8 * s, (uint32_t)((g / S) & 1), abort_flag, p.err) ||
-                    (g >= nkb &&
-                     !mbar_wait(bar_kb_empty + 8 * a, (uint32_t)(((g / nkb) - 1) & 1), abort_flag, p.err))) {
+                    (first && gk >= nkb &&
+                     !mbar_wait(bar_kb_empty + 8 * a, (uint32_t)(((gk / nkb) - 1) & 1), abort_flag, p.err))) {
                     stop = true;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)a * pk::KB_COLS;
                 const uint32_t dc = ACC ? tmem + corr0 : d;  // correction products
-                const uint32_t a0 = smem_u32(smem + (size_t)s * p.stage_bytes);
-                const uint32_t a1 = a0 + A_BYTES, a2 = a0 + 2 * A_BYTES;
-                const uint32_t b0 = a0 + (uint32_t)p.pieces * A_BYTES;
-                const uint32_t b1 = b0 + p.b_bytes, b2 = b0 + 2 * p.b_bytes;
+                // operand descriptors by offset from the stage's first one (see the one-tile kernel)
+                const uint64_t dA0 = desc0 + (uint64_t)(s * (p.stage_bytes >> 4));
+                const uint64_t dA1 = dA0 + (A_BYTES >> 4), dA2 = dA0 + 2 * (A_BYTES >> 4);
+                const uint64_t dB0 = dA0 + (uint64_t)(p.pieces * (A_BYTES >> 4));
+                const uint64_t dB1 = dB0 + (p.b_bytes >> 4), dB2 = dB0 + 2 * (p.b_bytes >> 4);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint32_t off = kk * 32;
-                    mma_op<BF16>(d, sdesc_sw128(a0 + off), sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
-                    if (ACC && kb == 0 && kk == 0 && j > 0 &&
+                for (int kk = 0; kk < KK; ++kk) {
+                    const uint64_t o = 2 * kk;
+                    mma_op<BF16>(d, dA0 + o, dB0 + o, idesc, (first && kk == 0) ? 0u : 1u);
+                    if (ACC && q == 0 && kk == 0 && j > 0 &&
                         !mbar_wait(bar_corr_empty, (uint32_t)((j - 1) & 1), abort_flag, p.err)) {
                         stop = true;  // the previous tile's corrections were never read
                         break;
                     }
                     // ACC: the tile's first correction product overwrites the region
-                    const uint32_t cacc = ACC ? ((kb > 0 || kk > 0) ? 1u : 0u) : 1u;
+                    const uint32_t cacc = ACC ? ((q > 0 || kk > 0) ? 1u : 0u) : 1u;
                     if (p.products >= 3) {
-                        mma_op<BF16>(dc, sdesc_sw128(a1 + off), sdesc_sw128(b0 + off), idesc, cacc);
-                        mma_op<BF16>(dc, sdesc_sw128(a0 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                        mma_op<BF16>(dc, dA1 + o, dB0 + o, idesc, cacc);
+                        mma_op<BF16>(dc, dA0 + o, dB1 + o, idesc, 1u);
                     }
                     if (p.products == 6) {
-                        mma_op<BF16>(dc, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), idesc, 1u);
-                        mma_op<BF16>(dc, sdesc_sw128(a2 + off), sdesc_sw128(b0 + off), idesc, 1u);
-                        mma_op<BF16>(dc, sdesc_sw128(a0 + off), sdesc_sw128(b2 + off), idesc, 1u);
+                        mma_op<BF16>(dc, dA1 + o, dB1 + o, idesc, 1u);
+                        mma_op<BF16>(dc, dA2 + o, dB0 + o, idesc, 1u);
+                        mma_op<BF16>(dc, dA0 + o, dB2 + o, idesc, 1u);
                     }
                 }
                 if (stop) break;
                 mma_commit(bar_empty + 8 * s);
-                mma_commit(bar_kb_full + 8 * a);
+                if (last) {
+                    mma_commit(bar_kb_full + 8 * a);
+                    ++gk;
+                }
                 s_consumed = g + 1;
             }
         }
@@ -929,11 +951,12 @@ bool make_map(CUtensorMap* map, const void* base, int inner, long long rows, int
     }
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)ld * (bf16 ? 2 : 4)};
-    cuuint32_t box[2] = {(cuuint32_t)(bf16 ? 2 * BKF : BKF), (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)(ROW / (bf16 ? 2 : 4)), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                     const_cast<void*>(base), dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, ROW == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         snprintf(g_driver_error, sizeof g_driver_error, "cuTensorMapEncodeTiled failed (%d) inner=%d rows=%lld ld=%d",
@@ -991,7 +1014,7 @@ TcConfig tc_make(int M, int n, int products, int nbatch, bool bf16, bool accurat
     c.bn = bn;
     c.tiles_n = (n + c.bn - 1) / c.bn;
     c.tiles_m = (int)((rows + BM - 1) / BM);
-    const unsigned b_bytes = (unsigned)c.bn * BKF * 4;
+    const unsigned b_bytes = (unsigned)c.bn * ROW;
     c.stage_bytes = (unsigned)c.pieces * ((unsigned)A_BYTES + b_bytes);
     int s = (SMEM_LIMIT - 1024) / (int)c.stage_bytes;
     if (s > 8) s = 8;
@@ -1116,7 +1139,7 @@ cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, in
     p.tmem_cols = cfg.tmem_cols;
     p.acc_cols = cfg.tmem_cols / (cfg.accurate ? 4 : 2);
     p.stage_bytes = cfg.stage_bytes;
-    p.b_bytes = (unsigned)cfg.bn * BKF * 4;
+    p.b_bytes = (unsigned)cfg.bn * ROW;
     p.tx_bytes = cfg.stage_bytes;
     p.err = err;
     p.e = e;
