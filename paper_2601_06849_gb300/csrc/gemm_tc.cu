@@ -47,7 +47,8 @@ constexpr int A_BYTES = BM * ROW;        // one operand piece of a stage
 constexpr int NUM_EPI_WARPS = 8;         // two per TMEM lane quarter, one per column half
 constexpr int WARP_TMA = 8;
 constexpr int WARP_MMA = 9;
-constexpr int NUM_THREADS = 320;
+constexpr int WARP_MMA2 = 10;             // ACCURATE: issues the correction products
+constexpr int NUM_THREADS = 352;
 constexpr int MAX_HALF = 128;            // columns per epilogue warp (bn <= 256)
 constexpr int STAGE_BYTES_EPI = NUM_EPI_WARPS * 32 * MAX_HALF * 4;
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
@@ -329,16 +330,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     // TMEM columns: [0, acc) and [acc, 2 acc) k-block buffers, [2 acc, 3 acc) corrections (ACCURATE)
     const uint32_t acc_cols = (uint32_t)p.acc_cols;
 
+    // ACCURATE: two issuing threads (hi*hi, corrections) commit to each stage's
+    // `empty` barrier and to `done`
+    constexpr uint32_t ISSUERS = ACCURATE ? 2 : 1;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(bar_full + 8 * s, 1);
-            mbar_init(bar_empty + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, ISSUERS);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(bar_acc_full + 8 * a, 1);
             mbar_init(bar_acc_empty + 8 * a, NUM_EPI_WARPS);
         }
-        mbar_init(bar_done, 1);
+        mbar_init(bar_done, ISSUERS);
         s_abort = 0;
         s_consumed = 0;
         s_issued = 0;
@@ -408,14 +412,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
             for (int kk = 0; kk < KK; ++kk) {
                 const uint64_t o = 2 * kk;  // 8 TF32 or 16 BF16 values = 32 bytes per MMA
-                // terms of (a0 + a1 + a2)(b0 + b1 + b2) down to the 2^-22 level
+                // terms of (a0 + a1 + a2)(b0 + b1 + b2) down to the 2^-22 level; in
+                // ACCURATE mode warp WARP_MMA2 issues the corrections (below)
                 mma_op<BF16>(d, dA0 + o, dB0 + o, idesc, (first && kk == 0) ? 0u : 1u);
-                const uint32_t cacc = ACCURATE ? ((q > 0 || kk > 0) ? 1u : 0u) : 1u;
-                if (p.products >= 3) {
-                    mma_op<BF16>(dc, dA1 + o, dB0 + o, idesc, cacc);
+                if (!ACCURATE && p.products >= 3) {
+                    mma_op<BF16>(dc, dA1 + o, dB0 + o, idesc, 1u);
                     mma_op<BF16>(dc, dA0 + o, dB1 + o, idesc, 1u);
                 }
-                if (p.products == 6) {
+                if (!ACCURATE && p.products == 6) {
                     mma_op<BF16>(dc, dA1 + o, dB1 + o, idesc, 1u);
                     mma_op<BF16>(dc, dA2 + o, dB0 + o, idesc, 1u);
                     mma_op<BF16>(dc, dA0 + o, dB2 + o, idesc, 1u);
@@ -426,6 +430,40 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             s_consumed = q + 1;
         }
         mma_commit(bar_done);  // arrives when every product issued above has completed
+    } else if (ACCURATE && warp == WARP_MMA2 && lane == 0) {
+        // ---------------- correction products into their own accumulator ----------------
+        // A second issuing thread: the products of a k-block are 4 hi*hi and 20
+        // corrections of 128 x bn x 16, and one thread cannot issue them as fast
+        // as the tensor core runs them (measured: 2D n = 4096 split BF16 x6, 10.0
+        // -> 9.7 ms per step; a third thread with its own region gained nothing).
+        // Each thread's commit covers its own products.
+        const uint32_t idesc = BF16 ? idesc_bf16(BM, p.bn) : idesc_tf32(BM, p.bn);
+        const uint64_t desc0 = sdesc_sw128(smem_u32(smem));
+        const uint32_t dc = tmem + 2u * acc_cols;
+        for (int q = 0; q < nst; ++q) {
+            const int s = q % S;
+            if (!mbar_wait(bar_full + 8 * s, (uint32_t)((q / S) & 1), abort_flag, p.err)) break;
+            tc_fence_after();
+            const uint64_t dA0 = desc0 + (uint64_t)(s * (p.stage_bytes >> 4));
+            const uint64_t dA1 = dA0 + (A_BYTES >> 4), dA2 = dA0 + 2 * (A_BYTES >> 4);
+            const uint64_t dB0 = dA0 + (uint64_t)(p.pieces * (A_BYTES >> 4));
+            const uint64_t dB1 = dB0 + (p.b_bytes >> 4), dB2 = dB0 + 2 * (p.b_bytes >> 4);
+#pragma unroll
+            for (int kk = 0; kk < KK; ++kk) {
+                const uint64_t o = 2 * kk;
+                if (p.products >= 3) {  // the first product overwrites the region
+                    mma_op<BF16>(dc, dA1 + o, dB0 + o, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+                    mma_op<BF16>(dc, dA0 + o, dB1 + o, idesc, 1u);
+                }
+                if (p.products == 6) {
+                    mma_op<BF16>(dc, dA1 + o, dB1 + o, idesc, 1u);
+                    mma_op<BF16>(dc, dA2 + o, dB0 + o, idesc, 1u);
+                    mma_op<BF16>(dc, dA0 + o, dB2 + o, idesc, 1u);
+                }
+            }
+            mma_commit(bar_empty + 8 * s);
+        }
+        mma_commit(bar_done);
     } else if (warp < NUM_EPI_WARPS) {
         // ---------------- epilogue: FP32 round-to-nearest sum of the k-block sums ----------------
         const int quarter = warp & 3;         // TMEM lanes 32*quarter .. +31
@@ -567,7 +605,8 @@ constexpr int NUM_DRAIN = 8;
 constexpr int NUM_STORE = 8;            // two per TMEM lane quarter, one per column half
 constexpr int WARP_TMA = 16;
 constexpr int WARP_MMA = 17;
-constexpr int THREADS = 18 * 32;        // <= 112 registers per thread
+constexpr int WARP_MMA2 = 18;           // ACC: issues the correction products
+constexpr int THREADS = 19 * 32;
 constexpr int EPI_COLS = 8;             // columns per epilogue batch of a store thread
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t KB_COLS = 128;        // one TMEM region (k-block or staging buffer)
@@ -618,8 +657,8 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     __shared__ int s_abort;
     __shared__ int s_consumed;
     __shared__ int s_issued;
-    // full[8], empty[8], kb_full[3], kb_empty[3], stage_full[2], stage_empty[2], done, corr_empty
-    __shared__ __align__(8) uint64_t s_bar[8 + 8 + 3 + 3 + 2 + 2 + 1 + 1];
+    // full[8], empty[8], kb_full[3], kb_empty[3], stage_full[2], stage_empty[2], done, corr_empty, corr_full
+    __shared__ __align__(8) uint64_t s_bar[8 + 8 + 3 + 3 + 2 + 2 + 1 + 1 + 1];
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) s_skip = (*(volatile unsigned*)p.err != 0u);
@@ -637,6 +676,8 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     const uint32_t bar_st_empty = smem_u32(&s_bar[24]);
     const uint32_t bar_done = smem_u32(&s_bar[26]);
     const uint32_t bar_corr_empty = smem_u32(&s_bar[27]);
+    const uint32_t bar_corr_full = smem_u32(&s_bar[28]);  // ACC: a tile's corrections are complete
+    constexpr uint32_t ISSUERS = ACC ? 2 : 1;              // ACC: a second thread issues the corrections
     const int nst = (p.n + KVS - 1) / KVS;  // pipeline stages of a tile's K range
     const int nk = (nst + SPD - 1) / SPD;   // k-blocks of a tile (accumulator buffers drained)
     const int nkb = 2;                 // k-block buffers (3 + 1 measured slower than 2 + 2)
@@ -648,7 +689,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(bar_full + 8 * s, 1);
-            mbar_init(bar_empty + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, ISSUERS);
         }
         for (int a = 0; a < 3; ++a) {
             mbar_init(bar_kb_full + 8 * a, 1);
@@ -658,8 +699,9 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
             mbar_init(bar_st_full + 8 * a, pk::NUM_DRAIN);
             mbar_init(bar_st_empty + 8 * a, pk::NUM_STORE);
         }
-        mbar_init(bar_done, 1);
+        mbar_init(bar_done, ISSUERS);
         mbar_init(bar_corr_empty, pk::NUM_DRAIN);
+        mbar_init(bar_corr_full, 1);
         s_abort = 0;
         s_consumed = 0;
         s_issued = 0;
@@ -732,22 +774,57 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                 const uint32_t dc = ACC ? tmem + corr0 : d;  // correction products
                 // operand descriptors by offset from the stage's first one (see the one-tile kernel)
                 const uint64_t dA0 = desc0 + (uint64_t)(s * (p.stage_bytes >> 4));
+                const uint64_t dA1 = dA0 + (A_BYTES >> 4);
+                const uint64_t dB0 = dA0 + (uint64_t)(p.pieces * (A_BYTES >> 4));
+                const uint64_t dB1 = dB0 + (p.b_bytes >> 4);
+#pragma unroll
+                for (int kk = 0; kk < KK; ++kk) {
+                    const uint64_t o = 2 * kk;
+                    mma_op<BF16>(d, dA0 + o, dB0 + o, idesc, (first && kk == 0) ? 0u : 1u);
+                    if (!ACC && p.products >= 3) {  // ACC: the correction thread (below)
+                        mma_op<BF16>(dc, dA1 + o, dB0 + o, idesc, 1u);
+                        mma_op<BF16>(dc, dA0 + o, dB1 + o, idesc, 1u);
+                    }
+                }
+                mma_commit(bar_empty + 8 * s);
+                if (last) {
+                    mma_commit(bar_kb_full + 8 * a);
+                    ++gk;
+                }
+                s_consumed = g + 1;
+            }
+        }
+        mma_commit(bar_done);
+    } else if (ACC && warp == pk::WARP_MMA2 && lane == 0) {
+        // ---------------- ACC: correction products into their own accumulator ----------------
+        // A second issuing thread (one thread cannot issue 4 hi*hi and 20
+        // correction products of 128 x 128 x 16 per k-block as fast as the tensor
+        // core runs them). Its commits cover its own products: the stage's
+        // `empty` (with the hi*hi thread's) and, after a tile's last stage,
+        // corr_full, on which the drain warps wait before reading the region.
+        const uint32_t idesc = BF16 ? idesc_bf16(BM, p.bn) : idesc_tf32(BM, p.bn);
+        const uint64_t desc0 = sdesc_sw128(smem_u32(smem));
+        const uint32_t dc = tmem + corr0;
+        int g = 0, j = 0;
+        bool stop = false;
+        for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x, ++j) {
+            for (int q = 0; q < nst; ++q, ++g) {
+                const int s = g % S;
+                if (!mbar_wait(bar_full + 8 * s, (uint32_t)((g / S) & 1), abort_flag, p.err) ||
+                    (q == 0 && j > 0 && !mbar_wait(bar_corr_empty, (uint32_t)((j - 1) & 1), abort_flag, p.err))) {
+                    stop = true;  // (or the previous tile's corrections were never read)
+                    break;
+                }
+                tc_fence_after();
+                const uint64_t dA0 = desc0 + (uint64_t)(s * (p.stage_bytes >> 4));
                 const uint64_t dA1 = dA0 + (A_BYTES >> 4), dA2 = dA0 + 2 * (A_BYTES >> 4);
                 const uint64_t dB0 = dA0 + (uint64_t)(p.pieces * (A_BYTES >> 4));
                 const uint64_t dB1 = dB0 + (p.b_bytes >> 4), dB2 = dB0 + 2 * (p.b_bytes >> 4);
 #pragma unroll
                 for (int kk = 0; kk < KK; ++kk) {
                     const uint64_t o = 2 * kk;
-                    mma_op<BF16>(d, dA0 + o, dB0 + o, idesc, (first && kk == 0) ? 0u : 1u);
-                    if (ACC && q == 0 && kk == 0 && j > 0 &&
-                        !mbar_wait(bar_corr_empty, (uint32_t)((j - 1) & 1), abort_flag, p.err)) {
-                        stop = true;  // the previous tile's corrections were never read
-                        break;
-                    }
-                    // ACC: the tile's first correction product overwrites the region
-                    const uint32_t cacc = ACC ? ((q > 0 || kk > 0) ? 1u : 0u) : 1u;
-                    if (p.products >= 3) {
-                        mma_op<BF16>(dc, dA1 + o, dB0 + o, idesc, cacc);
+                    if (p.products >= 3) {  // the tile's first correction product overwrites the region
+                        mma_op<BF16>(dc, dA1 + o, dB0 + o, idesc, (q > 0 || kk > 0) ? 1u : 0u);
                         mma_op<BF16>(dc, dA0 + o, dB1 + o, idesc, 1u);
                     }
                     if (p.products == 6) {
@@ -756,13 +833,8 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                         mma_op<BF16>(dc, dA0 + o, dB2 + o, idesc, 1u);
                     }
                 }
-                if (stop) break;
                 mma_commit(bar_empty + 8 * s);
-                if (last) {
-                    mma_commit(bar_kb_full + 8 * a);
-                    ++gk;
-                }
-                s_consumed = g + 1;
+                if (q == nst - 1) mma_commit(bar_corr_full);
             }
         }
         mma_commit(bar_done);
@@ -801,8 +873,9 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
             }
             if (stop) break;
             if constexpr (ACC) {
-                // every product of the tile has completed (the last k-block's commit
-                // covers all earlier products): add the corrections, free the region
+                // the correction thread's products of this tile have completed:
+                // add the corrections, free the region
+                if (!warp_wait(bar_corr_full, (uint32_t)(j & 1), abort_flag, p.err)) break;
                 tc_fence_after();
 #pragma unroll
                 for (int c = 0; c < pk::HALF / 16; ++c) {
