@@ -40,12 +40,80 @@ __device__ __forceinline__ void store_split(T* hi, T* lo, T* lo2, long long o, T
     hi[o] = v;
 }
 
+// Operand pieces of two adjacent values (element index o even): one 4-byte
+// (BF16 pair) or 8-byte (float pair) store per plane.
+__device__ __forceinline__ void store_split2(float* hi, float* lo, float* lo2, long long o, float va, float vb,
+                                             int split) {
+    if (split == SPLIT_BF16_2 || split == SPLIT_BF16_3) {
+        const __nv_bfloat16 ha = __float2bfloat16_rn(va), hb = __float2bfloat16_rn(vb);
+        const float ra = va - __bfloat162float(ha), rb = vb - __bfloat162float(hb);  // exact
+        const __nv_bfloat16 ma = __float2bfloat16_rn(ra), mb = __float2bfloat16_rn(rb);
+        reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(hi) + o)[0] = __halves2bfloat162(ha, hb);
+        reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(lo) + o)[0] = __halves2bfloat162(ma, mb);
+        if (split == SPLIT_BF16_3)
+            reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(lo2) + o)[0] = __halves2bfloat162(
+                __float2bfloat16_rn(ra - __bfloat162float(ma)), __float2bfloat16_rn(rb - __bfloat162float(mb)));
+        return;
+    }
+    if (split == SPLIT_TF32 || split == SPLIT_TF32_3) {
+        const float ha = tf32_rna(va), hb = tf32_rna(vb);
+        const float ra = va - ha, rb = vb - hb;  // exact
+        const float ma = tf32_rna(ra), mb = tf32_rna(rb);
+        reinterpret_cast<float2*>(hi + o)[0] = make_float2(ha, hb);
+        reinterpret_cast<float2*>(lo + o)[0] = make_float2(ma, mb);
+        if (split == SPLIT_TF32_3) reinterpret_cast<float2*>(lo2 + o)[0] = make_float2(tf32_rna(ra - ma), tf32_rna(rb - mb));
+        return;
+    }
+    if (split == SPLIT_TF32_HI) {
+        reinterpret_cast<float2*>(hi + o)[0] = make_float2(tf32_rna(va), tf32_rna(vb));
+        return;
+    }
+    reinterpret_cast<float2*>(hi + o)[0] = make_float2(va, vb);
+}
+
 // One warp task is a segment of RX_SEG consecutive points of one grid row
 // (RX_SEG / 32 per lane), so that every access is coalesced along the row, all
 // loads of a task are issued before its stores, and the only integer divisions
 // are two per task, not per point.
 constexpr int RX_SEG = 256;
 constexpr int RX_PER_LANE = RX_SEG / 32;
+
+// f(t, u) at one point: component values a (u) and b (v), x index, and the y [z]
+// factor u0yz of the manufactured solution (ETD_RX_AC_FORCED).
+template <typename T>
+__device__ __forceinline__ void rx_eval(const Rx<T>& r, T a, T b, int x, double u0yz, T& f0, T& f1) {
+    f0 = (T)0;
+    f1 = (T)0;
+    switch (r.kind) {
+        case ETD_RX_FHN:  // f_u = u - c3 u^3 - v,  f_v = eps (u - a v - b)
+            f0 = a - r.rp[0] * a * a * a - b;
+            f1 = r.rp[1] * (a - r.rp[2] * b - r.rp[3]);
+            break;
+        case ETD_RX_ALLEN_CAHN:
+            f0 = a - a * a * a;
+            break;
+        case ETD_RX_SINGULAR:
+            f0 = r.rp[0] * a / ((T)1 - a);
+            break;
+        case ETD_RX_AC_FORCED: {
+            // u0 = prod sin(pi x_axis) at x_i = (i+1)/(n+1); psi in FP64
+            const double ue = r.decay * u0yz * sinpi((double)(x + 1) / (double)(r.n + 1));
+            const double psi = r.psi_coef * ue - ue * (1.0 - ue * ue);
+            f0 = (T)((double)a * (1.0 - (double)a * (double)a) + psi);
+            break;
+        }
+        case ETD_RX_LINEAR:
+            f0 = r.rp[0] * a;
+            f1 = r.rp[0] * b;
+            break;
+        default:
+            if (r.kind < 0) {  // identity: split the field itself
+                f0 = a;
+                f1 = b;
+            }
+            break;
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
@@ -54,21 +122,17 @@ __global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
     const int nseg = (r.n + RX_SEG - 1) / RX_SEG;
     const long long tasks = rows_inst * r.ninst * nseg;
     const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+    // pairs of adjacent points per lane (8-byte loads, 4- or 8-byte stores) when
+    // every row starts on an even element
+    const bool pairs = sizeof(T) == 4 && (r.n % 2 == 0) && (r.ld_in % 2 == 0) && (r.ld_out % 2 == 0) &&
+                       (r.bs_in % 2 == 0) && (r.bs_out % 2 == 0);
     for (long long t = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < tasks; t += wstride) {
         const long long R = t / nseg;
-        const int x0 = (int)(t - R * nseg) * RX_SEG + lane;
+        const int xs = (int)(t - R * nseg) * RX_SEG;  // first point of the segment
         const long long inst = R / rows_inst;
         const long long row = R - inst * rows_inst;
         const T* __restrict__ in = r.in + inst * r.ncomp * r.bs_in + row * r.ld_in;
         const long long oo = inst * r.ncomp * r.bs_out + row * r.ld_out;
-        T u[RX_PER_LANE], v[RX_PER_LANE];
-#pragma unroll
-        for (int j = 0; j < RX_PER_LANE; ++j) {
-            const int x = x0 + 32 * j;
-            const bool ok = x < r.n;
-            u[j] = ok ? in[x] : (T)0;
-            v[j] = (ok && r.ncomp > 1) ? in[r.bs_in + x] : (T)0;
-        }
         double u0yz = 1.0;  // ETD_RX_AC_FORCED: the y [and z] factors of u0 on this row
         if (r.kind == ETD_RX_AC_FORCED) {
             const double inv = 1.0 / (double)(r.n + 1);
@@ -76,43 +140,47 @@ __global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
             u0yz = sinpi((double)(y + 1) * inv);
             if (r.d == 3) u0yz *= sinpi((double)(z + 1) * inv);
         }
+        if constexpr (sizeof(T) == 4) {
+            if (pairs) {
+                constexpr int NP = RX_SEG / 64;  // pairs per lane
+                float2 u[NP], v[NP];
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    const int x = xs + 2 * lane + 64 * j;  // even; x + 1 < n when x < n (n even)
+                    const bool ok = x < r.n;
+                    u[j] = ok ? reinterpret_cast<const float2*>(in + x)[0] : make_float2(0.f, 0.f);
+                    v[j] = (ok && r.ncomp > 1) ? reinterpret_cast<const float2*>(in + r.bs_in + x)[0]
+                                               : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    const int x = xs + 2 * lane + 64 * j;
+                    if (x >= r.n) continue;
+                    float fa0, fa1, fb0, fb1;
+                    rx_eval(r, u[j].x, v[j].x, x, u0yz, fa0, fa1);
+                    rx_eval(r, u[j].y, v[j].y, x + 1, u0yz, fb0, fb1);
+                    // component offsets go into the element index, never into pointer
+                    // arithmetic: the operand planes hold 4-byte or 2-byte values
+                    store_split2(r.out_hi, r.out_lo, r.out_lo2, oo + x, fa0, fb0, r.split);
+                    if (r.ncomp > 1) store_split2(r.out_hi, r.out_lo, r.out_lo2, oo + r.bs_out + x, fa1, fb1, r.split);
+                }
+                continue;
+            }
+        }
+        T u[RX_PER_LANE], v[RX_PER_LANE];
 #pragma unroll
         for (int j = 0; j < RX_PER_LANE; ++j) {
-            const int x = x0 + 32 * j;
+            const int x = xs + lane + 32 * j;
+            const bool ok = x < r.n;
+            u[j] = ok ? in[x] : (T)0;
+            v[j] = (ok && r.ncomp > 1) ? in[r.bs_in + x] : (T)0;
+        }
+#pragma unroll
+        for (int j = 0; j < RX_PER_LANE; ++j) {
+            const int x = xs + lane + 32 * j;
             if (x >= r.n) continue;
-            const T a = u[j], b = v[j];
-            T f0 = (T)0, f1 = (T)0;
-            switch (r.kind) {
-                case ETD_RX_FHN:  // f_u = u - c3 u^3 - v,  f_v = eps (u - a v - b)
-                    f0 = a - r.rp[0] * a * a * a - b;
-                    f1 = r.rp[1] * (a - r.rp[2] * b - r.rp[3]);
-                    break;
-                case ETD_RX_ALLEN_CAHN:
-                    f0 = a - a * a * a;
-                    break;
-                case ETD_RX_SINGULAR:
-                    f0 = r.rp[0] * a / ((T)1 - a);
-                    break;
-                case ETD_RX_AC_FORCED: {
-                    // u0 = prod sin(pi x_axis) at x_i = (i+1)/(n+1); psi in FP64
-                    const double ue = r.decay * u0yz * sinpi((double)(x + 1) / (double)(r.n + 1));
-                    const double psi = r.psi_coef * ue - ue * (1.0 - ue * ue);
-                    f0 = (T)((double)a * (1.0 - (double)a * (double)a) + psi);
-                    break;
-                }
-                case ETD_RX_LINEAR:
-                    f0 = r.rp[0] * a;
-                    f1 = r.rp[0] * b;
-                    break;
-                default:
-                    if (r.kind < 0) {  // identity: split the field itself
-                        f0 = a;
-                        f1 = b;
-                    }
-                    break;
-            }
-            // component offsets go into the element index, never into pointer
-            // arithmetic: the operand planes hold 4-byte or 2-byte values
+            T f0, f1;
+            rx_eval(r, u[j], v[j], x, u0yz, f0, f1);
             store_split(r.out_hi, r.out_lo, r.out_lo2, oo + x, f0, r.split);
             if (r.ncomp > 1) store_split(r.out_hi, r.out_lo, r.out_lo2, oo + r.bs_out + x, f1, r.split);
         }
