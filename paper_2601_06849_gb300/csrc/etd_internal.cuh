@@ -407,6 +407,8 @@ void launch_gemm_simt_f64(const double* A, const double* P, int M, int n, int nb
 void launch_react_f32(const Rx<float>& r, cudaStream_t st);
 void launch_react_f64(const Rx<double>& r, cudaStream_t st);
 void launch_stats_f32(const float* u, long long count, double* acc, cudaStream_t st);
+// *flag |= 1 if the byte ranges a and b (16-byte aligned, length a multiple of 4) differ.
+void launch_differ(const void* a, const void* b, size_t bytes, unsigned* flag, cudaStream_t st);
 void launch_stats_f64(const double* u, long long count, double* acc, cudaStream_t st);
 
 // tcgen05 transform pass (gemm_tc.cu)

@@ -245,6 +245,29 @@ __global__ void __launch_bounds__(256) stats_kernel(const T* __restrict__ u, lon
     }
 }
 
+// flag |= 1 if the two arrays of `words` 32-bit words differ anywhere (bitwise).
+__global__ void __launch_bounds__(256) differ_kernel(const uint4* __restrict__ a, const uint4* __restrict__ b,
+                                                     long long n16, const uint32_t* __restrict__ ta,
+                                                     const uint32_t* __restrict__ tb, int tail, unsigned* flag) {
+    unsigned d = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) {
+        const uint4 x = a[i], y = b[i];
+        d |= (x.x ^ y.x) | (x.y ^ y.y) | (x.z ^ y.z) | (x.w ^ y.w);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < tail) d |= ta[threadIdx.x] ^ tb[threadIdx.x];
+    if (__any_sync(0xffffffffu, d != 0) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+void launch_differ(const void* a, const void* b, size_t bytes, unsigned* flag, cudaStream_t st) {
+    const long long n16 = (long long)(bytes / 16);
+    const int tail = (int)((bytes % 16) / 4);
+    const uint32_t* ta = reinterpret_cast<const uint32_t*>(static_cast<const char*>(a) + n16 * 16);
+    const uint32_t* tb = reinterpret_cast<const uint32_t*>(static_cast<const char*>(b) + n16 * 16);
+    differ_kernel<<<grid_for(n16, 256), 256, 0, st>>>(static_cast<const uint4*>(a), static_cast<const uint4*>(b), n16,
+                                                       ta, tb, tail, flag);
+}
+
 void launch_stats_f32(const float* u, long long count, double* acc, cudaStream_t st) {
     stats_kernel<float><<<grid_for(count, 256), 256, 0, st>>>(u, count, (unsigned long long*)acc);
 }

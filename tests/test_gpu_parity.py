@@ -193,6 +193,37 @@ def test_host_entry_point_and_stats():
 
 
 @pytest.mark.gpu
+def test_host_loop_keeps_state_and_notices_edits():
+    """etd_step_host in a loop: handing back the field it returned keeps the
+    carried spectral state (the result equals one device call of all the steps);
+    an edited field is noticed and stepped from scratch."""
+    torch = need_gpu()
+    n = 96
+    u0 = inputs.fhn_uniform(n, 2, workload=12)
+    kw = dict(precision="bf16x6", reaction="fhn", rx_params=FHN, n_comp=2, kappa_comp=(1e-3, 5e-3))
+    plan = etd.Plan(2, n, 1e-3, 0.0, 1e-2, **kw)
+    host = torch.tensor(u0, dtype=torch.float32).pin_memory()
+    for _ in range(3):
+        plan.step_host(host, 4)
+    dplan = etd.Plan(2, n, 1e-3, 0.0, 1e-2, **kw)
+    dev = torch.tensor(u0, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        dplan.step(dev, 4)
+    dplan.sync()
+    assert torch.equal(host, dev.cpu())  # same carried state, same launches
+    ref = oracle_ref(2, n, (1e-3, 5e-3), 0.0, 1e-2, u0, 12, "fhn", FHN)
+    assert rel_err(host.double().numpy(), ref) < 1e-6
+    # an edit: the next call must rebuild the state from the edited field
+    host[0, 10, 10] += 0.05
+    edited = host.double().numpy().copy()
+    plan.step_host(host, 4)
+    ref2 = oracle_ref(2, n, (1e-3, 5e-3), 0.0, 1e-2, edited, 4, "fhn", FHN)
+    assert rel_err(host.double().numpy(), ref2) < 1e-6
+    plan.close()
+    dplan.close()
+
+
+@pytest.mark.gpu
 def test_bad_field_arguments():
     torch = need_gpu()
     plan = etd.Plan(2, 64, 0.01, 0.0, 1e-3, precision="tf32x3")
