@@ -156,6 +156,10 @@ etd_status etd_step(etd_plan* p, void* u_dev, int n_steps);
  * Same as etd_step for a HOST array u_host: copies it to a plan-owned device
  * field, advances n_steps, copies the result back and synchronises. Page-locked
  * host memory gives asynchronous copies; pageable memory works but is slower.
+ * When u_host holds exactly (bit for bit) the field the previous call returned,
+ * as in a host-side time-stepping loop, the carried spectral state is kept (a
+ * device-side comparison of the copied field decides); any other content
+ * rebuilds it, as etd_step does for a new field.
  */
 etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps);
 
