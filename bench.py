@@ -39,6 +39,10 @@ WORKLOADS = {
     "fhn2d_2048": (2, 2048, 1e-3, 5e-3, 0.0, 1e-2, "fhn",
                    "2D FitzHugh-Nagumo n=2048 (2 fields), kappa_u=1e-3 kappa_v=5e-3 eps=0.01 a=0.5 b=0.1 tau=1e-2"),
     "ac3d_256": (3, 256, 1e-3, None, 0.1, 5e-3, "allen_cahn", "3D Allen-Cahn n=256, kappa=1e-3 q=0.1 tau=5e-3"),
+    # grids with n + 1 a power of two, for the fast sine transform comparison (--precision dst32)
+    "fhn2d_4095": (2, 4095, 1e-3, 5e-3, 0.0, 1e-2, "fhn",
+                   "2D FitzHugh-Nagumo n=4095 (2 fields), kappa_u=1e-3 kappa_v=5e-3 eps=0.01 a=0.5 b=0.1 tau=1e-2"),
+    "ac3d_255": (3, 255, 1e-3, None, 0.1, 5e-3, "allen_cahn", "3D Allen-Cahn n=255, kappa=1e-3 q=0.1 tau=5e-3"),
     "ac3d_384": (3, 384, 1e-3, None, 0.1, 5e-3, "allen_cahn", "3D Allen-Cahn n=384, kappa=1e-3 q=0.1 tau=5e-3"),
     "ac2d_64": (2, 64, 1e-2, None, 0.0, 1e-3, "allen_cahn", "2D Allen-Cahn n=64, kappa=1e-2 q=0 tau=1e-3"),
     "ensemble512": (2, None, None, 5e-3, 0.0, None, "fhn",

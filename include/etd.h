@@ -53,7 +53,11 @@ enum {
     ETD_PREC_BF16X3 = 4, /* float fields, BF16 hi/lo split, three products */
     ETD_PREC_BF16X6 = 5, /* float fields, BF16 hi/mid/lo split, six products in every pass,
                             correction products in their own accumulator (most accurate) */
-    ETD_PREC_TF32X6 = 6  /* float fields, TF32 hi/mid/lo split, six products, as BF16X6 */
+    ETD_PREC_TF32X6 = 6, /* float fields, TF32 hi/mid/lo split, six products, as BF16X6 */
+    ETD_PREC_DST32 = 7   /* float fields, every transform as fast sine transforms (FFT-based DST-I
+                            in FP32 on CUDA cores) instead of the dense product with P: a
+                            comparison path, not the paper's dense-eigenbasis method; needs
+                            m + 1 a power of two, 16 <= m + 1 <= 8192 */
 };
 /* In every split mode (X3, X6) the two transforms whose error stays in the
  * result, U -> U^ when the carried spectral state is (re)built and the

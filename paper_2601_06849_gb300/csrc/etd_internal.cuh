@@ -405,6 +405,10 @@ void launch_gemm_simt_f32(const float* A, const float* P, int M, int n, int nbat
 void launch_gemm_simt_f64(const double* A, const double* P, int M, int n, int nbatch, const Epi<double>& e,
                           cudaStream_t st);
 void launch_react_f32(const Rx<float>& r, cudaStream_t st);
+// ETD_PREC_DST32: one transform pass as FFT-based DST-I of every row of A
+// (n + 1 a power of two), through tmp (nbatch * M rows of pitch ld) and the epilogue.
+cudaError_t launch_dst_pass(const float* A, int M, int n, int nbatch, int ld, long long bs, const float2* tw,
+                            float* tmp, const Epi<float>& e, cudaStream_t st);
 void launch_react_f64(const Rx<double>& r, cudaStream_t st);
 void launch_stats_f32(const float* u, long long count, double* acc, cudaStream_t st);
 // *flag |= 1 if the byte ranges a and b (16-byte aligned, length a multiple of 4) differ.

@@ -59,6 +59,9 @@ struct etd_plan {
     long long bs = 0, npts = 0;
     size_t elem = 4;
     bool use_tc = false;
+    bool dst = false;         // ETD_PREC_DST32: FFT-based sine transforms instead of products with P
+    float2* dst_tw = nullptr; // its FFT twiddles by stage (N - 1 of them, N = 2(n+1))
+    void* dst_tmp = nullptr;  // its natural-order scratch rows
     bool bf16 = false;  // BF16 operand pieces (ETD_PREC_BF16X3 / X6)
     size_t op_elem = 4; // bytes per operand-plane value
     int pieces = 1;     // operand planes allocated per buffer
@@ -213,7 +216,8 @@ void free_plan(etd_plan* p) {
         if (ev) cudaEventDestroy(ev);
     void* bufs[] = {p->P[0],     p->P[1],     p->P[2],     p->grid,     p->grid2,    p->uhat,     p->zhat,
                     p->wphys,    p->op[0][0], p->op[0][1], p->op[0][2], p->op[1][0],
-                    p->op[1][1], p->op[1][2], p->err,      p->stats,    p->host_field, p->host_in};
+                    p->op[1][1], p->op[1][2], p->err,      p->stats,    p->host_field, p->host_in,
+                    p->dst_tw,   p->dst_tmp};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->maps) tc_maps_destroy(p->maps);
@@ -301,6 +305,12 @@ etd_status run_pass(etd_plan* p, int cur, int slot, int mode, int out_split, voi
             cudaError_t ce =
                 launch_gemm_tc(p->tc[slot], slot, p->maps, cur, p->M, p->n, p->ninst * p->ncomp, e, p->err, p->stream);
             if (ce != cudaSuccess) return fail(ETD_ERR_CUDA, "tensor-core pass launch: %s", cudaGetErrorString(ce));
+            return ETD_OK;
+        }
+        if (p->dst) {
+            cudaError_t ce = launch_dst_pass((const float*)p->op[cur][0], p->M, p->n, p->ninst * p->ncomp, p->ld,
+                                             p->bs, p->dst_tw, (float*)p->dst_tmp, e, p->stream);
+            if (ce != cudaSuccess) return fail(ETD_ERR_CUDA, "sine transform pass: %s", cudaGetErrorString(ce));
             return ETD_OK;
         }
         launch_gemm_simt_f32((const float*)p->op[cur][0], (const float*)p->P[0], p->M, p->n, p->ninst * p->ncomp,
@@ -637,7 +647,12 @@ etd_status validate_options(int d, int m, int pade_order, const etd_options& opt
     if ((opt.reaction == ETD_RX_ALLEN_CAHN || opt.reaction == ETD_RX_SINGULAR || opt.reaction == ETD_RX_AC_FORCED) &&
         opt.n_comp != 1)
         return fail(ETD_ERR_INVALID_ARG, "this reaction needs n_comp = 1");
-    if (opt.precision < ETD_PREC_FP64 || opt.precision > ETD_PREC_TF32X6)
+    if (opt.precision == ETD_PREC_DST32) {
+        const int N = m + 1;
+        if (N < 16 || N > 8192 || (N & (N - 1)))
+            return fail(ETD_ERR_UNSUPPORTED, "ETD_PREC_DST32 needs m + 1 a power of two in [16, 8192] (m = %d)", m);
+    }
+    if (opt.precision < ETD_PREC_FP64 || opt.precision > ETD_PREC_DST32)
         return fail(ETD_ERR_INVALID_ARG, "unknown precision");
     return ETD_OK;
 }
@@ -755,6 +770,7 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     p->use_tc = p->bf16 || opt.precision == ETD_PREC_TF32 || opt.precision == ETD_PREC_TF32X3 ||
                 opt.precision == ETD_PREC_TF32X6;
     p->op_elem = p->bf16 ? 2 : p->elem;
+    p->dst = opt.precision == ETD_PREC_DST32;
     const int n = m;
     const int nb = ninst * p->ncomp;
     p->M = (d == 2) ? n : n * n;
@@ -817,7 +833,10 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     const size_t state_bytes = (size_t)nb * p->bs * sizeof(double);
     const size_t pbytes = (size_t)n * p->ld * p->op_elem;
     const size_t op_bytes = (size_t)nb * p->bs * p->op_elem;
-    for (int j = 0; j < p->pieces && s == ETD_OK; ++j) s = dalloc(p, &p->P[j], pbytes);
+    // the sine-transform path needs no P: its twiddles and a scratch field instead
+    for (int j = 0; j < (p->dst ? 0 : p->pieces) && s == ETD_OK; ++j) s = dalloc(p, &p->P[j], pbytes);
+    if (s == ETD_OK && p->dst) s = dalloc(p, (void**)&p->dst_tw, sizeof(float2) * (size_t)(2 * (n + 1) - 1));
+    if (s == ETD_OK && p->dst) s = dalloc(p, &p->dst_tmp, field_bytes);
     if (s == ETD_OK) s = dalloc(p, &p->grid, (size_t)nb * 3 * n * sizeof(double));
     if (s == ETD_OK) s = dalloc(p, &p->grid2, (size_t)nb * 3 * n * 2 * sizeof(float));
     if (s == ETD_OK) s = dalloc(p, &p->uhat, state_bytes);
@@ -834,7 +853,18 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     // P in its pieces: FP64 for ETD_PREC_FP64, FP32 for FP32 products, TF32
     // pieces (each rounded from the FP64 remainder) for the tensor-core modes
     cudaError_t ce = cudaSuccess;
-    for (int j = 0; j < p->pieces && ce == cudaSuccess; ++j) {
+    if (p->dst) {  // FFT twiddles by stage: half - 1 + pos -> e^{-i pi pos / half}, half = 1, 2, .., N/2
+        const int N = 2 * (n + 1);
+        std::vector<float2> tw((size_t)(N - 1));
+        const double pi = 3.14159265358979323846;
+        for (int half = 1; half < N; half *= 2)
+            for (int pos = 0; pos < half; ++pos) {
+                const double a = -pi * pos / half;
+                tw[(size_t)(half - 1 + pos)] = make_float2((float)std::cos(a), (float)std::sin(a));
+            }
+        ce = cudaMemcpy(p->dst_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    }
+    for (int j = 0; j < (p->dst ? 0 : p->pieces) && ce == cudaSuccess; ++j) {
         std::vector<char> hostbuf(pbytes, 0);
         for (int r = 0; r < n; ++r)
             for (int k = 0; k < n; ++k) {

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libetd.so")
 
 ETD_OK, ETD_ERR_INVALID_ARG, ETD_ERR_OOM, ETD_ERR_CUDA, ETD_ERR_UNSUPPORTED, ETD_ERR_DIVERGED, ETD_ERR_TIMEOUT = range(7)
-PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4, "bf16x6": 5, "tf32x6": 6}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4, "bf16x6": 5, "tf32x6": 6, "dst32": 7}
 REACTION = {"none": 0, "linear": 1, "allen_cahn": 2, "fhn": 3, "singular": 4, "ac_forced": 5}
 FAMILY = {"exact": 0, 2: 2, 4: 4, 0: 0}
 
