@@ -9,8 +9,9 @@
 // has the purely imaginary DFT Z_k = -2i sum_j x_j sin(pi j' k/(n+1)) (j' = j+1),
 // so y_k = -Im Z_{k+1} / 2. Two real rows a and b ride in one complex FFT
 // (z = z_a + i z_b): Z = i A - B with A, B real, so y_a = -Im Z / 2 and
-// y_b = Re Z / 2. The FFT is an iterative radix-2 decimation in time in shared
-// memory. Twiddles come from a host table computed in FP64 and laid out by stage
+// y_b = Re Z / 2. The FFT is an iterative decimation in time in shared memory,
+// two radix-2 stages per round (radix 4) after one single stage when log2 N is
+// odd. Twiddles come from a host table computed in FP64 and laid out by stage
 // (stage s, half = 2^s: entries half - 1 + pos = e^{-i pi pos / half}), so the
 // lanes of a warp read consecutive entries; read with the stride of one table
 // e^{-2 pi i k / N} they all hit one shared-memory bank.
@@ -65,19 +66,43 @@ __global__ void __launch_bounds__(512) dst_rows_kernel(const float* __restrict__
             }
         }
         __syncthreads();
-        for (int s = 0; s < logN; ++s) {
-            const int half = 1 << s;
+        int s = 0;
+        if (logN & 1) {  // one radix-2 stage (half = 1) when log2 N is odd
             for (int qq = threadIdx.x; qq < ((N / 2) << logG); qq += blockDim.x) {
                 const int g = qq >> (logN - 1), q = qq & (N / 2 - 1);
+                const int pi = g * NP + pad32(2 * q), pj = g * NP + pad32(2 * q + 1);
+                const float2 a = z[pi], b = z[pj];
+                z[pi] = make_float2(a.x + b.x, a.y + b.y);
+                z[pj] = make_float2(a.x - b.x, a.y - b.y);
+            }
+            __syncthreads();
+            s = 1;
+        }
+        // radix-4 rounds: stages s (half) and s + 1 (2 half) in registers
+        for (; s < logN; s += 2) {
+            const int half = 1 << s;
+            for (int qq = threadIdx.x; qq < ((N / 4) << logG); qq += blockDim.x) {
+                const int g = qq >> (logN - 2), q = qq & (N / 4 - 1);
                 const int pos = q & (half - 1);
-                const int i = ((q >> s) << (s + 1)) + pos;
-                const int pi = g * NP + pad32(i), pj = g * NP + pad32(i + half);
-                const float2 w = tw[half - 1 + pos];
-                const float2 b = z[pj];
-                const float2 t = make_float2(w.x * b.x - w.y * b.y, w.x * b.y + w.y * b.x);
-                const float2 a = z[pi];
-                z[pi] = make_float2(a.x + t.x, a.y + t.y);
-                z[pj] = make_float2(a.x - t.x, a.y - t.y);
+                const int i0 = ((q >> s) << (s + 2)) + pos;
+                const int p0 = g * NP + pad32(i0), p1 = g * NP + pad32(i0 + half);
+                const int p2 = g * NP + pad32(i0 + 2 * half), p3 = g * NP + pad32(i0 + 3 * half);
+                float2 x0 = z[p0], x1 = z[p1], x2 = z[p2], x3 = z[p3];
+                const float2 w1 = tw[half - 1 + pos];            // stage s
+                const float2 wa = tw[2 * half - 1 + pos];        // stage s + 1, first half
+                const float2 wb = tw[2 * half - 1 + pos + half]; // stage s + 1, second half
+                float2 t = make_float2(w1.x * x1.x - w1.y * x1.y, w1.x * x1.y + w1.y * x1.x);
+                x1 = make_float2(x0.x - t.x, x0.y - t.y);
+                x0 = make_float2(x0.x + t.x, x0.y + t.y);
+                t = make_float2(w1.x * x3.x - w1.y * x3.y, w1.x * x3.y + w1.y * x3.x);
+                x3 = make_float2(x2.x - t.x, x2.y - t.y);
+                x2 = make_float2(x2.x + t.x, x2.y + t.y);
+                t = make_float2(wa.x * x2.x - wa.y * x2.y, wa.x * x2.y + wa.y * x2.x);
+                z[p2] = make_float2(x0.x - t.x, x0.y - t.y);
+                z[p0] = make_float2(x0.x + t.x, x0.y + t.y);
+                t = make_float2(wb.x * x3.x - wb.y * x3.y, wb.x * x3.y + wb.y * x3.x);
+                z[p3] = make_float2(x1.x - t.x, x1.y - t.y);
+                z[p1] = make_float2(x1.x + t.x, x1.y + t.y);
             }
             __syncthreads();
         }
