@@ -45,6 +45,10 @@ WORKLOADS = {
     "ac3d_255": (3, 255, 1e-3, None, 0.1, 5e-3, "allen_cahn", "3D Allen-Cahn n=255, kappa=1e-3 q=0.1 tau=5e-3"),
     "ac3d_384": (3, 384, 1e-3, None, 0.1, 5e-3, "allen_cahn", "3D Allen-Cahn n=384, kappa=1e-3 q=0.1 tau=5e-3"),
     "ac2d_64": (2, 64, 1e-2, None, 0.0, 1e-3, "allen_cahn", "2D Allen-Cahn n=64, kappa=1e-2 q=0 tau=1e-3"),
+    "adjoint3d_128": (3, 128, 1e-3, 5e-3, 0.0, 1e-2, "fhn",
+                      "gradient of ||u(T) - u_target||^2 over 400 steps of 3D FitzHugh-Nagumo n=128 (2 fields), "
+                      "kappa_u=1e-3 kappa_v=5e-3 eps=0.01 a=0.5 b=0.1 tau=1e-2, checkpoints every 20 steps; "
+                      "u_target from the same run at kappa_u (1 + 1e-2)"),
     "ensemble512": (2, None, None, 5e-3, 0.0, None, "fhn",
                     "512 independent 2D FitzHugh-Nagumo instances, n uniform on {64,96,...,512}, kappa_u log-uniform "
                     "[1e-4,1e-2], tau uniform [1e-3,1e-2], kappa_v=5e-3 eps=0.01 a=0.5 b=0.1"),
@@ -52,6 +56,120 @@ WORKLOADS = {
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
 KERNEL_FILES = ["paper_2601_06849_gb300/csrc/gemm_tc.cu", "paper_2601_06849_gb300/csrc/etd_internal.cuh"]
 L2_BYTES = 129e6
+
+
+def run_adjoint(args, world, rank, local):
+    """Gradient workload: one timed iteration = forward solve over the window
+    (checkpoints every 20 steps) + loss + backward through the library's adjoint
+    steps (each segment recomputes its forward states on the device)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2601_06849_gb300 import autograd as AG
+    from paper_2601_06849_gb300 import etd, inputs
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    d, n, ku, kv, q, tau, rx, desc = WORKLOADS[args.workload]
+    window, every = 400, 20
+    u0 = torch.tensor(inputs.fhn_uniform(n, d, workload=4), dtype=torch.float32, device="cuda")
+    target = u0.clone()
+    tplan = etd.Plan(d, n, ku * (1 + 1e-2), q, tau, precision=args.precision, reaction="fhn", rx_params=FHN, n_comp=2,
+                     kappa_comp=(ku * (1 + 1e-2), kv))
+    tplan.step(target, window)
+    tplan.sync()
+    tplan.close()
+
+    u0_host = u0.cpu().pin_memory()
+
+    def iteration(src=None):
+        # src: pinned host copy of the initial field (the end-to-end leg copies it in)
+        u0_ = (u0.clone() if src is None else src.to("cuda", non_blocking=True)).requires_grad_(True)
+        kap = torch.tensor([ku, kv], dtype=torch.float64, requires_grad=True)
+        rp = torch.tensor(FHN, dtype=torch.float64, requires_grad=True)
+        u = AG.solve(u0_, kap, rp, d=d, n=n, q=q, dt=tau, n_steps=window, precision=args.precision, reaction="fhn",
+                     checkpoint_every=every)
+        loss = ((u - target) ** 2).sum()
+        loss.backward()
+        torch.cuda.synchronize()
+        return float(loss), kap.grad.clone(), rp.grad.clone()
+
+    iters = max(1, min(args.steps, 3))
+    for _ in range(args.warmup):
+        iteration()
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            loss, gk, gr = iteration()
+        el = time.perf_counter() - t0
+    el_max = barrier_max(el, world)
+    # end to end: the initial field copied in from pinned host memory, loss and
+    # gradients read back, every iteration
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        iteration(u0_host)
+    el_e2e = barrier_max(time.perf_counter() - t0, world)
+    unknowns = 2 * n ** d
+    value = world * unknowns * window * iters / el_max
+    # transform flops of an iteration: forward (4d passes per step), the recomputed
+    # forward and the adjoint's 9 transforms (d passes each) per step, 2 n^(d+1) per
+    # pass and component, times the split products
+    products = {"fp64": 1, "fp32": 1, "tf32": 1, "tf32x3": 3, "bf16x3": 3, "bf16x6": 6, "tf32x6": 6}.get(
+        args.precision, 1)
+    passes = window * (4 * d + 4 * d + 9 * d)
+    flops = passes * 2.0 * n ** (d + 1) * 2 * products * iters
+    peaks, src = measured_peaks()
+    bf16_mode = args.precision.startswith("bf16")
+    tpeak = peaks["bf16_tflops_sustained"] * (1.0 if bf16_mode else TF32_OVER_BF16)
+    achieved = flops / el_max / 1e12
+    line = {
+        "metric": "unknown-updates/s per ETD2RK-DS step (forward + adjoint)", "value": value,
+        "unit": "unknown-updates/s", "n_gpus": world, "steps": iters, "warmup": args.warmup,
+        "ms_per_step": el_max / iters / window * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": f"{args.precision} (f32 fields, double-float spectral state)",
+        "data": "synthetic",
+        "config": {"workload": desc, "d": d, "n": n, "window": window, "checkpoint_every": every,
+                   "precision": args.precision, "step": "one forward + backward solve over the window",
+                   "l2": "working set > 129 MB L2 (fields, checkpoints, adjoint workspace): no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": tpeak, "unit": "TFLOP/s",
+                     "frac": achieved / tpeak, "traffic": None,
+                     "kernel": "all transform passes of forward, recomputed forward and adjoint (whole-iteration rate)",
+                     "peak_source": f"{src}: bf16_tflops_sustained" + ("" if bf16_mode else " x 1.1/2.25")},
+        # per time step: forward (2 reactions + 4d passes), the segment's recomputed
+        # forward (the same), the adjoint step (9 transforms of 1 + d launches, 4
+        # spectral combinations, 2 Jacobian products, 2 gradient reductions)
+        "gpu_launches": iters * window * (2 * (2 + 4 * d) + 9 * (1 + d) + 8),
+        "e2e": {"value": world * unknowns * window * iters / el_e2e, "unit": "unknown-updates/s",
+                "h2d_bytes_per_step": 4 * unknowns, "d2h_bytes_per_step": 4 + 8 * 6,
+                "per": "iteration (one forward + backward over the window)",
+                "api": "torch.autograd through autograd.solve, initial field from pinned host memory, "
+                       "loss and gradients read back"},
+        "loss": loss, "grad_kappa": [float(x) for x in gk], "grad_rx": [float(x) for x in gr],
+    }
+    cs = clocks.summary()
+    if cs:
+        line["clocks"] = cs
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import adjoint as OA
+        from oracle import oracle as O
+
+        steps = 3
+        P = O.Problem(d=d, n=n, kappa=(ku, kv), q=q, tau=tau, reaction="fhn", rp=FHN)
+        x0 = u0.double().cpu().numpy()
+        t0 = time.perf_counter()
+        OA.adjoint_run(P, x0, steps, np.ones_like(x0))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": unknowns * steps / dt, "unit": "unknown-updates/s", "cores": O.max_threads(),
+                                "kind": "oracle", "sample": f"FP64 NumPy adjoint oracle, {steps} forward + {steps} "
+                                                            f"adjoint steps of the same 3D problem", "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_ensemble(args, world, rank, local):
@@ -379,6 +497,9 @@ def main():
 
     if args.workload == "ensemble512":
         run_ensemble(args, world, rank, local)
+        return
+    if args.workload == "adjoint3d_128":
+        run_adjoint(args, world, rank, local)
         return
 
     import torch
