@@ -80,7 +80,7 @@ constexpr int RX_PER_LANE = RX_SEG / 32;
 
 // f(t, u) at one point: component values a (u) and b (v), x index, and the y [z]
 // factor u0yz of the manufactured solution (ETD_RX_AC_FORCED).
-template <typename T>
+template <typename T, bool FORCED>
 __device__ __forceinline__ void rx_eval(const Rx<T>& r, T a, T b, int x, double u0yz, T& f0, T& f1) {
     f0 = (T)0;
     f1 = (T)0;
@@ -95,13 +95,14 @@ __device__ __forceinline__ void rx_eval(const Rx<T>& r, T a, T b, int x, double 
         case ETD_RX_SINGULAR:
             f0 = r.rp[0] * a / ((T)1 - a);
             break;
-        case ETD_RX_AC_FORCED: {
-            // u0 = prod sin(pi x_axis) at x_i = (i+1)/(n+1); psi in FP64
-            const double ue = r.decay * u0yz * sinpi((double)(x + 1) / (double)(r.n + 1));
-            const double psi = r.psi_coef * ue - ue * (1.0 - ue * ue);
-            f0 = (T)((double)a * (1.0 - (double)a * (double)a) + psi);
+        case ETD_RX_AC_FORCED:
+            if constexpr (FORCED) {
+                // u0 = prod sin(pi x_axis) at x_i = (i+1)/(n+1); psi in FP64
+                const double ue = r.decay * u0yz * sinpi((double)(x + 1) / (double)(r.n + 1));
+                const double psi = r.psi_coef * ue - ue * (1.0 - ue * ue);
+                f0 = (T)((double)a * (1.0 - (double)a * (double)a) + psi);
+            }
             break;
-        }
         case ETD_RX_LINEAR:
             f0 = r.rp[0] * a;
             f1 = r.rp[0] * b;
@@ -115,8 +116,11 @@ __device__ __forceinline__ void rx_eval(const Rx<T>& r, T a, T b, int x, double 
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
+// FORCED: the manufactured-solution reaction (FP64 forcing term) only; the
+// other reactions run in a variant with at most 64 registers per thread (four
+// resident blocks of loads in flight per SM instead of three).
+template <typename T, bool FORCED>
+__global__ void __launch_bounds__(256, FORCED ? 1 : 4) react_kernel(const Rx<T> r) {
     const int lane = threadIdx.x & 31;
     const long long rows_inst = r.npts / r.n;  // n^(d-1) rows per instance
     const int nseg = (r.n + RX_SEG - 1) / RX_SEG;
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
         const T* __restrict__ in = r.in + inst * r.ncomp * r.bs_in + row * r.ld_in;
         const long long oo = inst * r.ncomp * r.bs_out + row * r.ld_out;
         double u0yz = 1.0;  // ETD_RX_AC_FORCED: the y [and z] factors of u0 on this row
-        if (r.kind == ETD_RX_AC_FORCED) {
+        if (FORCED) {
             const double inv = 1.0 / (double)(r.n + 1);
             const long long y = row % r.n, z = row / r.n;
             u0yz = sinpi((double)(y + 1) * inv);
@@ -157,8 +161,8 @@ __global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
                     const int x = xs + 2 * lane + 64 * j;
                     if (x >= r.n) continue;
                     float fa0, fa1, fb0, fb1;
-                    rx_eval(r, u[j].x, v[j].x, x, u0yz, fa0, fa1);
-                    rx_eval(r, u[j].y, v[j].y, x + 1, u0yz, fb0, fb1);
+                    rx_eval<T, FORCED>(r, u[j].x, v[j].x, x, u0yz, fa0, fa1);
+                    rx_eval<T, FORCED>(r, u[j].y, v[j].y, x + 1, u0yz, fb0, fb1);
                     // component offsets go into the element index, never into pointer
                     // arithmetic: the operand planes hold 4-byte or 2-byte values
                     store_split2(r.out_hi, r.out_lo, r.out_lo2, oo + x, fa0, fb0, r.split);
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(256) react_kernel(const Rx<T> r) {
             const int x = xs + lane + 32 * j;
             if (x >= r.n) continue;
             T f0, f1;
-            rx_eval(r, u[j], v[j], x, u0yz, f0, f1);
+            rx_eval<T, FORCED>(r, u[j], v[j], x, u0yz, f0, f1);
             store_split(r.out_hi, r.out_lo, r.out_lo2, oo + x, f0, r.split);
             if (r.ncomp > 1) store_split(r.out_hi, r.out_lo, r.out_lo2, oo + r.bs_out + x, f1, r.split);
         }
@@ -195,16 +199,38 @@ static int grid_for(long long work, int threads) {
     return (int)blocks;
 }
 
-template <typename T>
+// One warp per task, at most the blocks that are resident at once (the warps
+// then stride over the tasks; no second wave of blocks).
+template <typename T, bool FORCED>
 static int react_grid(const Rx<T>& r) {
+    static int resident = 0;
+    if (!resident) {
+        int dev = 0, sms = 0, occ = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, react_kernel<T, FORCED>, 256, 0) != cudaSuccess ||
+            sms <= 0 || occ <= 0) {
+            sms = 152;
+            occ = 4;
+        }
+        resident = sms * occ;
+    }
     const long long tasks = (r.npts / r.n) * r.ninst * ((r.n + RX_SEG - 1) / RX_SEG);
-    return grid_for(tasks * 32, 256);  // one warp per task
+    long long blocks = (tasks + 7) / 8;
+    if (blocks > resident) blocks = resident;
+    return (int)(blocks < 1 ? 1 : blocks);
 }
 void launch_react_f32(const Rx<float>& r, cudaStream_t st) {
-    react_kernel<float><<<react_grid(r), 256, 0, st>>>(r);
+    if (r.kind == ETD_RX_AC_FORCED)
+        react_kernel<float, true><<<react_grid<float, true>(r), 256, 0, st>>>(r);
+    else
+        react_kernel<float, false><<<react_grid<float, false>(r), 256, 0, st>>>(r);
 }
 void launch_react_f64(const Rx<double>& r, cudaStream_t st) {
-    react_kernel<double><<<react_grid(r), 256, 0, st>>>(r);
+    if (r.kind == ETD_RX_AC_FORCED)
+        react_kernel<double, true><<<react_grid<double, true>(r), 256, 0, st>>>(r);
+    else
+        react_kernel<double, false><<<react_grid<double, false>(r), 256, 0, st>>>(r);
 }
 
 // acc[0] = max |u| (as the bit pattern of a non-negative double, so an
