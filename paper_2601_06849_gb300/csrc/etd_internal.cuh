@@ -59,6 +59,12 @@ __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float(r);
 }
 
+// Two floats that hold BF16 values exactly, packed as a bfloat162 word (a low).
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
 // ---- double-float arithmetic ----
 // A double-float is the unevaluated sum x + y of two floats with |y| <= ulp(x)/2,
 // about 48 significant bits. GB300 runs FP64 at a small fraction of its FP32
@@ -270,6 +276,142 @@ __device__ __forceinline__ void epi_apply_batch(const Epi<float>& e, int b, int 
                 e.write_operand_ff(o, u);
             }
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row-vector epilogue (FP32 paths): eight consecutive rows ml0 .. ml0+7 of one
+// (component, mh) and one column nn, so every store and state load of the
+// batch is a 16-byte access along the contiguous ml direction instead of eight
+// 2- to 8-byte accesses at the column stride. The per-element arithmetic is the
+// same as in epi_apply_batch (results are bitwise identical). Valid only when
+// epi_rows8_ok() holds on the host (n, pitches and strides multiples of 8,
+// 16-byte aligned planes); ml0 is then a multiple of 8.
+__host__ __device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+inline bool epi_rows8_ok(const Epi<float>& e) {
+    if (e.n % 8 != 0 || e.ld % 8 != 0 || e.bs % 8 != 0) return false;
+    if (!aligned16(e.op_hi) || !aligned16(e.op_lo) || !aligned16(e.op_lo2)) return false;
+    if (!aligned16(e.uhat) || !aligned16(e.zhat) || !aligned16(e.grid)) return false;
+    if (e.mode == EPI_PLAIN && (e.ld_dst % 8 != 0 || e.bs_dst % 8 != 0 || !aligned16(e.dst))) return false;
+    return true;
+}
+
+__device__ __forceinline__ void epi_load_rows8(const Epi<float>& e, int b, int mh, int ml0, int nn, float4 (&st)[4]) {
+    if (!e.reads_state()) return;
+    const float4* src = reinterpret_cast<const float4*>(e.state_in() + (long long)b * e.bs +
+                                                        ((long long)nn * e.mq + mh) * e.ld + ml0);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) st[i] = __ldg(src + i);  // state_in is never written by the same pass
+}
+
+__device__ __forceinline__ void store8(float* d, const float (&x)[8]) {
+    reinterpret_cast<float4*>(d)[0] = make_float4(x[0], x[1], x[2], x[3]);
+    reinterpret_cast<float4*>(d)[1] = make_float4(x[4], x[5], x[6], x[7]);
+}
+
+__device__ __forceinline__ void store8_ff(float2* d, const float2 (&w)[8]) {
+    float4* q = reinterpret_cast<float4*>(d);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) q[i] = make_float4(w[2 * i].x, w[2 * i].y, w[2 * i + 1].x, w[2 * i + 1].y);
+}
+
+// Operand pieces of eight double-float values at o .. o+7 (write_operand_ff per
+// element), packed as they are formed: one 16-byte store per BF16 piece plane,
+// two per TF32 plane.
+__device__ __forceinline__ void write_operand_ff8(const Epi<float>& e, long long o, const float2 (&w)[8]) {
+    if (e.split == SPLIT_BF16_2 || e.split == SPLIT_BF16_3) {
+        uint32_t h[4], l[4], l2[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float a[3], b[3];
+            ff_pieces<true>(w[2 * k], a);
+            ff_pieces<true>(w[2 * k + 1], b);
+            h[k] = bf16x2_bits(a[0], b[0]);
+            l[k] = bf16x2_bits(a[1], b[1]);
+            l2[k] = bf16x2_bits(a[2], b[2]);
+        }
+        *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(e.op_hi) + o) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(e.op_lo) + o) = make_uint4(l[0], l[1], l[2], l[3]);
+        if (e.split == SPLIT_BF16_3)
+            *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(e.op_lo2) + o) =
+                make_uint4(l2[0], l2[1], l2[2], l2[3]);
+        return;
+    }
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {  // four values per 16-byte store
+        float q0[4], q1[4], q2[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 x = w[4 * g + i];
+            if (e.split == SPLIT_TF32 || e.split == SPLIT_TF32_3) {
+                float q[3];
+                ff_pieces<false>(x, q);
+                q0[i] = q[0];
+                q1[i] = q[1];
+                q2[i] = q[2];
+            } else {
+                q0[i] = (e.split == SPLIT_TF32_HI) ? tf32_rna(x.x) : __fadd_rn(x.x, x.y);
+                q1[i] = q2[i] = 0.f;
+            }
+        }
+        reinterpret_cast<float4*>(e.op_hi + o)[g] = make_float4(q0[0], q0[1], q0[2], q0[3]);
+        if (e.split == SPLIT_TF32 || e.split == SPLIT_TF32_3)
+            reinterpret_cast<float4*>(e.op_lo + o)[g] = make_float4(q1[0], q1[1], q1[2], q1[3]);
+        if (e.split == SPLIT_TF32_3) reinterpret_cast<float4*>(e.op_lo2 + o)[g] = make_float4(q2[0], q2[1], q2[2], q2[3]);
+    }
+}
+
+__device__ __forceinline__ void epi_apply_rows8(const Epi<float>& e, int b, int mh, int ml0, int nn, const float (&v)[8],
+                                                const float4 (&st4)[4]) {
+    if (e.mode == EPI_PLAIN) {
+        store8(e.dst + (long long)b * e.bs_dst + ((long long)nn * e.mq + mh) * e.ld_dst + ml0, v);
+        return;
+    }
+    const long long o = (long long)b * e.bs + ((long long)nn * e.mq + mh) * e.ld + ml0;
+    float2 w[8];
+    if (e.mode == EPI_SPLIT || e.mode == EPI_CARRY) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] = make_float2(v[i], 0.f);
+        if (e.mode == EPI_SPLIT)
+            write_operand_ff8(e, o, w);
+        else
+            store8_ff(e.uhat + o, w);
+        return;
+    }
+    float2 st[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        st[2 * i] = make_float2(st4[i].x, st4[i].y);
+        st[2 * i + 1] = make_float2(st4[i].z, st4[i].w);
+    }
+    const float2* g = e.grid + (long long)b * 3 * e.n;
+    if (e.mode == EPI_STAGE1) {
+        const float2 sl = g[nn];
+        const float2 sj = (e.d == 2) ? sl : ff_mul(g[mh], sl);
+        float4* zq = reinterpret_cast<float4*>(e.zhat + o);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float2 z[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = 2 * k + h, ml = ml0 + i;
+                const float2 g1 = g[ml], g2 = g[e.n + ml], g3v = g[2 * e.n + ml];
+                const float g23 = __fsub_rn(g2.x, g3v.x) + g2.y - g3v.y;
+                const float2 t = ff_mul(g1, st[i]);
+                w[i] = ff_mul(ff_add_f(t, __fmul_rn(g2.x, v[i])), sj);
+                z[h] = ff_mul(ff_add_f(t, __fmul_rn(g23, v[i])), sj);
+            }
+            zq[k] = make_float4(z[0].x, z[0].y, z[1].x, z[1].y);
+        }
+        write_operand_ff8(e, o, w);
+        return;
+    }
+    if (e.mode == EPI_STAGE2) {  // U^+ = Z + tau E3 F_W^
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] = ff_add_f(st[i], __fmul_rn(g[2 * e.n + ml0 + i].x, v[i]));
+        store8_ff(e.uhat + o, w);
+        write_operand_ff8(e, o, w);
     }
 }
 

@@ -50,7 +50,8 @@ constexpr int WARP_MMA = 9;
 constexpr int WARP_MMA2 = 10;             // ACCURATE: issues the correction products
 constexpr int NUM_THREADS = 352;
 constexpr int MAX_HALF = 128;            // columns per epilogue warp (bn <= 256)
-constexpr int STAGE_BYTES_EPI = NUM_EPI_WARPS * 32 * MAX_HALF * 4;
+constexpr int EPI_CS = 36;               // staged column stride (floats): 32 rows + 4, no bank conflicts
+constexpr int STAGE_BYTES_EPI = NUM_EPI_WARPS * EPI_CS * MAX_HALF * 4;
 constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
 constexpr int SMEM_LIMIT = 227 * 1024 - 1024;  // dynamic bytes; leaves room for the static barriers
 
@@ -58,6 +59,7 @@ struct KParams {
     int M, n, bn, stages, products, pieces, tiles_m, tiles_n, tmem_cols;
     int acc_cols;  // columns of one accumulator region (power of two >= bn)
     int nbatch;
+    int vec;  // row-vector epilogue (epi_rows8_ok)
     unsigned stage_bytes, b_bytes, tx_bytes;
     unsigned* err;
     Epi<float> e;
@@ -533,14 +535,38 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             // the pipeline's shared memory is free: stage this warp's 32 x hcols sums
             // there column-major and apply the epilogue in a rolled loop (one copy
             // of its code instead of one per column).
-            float* stage = reinterpret_cast<float*>(smem) + (size_t)warp * 32 * MAX_HALF;
+            float* stage = reinterpret_cast<float*>(smem) + (size_t)warp * EPI_CS * MAX_HALF;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // after the TMA writes there
 #pragma unroll
             for (int c = 0; c < HALF; ++c)
-                if (c < hcols) stage[c * 32 + lane] = sum[c];
+                if (c < hcols) stage[c * EPI_CS + lane] = sum[c];
             __syncwarp();
             const int grow = tm * BM + quarter * 32 + lane;  // row of the stacked components
-            if (grow < p.nbatch * p.M) {
+            if (p.vec) {
+                // lane -> column cc of each group of 8, rows rr0 .. rr0+7 (16-byte accesses)
+                const int cc = lane >> 2, rr0 = (lane & 3) * 8;
+                const int grow0 = tm * BM + quarter * 32 + rr0;
+                const int nn0 = tn * p.bn + half * hcols;
+                const int cols = min(hcols, p.n - nn0);  // a multiple of 8
+                if (grow0 < p.nbatch * p.M) {
+                    const int b = grow0 / p.M, mm = grow0 - b * p.M;
+                    const int mh = mm / p.n, ml0 = mm - mh * p.n;
+                    float4 cur[4], nxt[4];
+                    if (cc < cols) epi_load_rows8(p.e, b, mh, ml0, nn0 + cc, cur);
+                    for (int c0 = 0; c0 < cols; c0 += 8) {
+                        const int c = c0 + cc;
+                        if (c + 8 < cols) epi_load_rows8(p.e, b, mh, ml0, nn0 + c + 8, nxt);
+                        if (c < cols) {
+                            const float4 a0 = *reinterpret_cast<const float4*>(stage + c * EPI_CS + rr0);
+                            const float4 a1 = *reinterpret_cast<const float4*>(stage + c * EPI_CS + rr0 + 4);
+                            const float v[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                            epi_apply_rows8(p.e, b, mh, ml0, nn0 + c, v, cur);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) cur[i] = nxt[i];
+                    }
+                }
+            } else if (grow < p.nbatch * p.M) {
                 const int b = grow / p.M, mm = grow - b * p.M;
                 const int mh = mm / p.n, ml = mm - mh * p.n;
                 const int nn0 = tn * p.bn + half * hcols;
@@ -552,7 +578,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     if (c0 + 16 < cols) epi_load_state<16>(p.e, b, mh, ml, nn0 + c0 + 16, min(16, cols - c0 - 16), nxt);
                     float v[16];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = stage[(c0 + i < hcols ? c0 + i : 0) * 32 + lane];
+                    for (int i = 0; i < 16; ++i) v[i] = stage[(c0 + i < hcols ? c0 + i : 0) * EPI_CS + lane];
                     epi_apply_batch<16>(p.e, b, mh, ml, nn0 + c0, v, min(16, cols - c0), cur);
 #pragma unroll
                     for (int i = 0; i < 16; ++i) cur[i] = nxt[i];
@@ -608,6 +634,8 @@ constexpr int WARP_MMA = 17;
 constexpr int WARP_MMA2 = 18;           // ACC: issues the correction products
 constexpr int THREADS = 19 * 32;
 constexpr int EPI_COLS = 8;             // columns per epilogue batch of a store thread
+constexpr int EPI_CS = 36;              // transposition buffer column stride (floats)
+constexpr int STATIC_SMEM = NUM_STORE * EPI_COLS * EPI_CS * 4 + 1024;  // buffers + barriers and flags
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t KB_COLS = 128;        // one TMEM region (k-block or staging buffer)
 }  // namespace pk
@@ -643,7 +671,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // correction products into a fourth TMEM region that spans the tile's whole K
 // range; the drain warps add it to their sums once the tile's last k-block is
 // in, then free it for the next tile (one staging buffer instead of two).
-template <bool BF16, bool ACC>
+template <bool BF16, bool ACC, bool VEC>
 __global__ void __launch_bounds__(pk::THREADS, 1)
     gemm_tf32_persistent_kernel(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
                                 const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mP0,
@@ -659,6 +687,9 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
     __shared__ int s_issued;
     // full[8], empty[8], kb_full[3], kb_empty[3], stage_full[2], stage_empty[2], done, corr_empty, corr_full
     __shared__ __align__(8) uint64_t s_bar[8 + 8 + 3 + 3 + 2 + 2 + 1 + 1 + 1];
+    // VEC: one EPI_COLS x 32-row transposition buffer per store warp (row-vector
+    // epilogue; a separate instantiation, as one kernel with both epilogues spills)
+    __shared__ __align__(16) float s_epi[VEC ? pk::NUM_STORE * pk::EPI_COLS * pk::EPI_CS : 4];
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) s_skip = (*(volatile unsigned*)p.err != 0u);
@@ -936,6 +967,37 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
             const int mh = mm / p.n, ml = mm - mh * p.n;
             const int nn0 = tn * p.bn + half * hcols;
             const int cols = min(hcols, p.n - nn0);  // may be <= 0 for the last column tile
+            if constexpr (VEC) {
+                // the batch's 32 rows x EC columns go through shared memory so that
+                // lane -> column cc, rows rr0 .. rr0+7: 16-byte accesses along the rows
+                float* buf = s_epi + (warp - pk::NUM_DRAIN) * (EC * pk::EPI_CS);
+                const int cc = lane >> 2, rr0 = (lane & 3) * 8;
+                const int grow0 = tm * BM + quarter * 32 + rr0;
+                const bool ok0 = grow0 < p.nbatch * p.M;
+                const int b0 = ok0 ? grow0 / p.M : 0, mm0 = grow0 - b0 * p.M;
+                const int mh0 = ok0 ? mm0 / p.n : 0, ml0 = mm0 - mh0 * p.n;
+                float4 cur4[4], nxt4[4];
+                if (ok0 && cc < cols) epi_load_rows8(p.e, b0, mh0, ml0, nn0 + cc, cur4);
+                for (int c0 = 0; c0 < hcols; c0 += EC) {
+                    uint32_t r[EC];
+                    tmem_ld8(src + (uint32_t)c0, r);
+                    const int c = c0 + cc;
+                    if (ok0 && c + EC < cols) epi_load_rows8(p.e, b0, mh0, ml0, nn0 + c + EC, nxt4);
+                    tmem_wait8(r);
+#pragma unroll
+                    for (int i = 0; i < EC; ++i) buf[i * pk::EPI_CS + lane] = __uint_as_float(r[i]);
+                    __syncwarp();
+                    const float4 a0 = *reinterpret_cast<const float4*>(buf + cc * pk::EPI_CS + rr0);
+                    const float4 a1 = *reinterpret_cast<const float4*>(buf + cc * pk::EPI_CS + rr0 + 4);
+                    __syncwarp();
+                    if (ok0 && c < cols) {
+                        const float v[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                        epi_apply_rows8(p.e, b0, mh0, ml0, nn0 + c, v, cur4);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) cur4[i] = nxt4[i];
+                }
+            } else {
             // state loads of the next EC columns go out before this batch's stores
             float2 cur[EC], nxt[EC];
             if (row_ok && cols > 0) epi_load_state<EC>(p.e, b, mh, ml, nn0, min(EC, cols), cur);
@@ -953,6 +1015,7 @@ __global__ void __launch_bounds__(pk::THREADS, 1)
                 }
 #pragma unroll
                 for (int i = 0; i < EC; ++i) cur[i] = nxt[i];
+            }
             }
             tc_fence_before();
             __syncwarp();
@@ -1089,7 +1152,8 @@ TcConfig tc_make(int M, int n, int products, int nbatch, bool bf16, bool accurat
     c.tiles_m = (int)((rows + BM - 1) / BM);
     const unsigned b_bytes = (unsigned)c.bn * ROW;
     c.stage_bytes = (unsigned)c.pieces * ((unsigned)A_BYTES + b_bytes);
-    int s = (SMEM_LIMIT - 1024) / (int)c.stage_bytes;
+    // the persistent kernel's static shared memory (transposition buffers) comes off the ring
+    int s = (SMEM_LIMIT - 1024 - (persistent ? pk::STATIC_SMEM : 0)) / (int)c.stage_bytes;
     if (s > 8) s = 8;
     if (c.persistent) {
         c.tmem_cols = (int)pk::TMEM_COLS;  // k-block buffers, corrections / staging buffers of 128 columns
@@ -1169,17 +1233,23 @@ cudaError_t tc_maps_create(TcMaps** out, int M, int n, int nbatch, int ld, const
     }
     static bool attr_set = false;
     if (!attr_set) {
-        const void* kernels[] = {(const void*)gemm_tf32_tc_kernel<false, false>,
+        const void* kernels[12] = {(const void*)gemm_tf32_tc_kernel<false, false>,
                                  (const void*)gemm_tf32_tc_kernel<true, false>,
                                  (const void*)gemm_tf32_tc_kernel<false, true>,
                                  (const void*)gemm_tf32_tc_kernel<true, true>,
-                                 (const void*)gemm_tf32_persistent_kernel<false, false>,
-                                 (const void*)gemm_tf32_persistent_kernel<true, false>,
-                                 (const void*)gemm_tf32_persistent_kernel<false, true>,
-                                 (const void*)gemm_tf32_persistent_kernel<true, true>};
+                                 (const void*)gemm_tf32_persistent_kernel<false, false, false>,
+                                 (const void*)gemm_tf32_persistent_kernel<true, false, false>,
+                                 (const void*)gemm_tf32_persistent_kernel<false, true, false>,
+                                 (const void*)gemm_tf32_persistent_kernel<true, true, false>,
+                                 (const void*)gemm_tf32_persistent_kernel<false, false, true>,
+                                 (const void*)gemm_tf32_persistent_kernel<true, false, true>,
+                                 (const void*)gemm_tf32_persistent_kernel<false, true, true>,
+                                 (const void*)gemm_tf32_persistent_kernel<true, true, true>};
         cudaError_t e = cudaSuccess;
-        for (const void* k : kernels)
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+        for (int i = 0; i < 12; ++i)  // persistent kernels (4-11): room for the VEC transposition buffers
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(kernels[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         i < 4 ? SMEM_LIMIT : SMEM_LIMIT - (pk::STATIC_SMEM - 1024));
         if (e != cudaSuccess) {
             delete m;
             return e;
@@ -1217,6 +1287,7 @@ cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, in
     p.err = err;
     p.e = e;
     p.nbatch = nbatch;
+    p.vec = epi_rows8_ok(e) ? 1 : 0;
     const long long ntiles = (long long)cfg.tiles_m * cfg.tiles_n;
     const CUtensorMap* A = maps->a[a_index];
     const CUtensorMap* P = maps->p[slot];
@@ -1230,14 +1301,19 @@ cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, in
         const unsigned grid = (unsigned)(ntiles < sms ? ntiles : sms);
         const int sm = cfg.smem_bytes;
         const int th = pk::THREADS;
-        if (cfg.accurate && cfg.bf16)
-            gemm_tf32_persistent_kernel<true, true><<<grid, th, sm, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
-        else if (cfg.accurate)
-            gemm_tf32_persistent_kernel<false, true><<<grid, th, sm, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
-        else if (cfg.bf16)
-            gemm_tf32_persistent_kernel<true, false><<<grid, th, sm, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
-        else
-            gemm_tf32_persistent_kernel<false, false><<<grid, th, sm, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p);
+#define ETD_PK(B, C, V) gemm_tf32_persistent_kernel<B, C, V><<<grid, th, sm, st>>>(A[0], A[1], A[2], P[0], P[1], P[2], p)
+        if (p.vec) {
+            if (cfg.accurate && cfg.bf16) ETD_PK(true, true, true);
+            else if (cfg.accurate) ETD_PK(false, true, true);
+            else if (cfg.bf16) ETD_PK(true, false, true);
+            else ETD_PK(false, false, true);
+        } else {
+            if (cfg.accurate && cfg.bf16) ETD_PK(true, true, false);
+            else if (cfg.accurate) ETD_PK(false, true, false);
+            else if (cfg.bf16) ETD_PK(true, false, false);
+            else ETD_PK(false, false, false);
+        }
+#undef ETD_PK
     } else {
         const unsigned g = (unsigned)ntiles;
         const int sm = cfg.smem_bytes;
