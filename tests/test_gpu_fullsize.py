@@ -1,7 +1,8 @@
 """Parity at the workload sizes, in the launch configuration bench.py times.
 
-- 2D FitzHugh-Nagumo n = 4096 (two fields, split-TF32) and 3D Allen-Cahn
-  n = 256: two steps against the full FP64 oracle field.
+- 2D FitzHugh-Nagumo n = 4096 (two fields) and 3D Allen-Cahn n = 256, in the
+  split BF16 x6 precision bench.py times by default and in split TF32: two steps
+  against the full FP64 oracle field.
 - Maximum sizes (2D n = 16384, 3D n = 512): no oracle run at that size; the
   f = 0 closed form holds at any size: a sine mode prod sin(k pi x) is
   multiplied per step by prod E_1(tau lambda_k) (Section 3.1 with the
@@ -18,12 +19,13 @@ FHN = (1.0, 0.01, 0.5, 0.1)
 
 
 @pytest.mark.gpu
-def test_fhn_2d_n4096_bench_configuration():
+@pytest.mark.parametrize("precision", ["bf16x6", "tf32x3"])
+def test_fhn_2d_n4096_bench_configuration(precision):
     torch = need_gpu()
     n, steps, tau = 4096, 2, 1e-2
     u0 = inputs.fhn_uniform(n, 2, workload=1)
     stream = torch.cuda.Stream()
-    plan = etd.Plan(2, n, 1e-3, 0.0, tau, pade=2, precision="tf32x3", reaction="fhn", rx_params=FHN, n_comp=2,
+    plan = etd.Plan(2, n, 1e-3, 0.0, tau, pade=2, precision=precision, reaction="fhn", rx_params=FHN, n_comp=2,
                     kappa_comp=(1e-3, 5e-3), stream=stream)
     with torch.cuda.stream(stream):
         u = torch.tensor(u0, dtype=torch.float32, device="cuda")
@@ -37,11 +39,12 @@ def test_fhn_2d_n4096_bench_configuration():
 
 
 @pytest.mark.gpu
-def test_allen_cahn_3d_n256():
+@pytest.mark.parametrize("precision", ["bf16x6", "tf32x3"])
+def test_allen_cahn_3d_n256(precision):
     torch = need_gpu()
     n, steps, tau = 256, 2, 5e-3
     u0 = inputs.gaussian_bump(n, 3)
-    plan = etd.Plan(3, n, 1e-3, 0.1, tau, pade=2, precision="tf32x3", reaction="allen_cahn")
+    plan = etd.Plan(3, n, 1e-3, 0.1, tau, pade=2, precision=precision, reaction="allen_cahn")
     u = torch.tensor(u0, dtype=torch.float32, device="cuda")
     plan.step(u, steps)
     plan.sync()
