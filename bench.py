@@ -585,6 +585,16 @@ def main():
                 "kernel": "tcgen05 transform pass (per-step passes, mean over the step)",
                 "peak_source": top["peak_source"], "avg_launch_ms": avg_gemm_ms,
                 "tensor": tens, "hbm": hbm}
+    elif args.precision == "dst32":
+        # fast sine transform passes (row FFTs in shared memory + a transposing
+        # epilogue): HBM against the pass's algorithmic bytes (operand in, result
+        # and carried state out; the row kernel's scratch round trip is not counted)
+        bytes_pass = info.step_bytes / info.gemms_per_step
+        hpeak = peaks["hbm_gbs"]
+        achieved = bytes_pass / (avg_gemm_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hpeak, "unit": "GB/s", "frac": achieved / hpeak,
+                "traffic": None, "kernel": "fast sine transform pass (dst_rows_kernel + dst_transpose_epi_kernel)",
+                "peak_source": f"{src}: hbm_gbs", "avg_launch_ms": avg_gemm_ms, "bytes_per_launch": bytes_pass}
     else:
         flops = info.gemm_flops
         lanes = 128 if plan.dtype == torch.float32 else 2  # FP32 lanes / FP64 units per SM

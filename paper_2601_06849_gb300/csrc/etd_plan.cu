@@ -1354,7 +1354,7 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
     const double vals = (double)p->ninst * p->ncomp * p->npts;
     const double pin = p->use_tc ? p->tc[0].pieces : 1;
     const double opb = vals * (double)p->op_elem;
-    const double basis = (double)p->n * p->n * (double)p->op_elem * pin;
+    const double basis = p->dst ? 0.0 : (double)p->n * p->n * (double)p->op_elem * pin;  // DST32 reads no P
     const double st = 8.0, fe = (double)p->elem;
     const double pass_in = pin * opb + basis;
     const double split_out = pin * opb;
