@@ -10,8 +10,8 @@
 // so y_k = -Im Z_{k+1} / 2. Two real rows a and b ride in one complex FFT
 // (z = z_a + i z_b): Z = i A - B with A, B real, so y_a = -Im Z / 2 and
 // y_b = Re Z / 2. The FFT is an iterative decimation in time in shared memory,
-// two radix-2 stages per round (radix 4) after one single stage when log2 N is
-// odd. Twiddles come from a host table computed in FP64 and laid out by stage
+// three radix-2 stages per round (radix 8) after one single stage or one radix-4
+// round when log2 N is not a multiple of 3. Twiddles come from a host table computed in FP64 and laid out by stage
 // (stage s, half = 2^s: entries half - 1 + pos = e^{-i pi pos / half}), so the
 // lanes of a warp read consecutive entries; read with the stride of one table
 // e^{-2 pi i k / N} they all hit one shared-memory bank.
@@ -34,6 +34,13 @@ namespace {
 // 32 elements, so that the strided accesses of the bit-reversed stores and of
 // the butterflies of early stages spread over the banks.
 __device__ __forceinline__ int pad32(int i) { return i + (i >> 5); }
+
+// One radix-2 butterfly with twiddle w: (a, b) <- (a + w b, a - w b).
+__device__ __forceinline__ void bfly(float2& a, float2& b, float2 w) {
+    const float2 t = make_float2(w.x * b.x - w.y * b.y, w.x * b.y + w.y * b.x);
+    b = make_float2(a.x - t.x, a.y - t.y);
+    a = make_float2(a.x + t.x, a.y + t.y);
+}
 
 // G row pairs per block iteration (G N = 4096 complex values for short rows), so
 // that one barrier per butterfly stage serves several transforms. Row r of the
@@ -66,8 +73,11 @@ __global__ void __launch_bounds__(512) dst_rows_kernel(const float* __restrict__
             }
         }
         __syncthreads();
+        // stages 0 .. logN-1: one radix-2 stage or one radix-4 round first when
+        // log2 N is not a multiple of 3, then radix-8 rounds (three stages per
+        // shared-memory round trip)
         int s = 0;
-        if (logN & 1) {  // one radix-2 stage (half = 1) when log2 N is odd
+        if (logN % 3 == 1) {  // radix-2 stage (half = 1)
             for (int qq = threadIdx.x; qq < ((N / 2) << logG); qq += blockDim.x) {
                 const int g = qq >> (logN - 1), q = qq & (N / 2 - 1);
                 const int pi = g * NP + pad32(2 * q), pj = g * NP + pad32(2 * q + 1);
@@ -77,32 +87,50 @@ __global__ void __launch_bounds__(512) dst_rows_kernel(const float* __restrict__
             }
             __syncthreads();
             s = 1;
-        }
-        // radix-4 rounds: stages s (half) and s + 1 (2 half) in registers
-        for (; s < logN; s += 2) {
-            const int half = 1 << s;
+        } else if (logN % 3 == 2) {  // radix-4 round: stages 0 (half = 1) and 1
             for (int qq = threadIdx.x; qq < ((N / 4) << logG); qq += blockDim.x) {
                 const int g = qq >> (logN - 2), q = qq & (N / 4 - 1);
-                const int pos = q & (half - 1);
-                const int i0 = ((q >> s) << (s + 2)) + pos;
-                const int p0 = g * NP + pad32(i0), p1 = g * NP + pad32(i0 + half);
-                const int p2 = g * NP + pad32(i0 + 2 * half), p3 = g * NP + pad32(i0 + 3 * half);
+                const int i0 = q << 2;
+                const int p0 = g * NP + pad32(i0), p1 = g * NP + pad32(i0 + 1);
+                const int p2 = g * NP + pad32(i0 + 2), p3 = g * NP + pad32(i0 + 3);
                 float2 x0 = z[p0], x1 = z[p1], x2 = z[p2], x3 = z[p3];
-                const float2 w1 = tw[half - 1 + pos];            // stage s
-                const float2 wa = tw[2 * half - 1 + pos];        // stage s + 1, first half
-                const float2 wb = tw[2 * half - 1 + pos + half]; // stage s + 1, second half
-                float2 t = make_float2(w1.x * x1.x - w1.y * x1.y, w1.x * x1.y + w1.y * x1.x);
-                x1 = make_float2(x0.x - t.x, x0.y - t.y);
-                x0 = make_float2(x0.x + t.x, x0.y + t.y);
-                t = make_float2(w1.x * x3.x - w1.y * x3.y, w1.x * x3.y + w1.y * x3.x);
-                x3 = make_float2(x2.x - t.x, x2.y - t.y);
-                x2 = make_float2(x2.x + t.x, x2.y + t.y);
-                t = make_float2(wa.x * x2.x - wa.y * x2.y, wa.x * x2.y + wa.y * x2.x);
-                z[p2] = make_float2(x0.x - t.x, x0.y - t.y);
-                z[p0] = make_float2(x0.x + t.x, x0.y + t.y);
-                t = make_float2(wb.x * x3.x - wb.y * x3.y, wb.x * x3.y + wb.y * x3.x);
-                z[p3] = make_float2(x1.x - t.x, x1.y - t.y);
-                z[p1] = make_float2(x1.x + t.x, x1.y + t.y);
+                bfly(x0, x1, tw[0]);
+                bfly(x2, x3, tw[0]);
+                bfly(x0, x2, tw[1]);
+                bfly(x1, x3, tw[2]);
+                z[p0] = x0;
+                z[p1] = x1;
+                z[p2] = x2;
+                z[p3] = x3;
+            }
+            __syncthreads();
+            s = 2;
+        }
+        for (; s < logN; s += 3) {  // radix-8 rounds: stages s (half), s + 1, s + 2 in registers
+            const int half = 1 << s;
+            for (int qq = threadIdx.x; qq < ((N / 8) << logG); qq += blockDim.x) {
+                const int g = qq >> (logN - 3), q = qq & (N / 8 - 1);
+                const int pos = q & (half - 1);
+                const int i0 = ((q >> s) << (s + 3)) + pos;
+                int pk[8];
+                float2 x[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    pk[k] = g * NP + pad32(i0 + k * half);
+                    x[k] = z[pk[k]];
+                }
+                const float2 w1 = tw[half - 1 + pos];  // stage s
+#pragma unroll
+                for (int a = 0; a < 8; a += 2) bfly(x[a], x[a + 1], w1);
+                const float2 wa = tw[2 * half - 1 + pos], wb = tw[2 * half - 1 + pos + half];  // stage s + 1
+                bfly(x[0], x[2], wa);
+                bfly(x[1], x[3], wb);
+                bfly(x[4], x[6], wa);
+                bfly(x[5], x[7], wb);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) bfly(x[k], x[k + 4], tw[4 * half - 1 + pos + k * half]);  // stage s + 2
+#pragma unroll
+                for (int k = 0; k < 8; ++k) z[pk[k]] = x[k];
             }
             __syncthreads();
         }
