@@ -166,10 +166,17 @@ __global__ void __launch_bounds__(256) dst_transpose_epi_kernel(const float* __r
     if (r >= R) return;
     const int b = (int)(r / M), mm = (int)(r - (long long)b * M);
     const int mh = mm / n, ml = mm - mh * n;
-    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
-        const int nn = c0 + i;
-        if (nn < n) e.apply(b, mh, ml, nn, tile[threadIdx.x][i]);
-    }
+    // four consecutive columns per thread (blockDim.y = 8): their state loads go
+    // out together, then the batched epilogue
+    const int i0 = 4 * threadIdx.y, nn0 = c0 + i0;
+    if (nn0 >= n) return;
+    const int count = min(4, n - nn0);
+    float2 st[4];
+    epi_load_state<4>(e, b, mh, ml, nn0, count, st);
+    float v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = tile[threadIdx.x][i0 + i];
+    epi_apply_batch<4>(e, b, mh, ml, nn0, v, count, st);
 }
 
 }  // namespace
