@@ -242,9 +242,10 @@ __device__ __forceinline__ void epi_apply_batch(const Epi<float>& e, int b, int 
         return;
     }
     // The transformed reaction v carries the transform's relative error (about
-    // 2^-22 for split TF32), so its products with tau E2 and tau E3 are formed
-    // in FP32 (relative error 2^-24) and added to the double-float terms;
-    // E1 U^ and the products with S keep double-float precision.
+    // 2^-22 for split TF32), so its products with S, tau E2 and tau E3 are formed
+    // in FP32 (relative error about 2^-23) and added to the double-float term
+    // S E1 U^, which keeps double-float precision and is formed once for both W^
+    // and Z.
     const float2* g = e.grid + (long long)b * 3 * e.n;
     const float g3 = g[2 * e.n + ml].x;
     if (e.mode == EPI_STAGE1) {
@@ -258,9 +259,10 @@ __device__ __forceinline__ void epi_apply_batch(const Epi<float>& e, int b, int 
                 const long long o = o0 + j * step;
                 const float2 sl = g[nn0 + j];
                 const float2 sj = (e.d == 2) ? sl : ff_mul(gm, sl);
-                const float2 t = ff_mul(g1, st[j]);
-                const float2 w = ff_mul(ff_add_f(t, __fmul_rn(g2.x, v[j])), sj);
-                e.zhat[o] = ff_mul(ff_add_f(t, __fmul_rn(g23, v[j])), sj);
+                const float2 su = ff_mul(ff_mul(g1, st[j]), sj);  // S E1 U^, double-float
+                const float sv = __fmul_rn(sj.x, v[j]);              // S F^, FP32
+                const float2 w = ff_add_f(su, __fmul_rn(g2.x, sv));
+                e.zhat[o] = ff_add_f(su, __fmul_rn(g23, sv));
                 e.write_operand_ff(o, w);
             }
         }
@@ -398,9 +400,10 @@ __device__ __forceinline__ void epi_apply_rows8(const Epi<float>& e, int b, int 
                 const int i = 2 * k + h, ml = ml0 + i;
                 const float2 g1 = g[ml], g2 = g[e.n + ml], g3v = g[2 * e.n + ml];
                 const float g23 = __fsub_rn(g2.x, g3v.x) + g2.y - g3v.y;
-                const float2 t = ff_mul(g1, st[i]);
-                w[i] = ff_mul(ff_add_f(t, __fmul_rn(g2.x, v[i])), sj);
-                z[h] = ff_mul(ff_add_f(t, __fmul_rn(g23, v[i])), sj);
+                const float2 su = ff_mul(ff_mul(g1, st[i]), sj);  // S E1 U^, double-float
+                const float sv = __fmul_rn(sj.x, v[i]);              // S F^, FP32
+                w[i] = ff_add_f(su, __fmul_rn(g2.x, sv));
+                z[h] = ff_add_f(su, __fmul_rn(g23, sv));
             }
             zq[k] = make_float4(z[0].x, z[0].y, z[1].x, z[1].y);
         }
