@@ -73,7 +73,8 @@ def run_adjoint(args, world, rank, local):
     torch.cuda.set_device(local)
     d, n, ku, kv, q, tau, rx, desc = WORKLOADS[args.workload]
     window, every = 400, 20
-    u0 = torch.tensor(inputs.fhn_uniform(n, d, workload=4), dtype=torch.float32, device="cuda")
+    fdt = torch.float64 if args.precision == "fp64" else torch.float32  # the plan's field type
+    u0 = torch.tensor(inputs.fhn_uniform(n, d, workload=4), dtype=fdt, device="cuda")
     target = u0.clone()
     tplan = etd.Plan(d, n, ku * (1 + 1e-2), q, tau, precision=args.precision, reaction="fhn", rx_params=FHN, n_comp=2,
                      kappa_comp=(ku * (1 + 1e-2), kv))
@@ -131,7 +132,8 @@ def run_adjoint(args, world, rank, local):
         "metric": "unknown-updates/s per ETD2RK-DS step (forward + adjoint)", "value": value,
         "unit": "unknown-updates/s", "n_gpus": world, "steps": iters, "warmup": args.warmup,
         "ms_per_step": el_max / iters / window * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": f"{args.precision} (f32 fields, double-float spectral state)",
+        "vs_baseline": None,
+        "dtype": ("fp64" if args.precision == "fp64" else f"{args.precision} (f32 fields, double-float spectral state)"),
         "data": "synthetic",
         "config": {"workload": desc, "d": d, "n": n, "window": window, "checkpoint_every": every,
                    "precision": args.precision, "step": "one forward + backward solve over the window",

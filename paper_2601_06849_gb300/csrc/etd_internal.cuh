@@ -492,6 +492,7 @@ struct SpecCombine {
     int ncomp, d, n;
     long long npts;
     const double* grid;
+    const float2* grid2;  // double-float copy (FP32 paths)
     const T* in1;
     int xsel1, s1;
     double alpha;
@@ -516,6 +517,8 @@ struct GradKappa {
     long long npts;
     const double* grid;
     const double* dgrid;  // kappa derivatives of E1, tau E2, tau E3
+    const float2* grid2;  // double-float copies (FP32 paths)
+    const float2* dgrid2;
     const T* Lh;          // U+bar^
     const T* Gbh;         // Gbar^
     const T* Wbh;         // Wbar^

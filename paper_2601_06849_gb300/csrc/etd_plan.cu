@@ -104,6 +104,7 @@ struct etd_plan {
     std::vector<void*> adj_traj;  // forward states of the window being differentiated
     void* adj_work[14] = {nullptr};
     double* adj_dgrid = nullptr;  // kappa derivatives of E1, tau E2, tau E3 per component
+    float2* adj_dgrid2 = nullptr;  // the same as double-floats (FP32 paths)
     double* adj_acc = nullptr;    // [2] kappa gradients, [4] reaction-parameter gradients
     cudaStream_t cap_stream = nullptr;      // capture origin (the caller's stream may be the legacy one)
 };
@@ -210,6 +211,7 @@ void free_plan(etd_plan* p) {
     for (void* f : p->adj_work)
         if (f) cudaFree(f);
     if (p->adj_dgrid) cudaFree(p->adj_dgrid);
+    if (p->adj_dgrid2) cudaFree(p->adj_dgrid2);
     if (p->adj_acc) cudaFree(p->adj_acc);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (auto ev : p->ev_done)
@@ -487,6 +489,7 @@ etd_status spec(etd_plan* p, const void* in1, int x1, int s1, double a, const vo
     c.n = p->n;
     c.npts = p->npts;
     c.grid = (const double*)p->grid;
+    c.grid2 = (const float2*)p->grid2;
     c.in1 = (const T*)in1;
     c.xsel1 = x1;
     c.s1 = s1;
@@ -549,6 +552,8 @@ etd_status adjoint_step_impl(etd_plan* p, const void* U, void* lam) {
     gk.npts = p->npts;
     gk.grid = (const double*)p->grid;
     gk.dgrid = p->adj_dgrid;
+    gk.grid2 = (const float2*)p->grid2;
+    gk.dgrid2 = p->adj_dgrid2;
     gk.Lh = (const T*)Lh;
     gk.Gbh = (const T*)Gbh;
     gk.Wbh = (const T*)Wbh;
@@ -581,12 +586,16 @@ etd_status adjoint_impl(etd_plan* p, const void* u_ckpt, void* lam, int n_steps)
         p->adj_traj.push_back(f);
     }
     // forward states U^0 .. U^{N-1} of the window, recomputed from the checkpoint
+    // in one work field (its carried spectral state stays valid from step to
+    // step, as in the forward run) and copied out after every step
     const double t0 = p->t;
+    void* work = p->adj_work[12];  // free until the backward steps
     ETD_CUDA(cudaMemcpyAsync(p->adj_traj[0], u_ckpt, fbytes, cudaMemcpyDeviceToDevice, p->stream));
+    if (n_steps > 1) ETD_CUDA(cudaMemcpyAsync(work, u_ckpt, fbytes, cudaMemcpyDeviceToDevice, p->stream));
     for (int j = 1; j < n_steps; ++j) {
-        ETD_CUDA(cudaMemcpyAsync(p->adj_traj[j], p->adj_traj[j - 1], fbytes, cudaMemcpyDeviceToDevice, p->stream));
-        etd_status s = step_impl<T>(p, p->adj_traj[j], 1);
+        etd_status s = step_impl<T>(p, work, 1);
         if (s != ETD_OK) return s;
+        ETD_CUDA(cudaMemcpyAsync(p->adj_traj[j], work, fbytes, cudaMemcpyDeviceToDevice, p->stream));
     }
     p->t = t0;
     p->uhat_valid = false;  // the carried state now belongs to the recomputed window
@@ -1156,6 +1165,7 @@ etd_status etd_step_adjoint(etd_plan* p, const void* u_ckpt, void* lambda_dev, i
         for (int i = 0; i < 14 && s == ETD_OK; ++i) s = dalloc(p, &p->adj_work[i], fbytes);
         if (s == ETD_OK) s = dalloc(p, (void**)&p->adj_acc, 8 * sizeof(double));
         if (s == ETD_OK) s = dalloc(p, (void**)&p->adj_dgrid, (size_t)p->ncomp * 3 * p->n * sizeof(double));
+        if (s == ETD_OK) s = dalloc(p, (void**)&p->adj_dgrid2, (size_t)p->ncomp * 3 * p->n * sizeof(float2));
         if (s != ETD_OK) return s;
         // d/dkappa of E1(tau lambda), tau E2, tau E3: tau mu E_l'(tau lambda), mu = dlambda/dkappa
         const int n = p->n;
@@ -1173,6 +1183,12 @@ etd_status etd_step_adjoint(etd_plan* p, const void* u_ckpt, void* lambda_dev, i
                 dg[((size_t)c * 3 + 2) * n + k] = p->tau * p->tau * mu * de[2];
             }
         ETD_CUDA(cudaMemcpy(p->adj_dgrid, dg.data(), dg.size() * sizeof(double), cudaMemcpyHostToDevice));
+        std::vector<float2> dg2(dg.size());  // hi = rn(g), lo = rn(g - hi)
+        for (size_t i = 0; i < dg.size(); ++i) {
+            dg2[i].x = (float)dg[i];
+            dg2[i].y = (float)(dg[i] - (double)dg2[i].x);
+        }
+        ETD_CUDA(cudaMemcpy(p->adj_dgrid2, dg2.data(), dg2.size() * sizeof(float2), cudaMemcpyHostToDevice));
     }
     ETD_CUDA(cudaMemsetAsync(p->adj_acc, 0, 8 * sizeof(double), p->stream));
     s = (p->elem == 8) ? adjoint_impl<double>(p, u_ckpt, lambda_dev, n_steps)
