@@ -111,15 +111,19 @@ def test_pade04(precision, d, n):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
-def test_exact_exponential_2d(precision):
-    """eq. (9)-(10) with exact exponentials against the FP64 Sylvester oracle."""
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "bf16x6"])
+@pytest.mark.parametrize("d,n", [(2, 80), (3, 36)])
+def test_exact_exponential(precision, d, n):
+    """eq. (9)-(10) with exact exponentials against the FP64 Sylvester oracle
+    (whose factor grids are pinned to quadrature of the phi integrals). With
+    kappa = 1e-3, q = 0.1, tau = 5e-3 the products tau lambda_k run from about
+    2.5e-4 to 0.13, so both the series and the closed-form branches of E_3 are used."""
     torch = need_gpu()
-    n, tau, steps = 80, 5e-3, 12
-    u0 = inputs.allen_cahn_2d(n, workload=6)
-    P = O.Problem(d=2, n=n, kappa=(1e-3,), q=0.1, tau=tau, reaction="allen_cahn")
+    tau, steps = 5e-3, 12
+    u0 = inputs.allen_cahn_2d(n, workload=6) if d == 2 else inputs.gaussian_bump(n, 3)
+    P = O.Problem(d=d, n=n, kappa=(1e-3,), q=0.1, tau=tau, reaction="allen_cahn")
     ref = S.run(P, u0, steps, react=lambda t, u: u - u ** 3, kind="exact")
-    got = run_gpu(torch, 2, n, 1e-3, 0.1, tau, u0, steps, precision, "allen_cahn", pade="exact")
+    got = run_gpu(torch, d, n, 1e-3, 0.1, tau, u0, steps, precision, "allen_cahn", pade="exact")
     assert rel_err(got, ref) < tol(precision, n)
 
 

@@ -79,6 +79,126 @@ def test_factors_in_unit_interval():
             assert np.all(v > 0) and np.all(v <= 1.0 + 1e-15)
 
 
+# ---------------------------------- exact exponential factors, eq. (9)-(10)
+
+def phi_quadrature(x):
+    """(e^{-x}, int_0^1 e^{-x(1-s)} ds, int_0^1 s e^{-x(1-s)} ds) by 40-digit
+    quadrature of the integral forms of eq. (9)-(10) (the integrals whose closed
+    forms the scheme uses), independent of any closed form or series."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    X = mp.mpf(float(x))
+    f2 = lambda s: mp.exp(-X * (1 - s))
+    f3 = lambda s: s * mp.exp(-X * (1 - s))
+    # the integrands live within ~1/x of s = 1: give the quadrature that breakpoint
+    pts = [0, 1 - mp.mpf(80) / X, 1] if X > 80 else [0, 1]
+    return float(mp.exp(-X)), float(mp.quad(f2, pts)), float(mp.quad(f3, pts))
+
+
+EXACT_XS = np.concatenate([[0.0, 1e-12, 1e-7, 9.99e-4, 1.0001e-3, 0.0499, 0.0501, 0.0999, 0.1001, 0.5, 1.0,
+                            30.0, 1e3], np.logspace(-10, 3, 27)])
+
+
+def test_exact_factors_equal_phi_integrals():
+    """Both branches of the exact-exponential grids (series below the switch,
+    expm1 forms above) against quadrature of the integral definitions, at
+    points on both sides of every switch (1e-3, 0.05, 0.1)."""
+    e1, e2, e3 = S.rational_grids("exact", EXACT_XS)
+    for i, x in enumerate(EXACT_XS):
+        r1, r2, r3 = phi_quadrature(x) if x > 0 else (1.0, 1.0, 0.5)
+        assert abs(e1[i] - r1) <= 1e-15 * r1, x
+        assert abs(e2[i] - r2) <= 1e-14 * r2, x
+        assert abs(e3[i] - r3) <= 1e-14 * r3, x
+
+
+def test_exact_factors_recurrences_and_limits():
+    """phi_{l+1}(x) = (1 - phi_l(x)) / x (with phi_0 = e^{-x}) where no
+    cancellation occurs, the limits 1, 1, 1/2 at x = 0, and the Pade factors of
+    Section 3.1 / Section 5 converging to them near 0 (E_1 to e^{-x} with order
+    3 / 5)."""
+    xs = np.linspace(1.0, 50.0, 50)
+    e1, e2, e3 = S.rational_grids("exact", xs)
+    np.testing.assert_allclose(e2, (1 - e1) / xs, rtol=1e-14)
+    np.testing.assert_allclose(e3, (1 - e2) / xs, rtol=1e-13)
+    z = S.rational_grids("exact", np.array([0.0]))
+    assert (z[0][0], z[1][0], z[2][0]) == (1.0, 1.0, 0.5)
+    # E_{l+1} = (1 - E_l)/x for the Pade factors too, so each step down the
+    # recurrence costs one order: E_1, E_2, E_3 err by O(x^3), O(x^2), O(x) (P_{0,2})
+    for pade, order in ((2, 3), (4, 5)):
+        h = np.array([0.02, 0.01])
+        ex = S.rational_grids("exact", h)
+        pa = S.rational_grids(pade, h)
+        for ell in range(3):
+            err = np.abs(ex[ell] - pa[ell])
+            assert abs(np.log2(err[0] / err[1]) - (order - ell)) < 0.1, (pade, ell)
+
+
+@pytest.mark.parametrize("d,n,modes", [(2, 20, [(1, 1), (4, 17)]), (3, 9, [(2, 1, 3), (9, 9, 9)])])
+def test_exact_scheme_f0_modes_decay_by_exponential(d, n, modes):
+    """f = 0, exact-exponential grids: each sine mode is multiplied per step by
+    exp(-tau (lambda_kx + lambda_ky [+ lambda_kz]))."""
+    kappa, q, tau, N = 0.03, 0.4, 0.02, 6
+    lam = eig1d(n, kappa, q, d)
+    P = O.Problem(d=d, n=n, kappa=(kappa,), q=q, tau=tau, pade=2, reaction="none")
+    u0 = np.zeros((n,) * d)
+    want = np.zeros((n,) * d)
+    for w, m in enumerate(modes):
+        shape = inputs.sine_mode(n, d, m)
+        rate = sum(lam[k - 1] for k in m)
+        u0 += (w + 1) * shape
+        want += (w + 1) * np.exp(-tau * rate * N) * shape
+    got = S.run(P, u0[None], N, react=lambda t, u: np.zeros_like(u), kind="exact")[0]
+    np.testing.assert_allclose(got, want, atol=1e-13 * np.abs(u0).max())
+
+
+def test_exact_scheme_linear_reaction_modal_recurrence():
+    """f = c u on one sine mode with the exact grids: the scalar recurrence of
+    eq. (9)-(10) with phi_1, phi_2 taken from quadrature."""
+    n, kappa, q, tau, c, N = 16, 0.02, 0.4, 0.05, 1.3, 8
+    lam = eig1d(n, kappa, q, 2)
+    m = (3, 5)
+    _, p1, p2 = phi_quadrature(tau * lam[m[0] - 1])
+    e1x = np.exp(-tau * lam[m[0] - 1])
+    s = np.exp(-tau * lam[m[1] - 1])
+    a = 1.0
+    for _ in range(N):
+        w = e1x * s * a + tau * p1 * s * c * a
+        a = w + tau * p2 * (c * w - s * c * a)
+    P = O.Problem(d=2, n=n, kappa=(kappa,), q=q, tau=tau, pade=2, reaction="linear", rp=(c,))
+    got = S.run(P, inputs.sine_mode(n, 2, m)[None], N, react=lambda t, u: c * u, kind="exact")[0]
+    np.testing.assert_allclose(got, a * inputs.sine_mode(n, 2, m), atol=1e-14)
+
+
+def discrete_manufactured_error(kind, N, n=31, d=2, lam=1.0, coarse=16):
+    """E(N) against the exact solution of the semi-discrete problem: psi built
+    with the discrete eigenvalue of sin(pi x) (A_h u0 = d mu_1 u0), so that
+    u_h(t) = e^{-lam t} u0 solves u' + A_h u = u (1 - u^2) + psi exactly and the
+    error is the time discretisation alone (the quantity the convergence
+    theorems of Section 4 bound)."""
+    h = 1.0 / (n + 1)
+    mu1 = 4 / h ** 2 * np.sin(np.pi * h / 2) ** 2
+    u0 = inputs.sine_mode(n, d, (1,) * d)
+
+    def react(t, u):
+        ue = np.exp(-lam * t) * u0
+        return u * (1 - u * u) + ((-lam + d * mu1) * ue - ue * (1 - ue * ue))[None]
+
+    P = O.Problem(d=d, n=n, kappa=(1.0,), q=0.0, tau=1.0 / N, pade=2, reaction="none")
+    u, E, per = u0[None].copy(), 0.0, N // coarse
+    for c in range(coarse):
+        u = S.run(P, u, per, t0=c * per / N, react=react, kind=kind)
+        E = max(E, np.abs(u[0] - np.exp(-lam * (c + 1) * per / N) * u0).max())
+    return E
+
+
+def test_exact_scheme_second_order():
+    """The exact-exponential ETD2RK-DS scheme converges with order 2 in tau
+    (the convergence theorem for eq. (9)-(10) in Section 4)."""
+    E = np.array([discrete_manufactured_error("exact", N) for N in (16, 32, 64, 128)])
+    eoc = np.log2(E[:-1] / E[1:])
+    assert np.all(eoc > 1.85) and np.all(eoc < 2.1), eoc
+
+
 # ------------------------------------------------- closed forms on sine modes
 
 @pytest.mark.parametrize("d,n,modes,pade,q", [
@@ -311,11 +431,12 @@ def singular_reference():
     return singular_trajectory(512)
 
 
-def singular_trajectory(N, n=511):
-    u = 0.99 * inputs.sine_mode(n, 2, (1, 1))[None]
-    P = O.Problem(d=2, n=n, kappa=(1.0,), q=1.0, tau=1.0 / N, reaction="singular", rp=(0.1,))
-    out, per = [], N // 16
-    for c in range(16):
+def singular_trajectory(N, n=511, d=2, coarse=16):
+    """The Example 5.2 run at the coarse times S_coarse (kappa = 1, q = 1, rho = 0.1)."""
+    u = 0.99 * inputs.sine_mode(n, d, (1,) * d)[None]
+    P = O.Problem(d=d, n=n, kappa=(1.0,), q=1.0, tau=1.0 / N, reaction="singular", rp=(0.1,))
+    out, per = [], N // coarse
+    for c in range(coarse):
         u = O.run(P, u, per, t0=c * per / N)
         out.append(u)
     return out
@@ -325,4 +446,16 @@ def singular_trajectory(N, n=511):
 def test_table4_singular_source_2d(pade, N, E, singular_reference):
     tr = singular_trajectory(N)
     err = max(np.abs(a - b).max() for a, b in zip(tr, singular_reference))
+    assert three_sig(err) == pytest.approx(E, rel=1e-9)
+
+
+@pytest.fixture(scope="module")
+def singular_reference_3d():
+    return singular_trajectory(320, n=79, d=3, coarse=10)
+
+
+@pytest.mark.parametrize("pade,N,E", load_golden("table4b_ex52_3d.txt"))
+def test_table4b_singular_source_3d(pade, N, E, singular_reference_3d):
+    tr = singular_trajectory(N, n=79, d=3, coarse=10)
+    err = max(np.abs(a - b).max() for a, b in zip(tr, singular_reference_3d))
     assert three_sig(err) == pytest.approx(E, rel=1e-9)
