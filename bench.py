@@ -10,6 +10,9 @@ eight transform passes over both fields.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--precision P]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+    python bench.py --accuracy --workload NAME [--precisions P1,P2]
+        # error vs the FP64 oracle over the configuration's whole run length,
+        # beside the floors of FP32 input rounding and of the oracle's FP32 shadow
 
 Prints one JSON line (rank 0). With N > 1 (torchrun), every rank advances its
 own replica of the workload (the problem has no data-parallel exchange; see
@@ -53,6 +56,9 @@ WORKLOADS = {
                     "512 independent 2D FitzHugh-Nagumo instances, n uniform on {64,96,...,512}, kappa_u log-uniform "
                     "[1e-4,1e-2], tau uniform [1e-3,1e-2], kappa_v=5e-3 eps=0.01 a=0.5 b=0.1"),
 }
+# run length of each workload's configuration (the accuracy check runs all of it)
+RUN_STEPS = {"fhn2d_4096": 1000, "fhn2d_2048": 1000, "fhn2d_4095": 1000, "ac3d_256": 200, "ac3d_384": 200,
+             "ac3d_255": 200, "ac2d_64": 100, "ensemble512": 500, "adjoint3d_128": 400}
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
 KERNEL_FILES = ["paper_2601_06849_gb300/csrc/gemm_tc.cu", "paper_2601_06849_gb300/csrc/etd_internal.cuh"]
 L2_BYTES = 129e6
@@ -125,8 +131,7 @@ def run_adjoint(args, world, rank, local):
     passes = window * (4 * d + 4 * d + 9 * d)
     flops = passes * 2.0 * n ** (d + 1) * 2 * products * iters
     peaks, src = measured_peaks()
-    bf16_mode = args.precision.startswith("bf16")
-    tpeak = peaks["bf16_tflops_sustained"] * (1.0 if bf16_mode else TF32_OVER_BF16)
+    tpeak, tsrc = tensor_peak(peaks, src, args.precision, el_max)
     achieved = flops / el_max / 1e12
     line = {
         "metric": "unknown-updates/s per ETD2RK-DS step (forward + adjoint)", "value": value,
@@ -142,7 +147,7 @@ def run_adjoint(args, world, rank, local):
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": tpeak, "unit": "TFLOP/s",
                      "frac": achieved / tpeak, "traffic": None,
                      "kernel": "all transform passes of forward, recomputed forward and adjoint (whole-iteration rate)",
-                     "peak_source": f"{src}: bf16_tflops_sustained" + ("" if bf16_mode else " x 1.1/2.25")},
+                     "peak_source": tsrc},
         # per time step: forward (2 reactions + 4d passes), the segment's recomputed
         # forward (the same), the adjoint step (9 transforms of 1 + d launches, 4
         # spectral combinations, 2 Jacobian products, 2 gradient reductions)
@@ -225,12 +230,10 @@ def run_ensemble(args, world, rank, local):
         e2e_s = barrier_max(time.perf_counter() - t0, world)
     peaks, src = measured_peaks()
     flops = info.step_flops * max(info.products, 1) * args.steps
-    bf16_mode = args.precision.startswith("bf16")
-    tpeak = peaks["bf16_tflops_sustained"] * (1.0 if bf16_mode else TF32_OVER_BF16)
     sec = el_max / 1e3
+    tpeak, tsrc = tensor_peak(peaks, src, args.precision, sec)
     tens = {"achieved": flops / sec / 1e12, "peak": tpeak, "unit": "TFLOP/s", "frac": flops / sec / 1e12 / tpeak,
-            "peak_source": (f"{src}: bf16_tflops_sustained" if bf16_mode else
-                            f"{src}: bf16_tflops_sustained x 1.1/2.25 (TF32/BF16 nominal)")}
+            "peak_source": tsrc}
     sbytes = info.step_bytes * args.steps
     hbm = {"achieved": sbytes / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
            "frac": sbytes / sec / 1e9 / peaks["hbm_gbs"], "peak_source": f"{src}: hbm_gbs"}
@@ -259,9 +262,172 @@ def run_ensemble(args, world, rank, local):
     cs = clocks.summary()
     if cs:
         line["clocks"] = cs
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the timed fields went through warmup + steps steps: the FP64 oracle on
+        # the first member of each grid size, from the same FP32-held input
+        import numpy as np
+
+        from oracle import oracle as O
+
+        steps = args.warmup + args.steps
+        errs, t0 = [], time.perf_counter()
+        for i in ensemble_sample(members):
+            m = members[i]
+            P = O.Problem(d=2, n=m.n, kappa=(m.kappa_u, kv), q=q, tau=m.tau, reaction="fhn", rp=FHN)
+            u0f = m.u0.astype(np.float32).astype(np.float64) if batch.dtype == torch.float32 else m.u0
+            errs.append(max(rel_errs(fields[i].double().cpu().numpy(), O.run(P, u0f, steps))))
+        dt = time.perf_counter() - t0
+        line["rel_err_vs_fp64_oracle"] = max(errs)
+        line["cpu_baseline"] = {"value": sum(2 * members[i].n ** 2 for i in ensemble_sample(members)) * steps / dt,
+                                "unit": "unknown-updates/s", "cores": O.max_threads(), "kind": "oracle",
+                                "sample": f"{steps} FP64 oracle steps of the first member of each of the "
+                                          f"{len(errs)} grid sizes", "seconds": dt}
     batch.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def rel_errs(got, ref):
+    """max |got - ref| / max |ref| per component over the whole field (the error metric)."""
+    import numpy as np
+
+    return [float(np.abs(got[c] - ref[c]).max() / np.abs(ref[c]).max()) for c in range(ref.shape[0])]
+
+
+def ensemble_sample(members):
+    """Indices of the ensemble members whose error is checked: the first member
+    of each grid size (all 15 sizes of the workload, 64 .. 512)."""
+    seen, idx = set(), []
+    for i, m in enumerate(members):
+        if m.n not in seen:
+            seen.add(m.n)
+            idx.append(i)
+    return idx
+
+
+def run_accuracy(args, world, rank, local):
+    """--accuracy: the error of each precision against the FP64 oracle over the
+    configuration's whole run length (checked at every tenth of the run, the
+    largest of those errors reported), beside two floors that no FP32-field path
+    can beat: the FP64 oracle run from the unrounded FP64 draw of u0 against the
+    one from its FP32 rounding (one FP32 rounding of the input, amplified by the
+    dynamics), and the oracle's FP32 shadow (the same LU scheme in FP32
+    arithmetic). FP32 paths are compared with the oracle run from the same
+    FP32-held input; the FP64 path with the one from the FP64 draw."""
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from oracle import oracle as O
+    from paper_2601_06849_gb300 import etd, inputs
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    name = args.workload
+    total = args.accuracy_steps or RUN_STEPS[name]
+    marks = sorted(set(max(1, total * (i + 1) // 10) for i in range(10)))
+    precisions = [x for x in args.precisions.split(",") if x]
+    O.lib()
+    if name == "ensemble512":
+        members = inputs.fhn_ensemble(512, workload=3)
+        sample = ensemble_sample(members)
+        d, _, _, kv, q, _, rx, desc = WORKLOADS[name]
+
+        def oracle_runs(src):  # checkpoints of every sampled member
+            out = []
+            for i in sample:
+                m = members[i]
+                P = O.Problem(d=2, n=m.n, kappa=(m.kappa_u, kv), q=q, tau=m.tau, reaction="fhn", rp=FHN)
+                u, prev, cps = src(m), 0, []
+                for k in marks:
+                    u = O.run(P, u, k - prev)
+                    cps.append(u)
+                    prev = k
+                out.append(cps)
+            return out
+        t0 = time.perf_counter()
+        ref32 = oracle_runs(lambda m: m.u0.astype(np.float32).astype(np.float64))
+        ref64 = oracle_runs(lambda m: m.u0)
+        oracle_s = time.perf_counter() - t0
+        floor_in = [max(max(rel_errs(a[j], b[j])) for a, b in zip(ref64, ref32)) for j in range(len(marks))]
+        floor_sh = [0.0] * len(marks)
+        for si, i in enumerate(sample):
+            m = members[i]
+            P = O.Problem(d=2, n=m.n, kappa=(m.kappa_u, kv), q=q, tau=m.tau, reaction="fhn", rp=FHN)
+            u, prev = m.u0.astype(np.float32).astype(np.float64), 0
+            for j, k in enumerate(marks):
+                u = O.run(P, u, k - prev, precision="f32").astype(np.float64)
+                floor_sh[j] = max(floor_sh[j], max(rel_errs(u, ref32[si][j])))
+                prev = k
+        errors = {}
+        for prec in precisions:
+            batch = etd.Batch(2, [m.n for m in members], [m.kappa_u for m in members], [q] * len(members),
+                              [m.tau for m in members], precision=prec, reaction="fhn", rx_params=FHN, n_comp=2,
+                              kappa_v=kv)
+            ref = ref64 if prec == "fp64" else ref32
+            fields = [torch.tensor(m.u0, dtype=batch.dtype, device="cuda") for m in members]
+            prev, per = 0, []
+            for j, k in enumerate(marks):
+                batch.step(fields, k - prev)
+                batch.sync()
+                prev = k
+                per.append(max(max(rel_errs(fields[i].double().cpu().numpy(), ref[si][j]))
+                               for si, i in enumerate(sample)))
+            errors[prec] = {"max": max(per), "final": per[-1], "per_checkpoint": per}
+            batch.close()
+        line = {"metric": "max rel err vs FP64 oracle over the run", "workload": desc, "steps": total,
+                "checkpoints": marks, "sampled_instances": [{"index": i, "n": members[i].n} for i in sample],
+                "errors": errors,
+                "floors": {"fp32_input_rounding": {"max": max(floor_in), "per_checkpoint": floor_in},
+                           "fp32_shadow": {"max": max(floor_sh), "per_checkpoint": floor_sh}},
+                "oracle": {"seconds": oracle_s, "cores": O.max_threads()},
+                "error_metric": "max over checkpoints, components and sampled instances of "
+                                "max|U - U_ref| / max|U_ref|"}
+        print(json.dumps(line), flush=True)
+        return
+    d, n, ku, kv, q, tau, rx, desc = WORKLOADS[name]
+    kap = (ku, kv) if rx == "fhn" else (ku,)
+    P = O.Problem(d=d, n=n, kappa=kap, q=q, tau=tau, pade=2, reaction=rx, rp=FHN if rx == "fhn" else ())
+    u0 = initial_field(name)
+    u0f = u0.astype(np.float32).astype(np.float64)  # the values an FP32 field holds
+
+    def oracle_checkpoints(u, precision="f64"):
+        out, prev = [], 0
+        for k in marks:
+            u = O.run(P, u, k - prev, t0=prev * tau, precision=precision)
+            out.append(np.asarray(u, dtype=np.float64))
+            prev = k
+        return out
+    t0 = time.perf_counter()
+    ref32 = oracle_checkpoints(u0f)
+    oracle_s = time.perf_counter() - t0
+    ref64 = oracle_checkpoints(u0)
+    floor_in = [max(rel_errs(a, b)) for a, b in zip(ref64, ref32)]
+    floor_sh = [max(rel_errs(a, b)) for a, b in zip(oracle_checkpoints(u0f, "f32"), ref32)]
+    errors = {}
+    for prec in precisions:
+        plan = make_plan(name, prec)
+        ref = ref64 if prec == "fp64" else ref32
+        x = torch.tensor(u0, dtype=plan.dtype, device="cuda")
+        prev, per = 0, []
+        t0 = time.perf_counter()
+        for j, k in enumerate(marks):
+            plan.step(x, k - prev)
+            plan.sync()
+            prev = k
+            per.append(max(rel_errs(x.double().cpu().numpy(), ref[j])))
+        errors[prec] = {"max": max(per), "final": per[-1], "per_checkpoint": per,
+                        "seconds": time.perf_counter() - t0}
+        plan.close()
+    line = {"metric": "max rel err vs FP64 oracle over the run", "workload": desc, "steps": total,
+            "checkpoints": marks, "errors": errors,
+            "floors": {"fp32_input_rounding": {"max": max(floor_in), "per_checkpoint": floor_in},
+                       "fp32_shadow": {"max": max(floor_sh), "per_checkpoint": floor_sh}},
+            "oracle": {"seconds_per_run": oracle_s, "cores": O.max_threads()},
+            "error_metric": "max over checkpoints and components of max|U - U_ref| / max|U_ref|"}
+    print(json.dumps(line), flush=True)
 
 
 def initial_field(name):
@@ -284,6 +450,17 @@ def make_plan(name, precision, stream=None, autotune=False):
                         kappa_comp=(ku, kv), stream=stream, autotune=autotune)
     return etd.Plan(d, n, ku, q, tau, pade=2, precision=precision, reaction=rx, n_comp=1, stream=stream,
                     autotune=autotune)
+
+
+def tensor_peak(peaks, src, precision, timed_s):
+    """Tensor peak for the precision's product kind: the measured BF16 burst rate
+    for a timed region shorter than 2 s (the kernels run near the burst clocks),
+    the sustained rate for longer ones; TF32 products at the nominal TF32/BF16
+    ratio of it."""
+    key = "bf16_tflops" if timed_s < 2.0 else "bf16_tflops_sustained"
+    bf16_mode = precision.startswith("bf16")
+    peak = peaks[key] * (1.0 if bf16_mode else TF32_OVER_BF16)
+    return peak, f"{src}: {key}" + ("" if bf16_mode else " x 1.1/2.25 (TF32/BF16 nominal)")
 
 
 def measured_peaks():
@@ -385,11 +562,12 @@ def barrier(world):
         dist.barrier()
 
 
-def cpu_baseline(name, gpu_field=None, gpu_steps=0, max_steps=200):
+def cpu_baseline(name, gpu_field=None, gpu_steps=0, max_steps=200, fp32_input=True):
     """The FP64 CPU oracle as it stands, all host cores, on the same workload.
 
     It runs min(gpu_steps, max_steps) time steps (at least 5) from the same
-    initial field; when that covers every step the GPU took, the GPU's field is
+    initial field (as the GPU received it: rounded to FP32 for the FP32-field
+    precisions); when that covers every step the GPU took, the GPU's field is
     compared with the oracle's (max |U_gpu - U_oracle| / max |U_oracle| per
     component, the error the metric is quoted at)."""
     import numpy as np
@@ -400,6 +578,8 @@ def cpu_baseline(name, gpu_field=None, gpu_steps=0, max_steps=200):
     kap = (ku, kv) if rx == "fhn" else (ku,)
     P = O.Problem(d=d, n=n, kappa=kap, q=q, tau=tau, pade=2, reaction=rx, rp=FHN if rx == "fhn" else ())
     u0 = initial_field(name)
+    if fp32_input:
+        u0 = u0.astype(np.float32).astype(np.float64)
     O.lib()  # build and load before timing
     steps = max(5, min(gpu_steps, max_steps))
     t0 = time.perf_counter()
@@ -490,11 +670,18 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true", help="time the pass kernel candidates at plan creation")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="error vs the FP64 oracle over the workload's whole run length, with floors")
+    ap.add_argument("--precisions", default="bf16x6,tf32x3", help="--accuracy: comma-separated precisions")
+    ap.add_argument("--accuracy-steps", type=int, default=None, help="--accuracy: override the run length")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.accuracy:
+        run_accuracy(args, world, rank, local)
         return
 
     if args.workload == "ensemble512":
@@ -566,14 +753,11 @@ def main():
         # the bound whose time is larger (2D m=4096: tensor; 3D m=256: HBM)
         flops = info.gemm_flops * info.products
         bytes_pass = info.step_bytes / info.gemms_per_step
-        bf16_mode = args.precision.startswith("bf16")
-        tpeak = peaks["bf16_tflops_sustained"] * (1.0 if bf16_mode else TF32_OVER_BF16)
+        tpeak, tsrc = tensor_peak(peaks, src, args.precision, el_max / 1e3)
         hpeak = peaks["hbm_gbs"]
         sec = avg_gemm_ms * 1e-3
         tens = {"achieved": flops / sec / 1e12, "peak": tpeak, "unit": "TFLOP/s",
-                "frac": flops / sec / 1e12 / tpeak, "per_launch": flops,
-                "peak_source": (f"{src}: bf16_tflops_sustained" if bf16_mode else
-                                f"{src}: bf16_tflops_sustained x 1.1/2.25 (TF32/BF16 nominal)")}
+                "frac": flops / sec / 1e12 / tpeak, "per_launch": flops, "peak_source": tsrc}
         hbm = {"achieved": bytes_pass / sec / 1e9, "peak": hpeak, "unit": "GB/s",
                "frac": bytes_pass / sec / 1e9 / hpeak, "per_launch": bytes_pass, "peak_source": f"{src}: hbm_gbs"}
         bound = "hbm" if bytes_pass / (hpeak * 1e9) > flops / (tpeak * 1e12) else "tensor"
@@ -644,7 +828,8 @@ def main():
     if cs:
         line["clocks"] = cs
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(name, gpu_field, args.warmup + args.steps)
+        line["cpu_baseline"] = cpu_baseline(name, gpu_field, args.warmup + args.steps,
+                                            fp32_input=plan.dtype == torch.float32)
         if "rel_err_vs_gpu" in line["cpu_baseline"]:
             line["rel_err_vs_fp64_oracle"] = line["cpu_baseline"]["rel_err_vs_gpu"]
     plan.close()

@@ -21,8 +21,10 @@
  *   - The caller owns every field pointer. The plan owns P, the grids, all
  *     workspaces and the carried spectral state; etd_plan_destroy frees them.
  *   - Every call returns an etd_status; none aborts or throws. Kernel-side
- *     errors (a bounded wait that gave up, a non-finite field) are reported by
- *     the next etd_sync (or etd_step_host, which synchronises).
+ *     errors are reported by the next etd_sync (or etd_step_host, which
+ *     synchronises): a bounded device wait that gave up (ETD_ERR_TIMEOUT) and,
+ *     when the plan checks its field (etd_options.diag_every > 0), a field
+ *     with non-finite values or beyond the bound diag_max_abs (ETD_ERR_DIVERGED).
  *   - Calls on one plan must come from one host thread at a time.
  */
 #ifndef ETD_H
@@ -40,7 +42,7 @@ typedef enum {
     ETD_ERR_OOM = 2,         /* a device allocation failed */
     ETD_ERR_CUDA = 3,        /* a CUDA runtime or driver call failed */
     ETD_ERR_UNSUPPORTED = 4, /* valid request this build or GPU cannot run */
-    ETD_ERR_DIVERGED = 5,    /* non-finite values found by etd_field_stats */
+    ETD_ERR_DIVERGED = 5,    /* non-finite values or |u| beyond diag_max_abs (in-step check, etd_field_stats) */
     ETD_ERR_TIMEOUT = 6      /* a device-side wait exceeded its time limit */
 } etd_status;
 
@@ -49,10 +51,11 @@ enum {
     ETD_PREC_FP64 = 0,   /* double fields and state, FP64 CUDA-core products */
     ETD_PREC_FP32 = 1,   /* float fields, FP32 CUDA-core products */
     ETD_PREC_TF32 = 2,   /* float fields, one TF32 tensor-core product */
-    ETD_PREC_TF32X3 = 3, /* float fields, split TF32: hi*hi + hi*lo + lo*hi (default) */
+    ETD_PREC_TF32X3 = 3, /* float fields, split TF32: hi*hi + hi*lo + lo*hi */
     ETD_PREC_BF16X3 = 4, /* float fields, BF16 hi/lo split, three products */
     ETD_PREC_BF16X6 = 5, /* float fields, BF16 hi/mid/lo split, six products in every pass,
-                            correction products in their own accumulator (most accurate) */
+                            correction products in their own accumulator (default; the most
+                            accurate tensor-core mode) */
     ETD_PREC_TF32X6 = 6, /* float fields, TF32 hi/mid/lo split, six products, as BF16X6 */
     ETD_PREC_DST32 = 7   /* float fields, every transform as fast sine transforms (FFT-based DST-I
                             in FP32 on CUDA cores) instead of the dense product with P: a
@@ -90,14 +93,31 @@ enum {
 };
 
 typedef struct {
-    int precision;         /* ETD_PREC_*, default ETD_PREC_TF32X3 */
+    int precision;         /* ETD_PREC_*, default ETD_PREC_BF16X6 */
     int reaction;          /* ETD_RX_*, default ETD_RX_ALLEN_CAHN */
     double rx_params[8];   /* reaction parameters, see ETD_RX_* */
     int n_comp;            /* 1 or 2; default 1 */
     double kappa_comp[2];  /* per-component diffusivity; <= 0 means "use kappa" */
     void* stream;          /* cudaStream_t the plan launches on; NULL = legacy default */
     int flags;             /* ETD_FLAG_* bits, default 0 */
+    int diag_every;        /* in-step field check (step a8) every diag_every time steps; 0 (default) = off */
+    double diag_max_abs;   /* bound on max |u| for that check; <= 0 (default) = only non-finite values */
 } etd_options;
+
+/*
+ * In-step field check (diag_every = k > 0). The stability theorem of Section 4
+ * bounds max |U^n| by a constant M_* independent of n and tau; a field that
+ * leaves such a bound, or holds NaN/Inf, means the run has failed. After every
+ * k-th time step of etd_step (counted over the plan's life) the plan reduces
+ * max |u| and the number of non-finite values of the returned field in FP64 on
+ * the device, with no host synchronisation. When the field has a non-finite
+ * value, or max |u| > diag_max_abs > 0, the plan raises its error flag: later
+ * tensor-core passes of the plan return at once, and the next etd_sync returns
+ * ETD_ERR_DIVERGED (its etd_last_error names the step, max |u| and the count),
+ * clears the flag and forgets the carried spectral state. An ensemble
+ * (etd_batch_create) checks every group's fields after the last step of each
+ * etd_batch_step call.
+ */
 
 /*
  * ETD_FLAG_AUTOTUNE: at plan creation (and for each group of an ensemble),
@@ -233,7 +253,7 @@ etd_status etd_set_time(etd_plan* p, double t);
 etd_status etd_sync(etd_plan* p);
 
 /*
- * FP64 diagnostics of a device field (step a8): *max_abs = max |u| and
+ * FP64 diagnostics of a device field (step a8, on demand): *max_abs = max |u| and
  * *n_nonfinite = number of NaN/Inf entries over all components. Synchronises.
  * Returns ETD_ERR_DIVERGED when n_nonfinite > 0 (outputs still written).
  */
@@ -267,9 +287,13 @@ etd_status etd_kernel_times(etd_plan* p, int kind, double* total_ms, long long* 
  * n^2 + k n_comp n^d floats (k = 1 in 2D, 2 in 3D) and returns ETD_ERR_INVALID_ARG
  * beyond that. The call allocates nothing. Its first call on a device looks up
  * the array's device address (cudaGetSymbolAddress, with that device current);
- * make that first call before any stream capture. All calls share the array and
- * it keeps the last call's contents: calls that overlap on the GPU (other streams,
- * other host threads) race. Asynchronous on `stream`.
+ * make that first call before any stream capture. The address is kept per device
+ * together with the CUDA context's id; after cudaDeviceReset (a new context, the
+ * array loaded again) the next call repeats the look-up, so make it outside a
+ * capture as well. All calls share the array and it keeps the last call's
+ * contents: calls that overlap on the GPU (other streams, other host threads)
+ * race. Launch failures are read from each launch's own return code; an error
+ * that earlier work left pending is not cleared. Asynchronous on `stream`.
  */
 #define ETD_NOALLOC_MAX_ELEMS 4194304
 etd_status etd_transform_noalloc(int d, int n, int n_comp, const void* in_dev, void* out_dev, void* stream);

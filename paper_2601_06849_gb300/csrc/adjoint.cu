@@ -216,11 +216,18 @@ int blocks_for(long long work) {
     return (int)(b < 1 ? 1 : b);
 }
 
+// Blocks for the kernels that give one warp to each spectral row of n modes
+// (eight rows per 256-thread block): a grid sized by points would leave most
+// warps without a row.
+int blocks_for_rows(long long npts, int n) {
+    return blocks_for((npts / n) * 32);
+}
+
 }  // namespace
 
 template <typename T>
 void launch_spec_combine(const SpecCombine<T>& a, cudaStream_t st) {
-    spec_combine_kernel<T><<<dim3(blocks_for(a.npts), a.ncomp), 256, 0, st>>>(a);
+    spec_combine_kernel<T><<<dim3(blocks_for_rows(a.npts, a.n), a.ncomp), 256, 0, st>>>(a);
 }
 template <typename T>
 void launch_react_vjp(const ReactVjp<T>& a, cudaStream_t st) {
@@ -228,7 +235,7 @@ void launch_react_vjp(const ReactVjp<T>& a, cudaStream_t st) {
 }
 template <typename T>
 void launch_grad_kappa(const GradKappa<T>& a, cudaStream_t st) {
-    grad_kappa_kernel<T><<<dim3(blocks_for(a.npts), a.ncomp), 256, 0, st>>>(a);
+    grad_kappa_kernel<T><<<dim3(blocks_for_rows(a.npts, a.n), a.ncomp), 256, 0, st>>>(a);
 }
 template <typename T>
 void launch_grad_rx(const GradRx<T>& a, cudaStream_t st) {

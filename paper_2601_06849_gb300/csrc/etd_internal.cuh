@@ -51,7 +51,7 @@ __device__ __forceinline__ void split_bf16_f(float v, int pieces, __nv_bfloat16*
     lo2[o] = __float2bfloat16_rn(r1 - __bfloat162float(m));
 }
 
-enum ErrBits : unsigned { ERR_TIMEOUT = 1u, ERR_BAD_CONFIG = 2u };
+enum ErrBits : unsigned { ERR_TIMEOUT = 1u, ERR_BAD_CONFIG = 2u, ERR_DIVERGED = 4u };
 
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;
@@ -562,6 +562,11 @@ void launch_stats_f32(const float* u, long long count, double* acc, cudaStream_t
 // *flag |= 1 if the byte ranges a and b (16-byte aligned, length a multiple of 4) differ.
 void launch_differ(const void* a, const void* b, size_t bytes, unsigned* flag, cudaStream_t st);
 void launch_stats_f64(const double* u, long long count, double* acc, cudaStream_t st);
+// In-step check (step a8): after launch_stats_* into acc[0..1], raise ERR_DIVERGED
+// in err[0] when acc holds a non-finite count or max |u| > limit > 0; the first
+// failure records its step in err[1] and max |u|, count in saved[0..1].
+void launch_diag_check(const double* acc, double limit, unsigned step, unsigned* err, double* saved,
+                       cudaStream_t st);
 
 // tcgen05 transform pass (gemm_tc.cu)
 struct TcConfig {

@@ -49,7 +49,7 @@ struct TimedLaunch {
 };
 
 struct etd_plan {
-    int d = 0, n = 0, ncomp = 1, precision = ETD_PREC_TF32X3, pade = 2, reaction = ETD_RX_ALLEN_CAHN;
+    int d = 0, n = 0, ncomp = 1, precision = ETD_PREC_BF16X6, pade = 2, reaction = ETD_RX_ALLEN_CAHN;
     int ninst = 1;  // instances stepped together (same d and n); batch index = instance * ncomp + comp
     double rp[8] = {0};
     double kappa[2] = {0, 0};
@@ -75,7 +75,10 @@ struct etd_plan {
     void* wphys = nullptr;
     void* op[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // operand buffers x pieces
     unsigned* err = nullptr;
-    double* stats = nullptr;
+    double* stats = nullptr;  // [0..1] reductions, [3] etd_step_host's compare flag, [4..5] first failed check
+    int diag_every = 0;       // in-step field check every diag_every steps (0 = off)
+    double diag_max = 0;      // bound on max |u| of that check (<= 0: non-finite values only)
+    long long steps_done = 0; // time steps taken over the plan's life (the check's counter)
     void* host_field = nullptr;  // etd_step_host: the field being stepped (the last one returned)
     void* host_in = nullptr;     // etd_step_host: the incoming field
     bool host_valid = false;     // host_field holds the field the last etd_step_host returned
@@ -417,10 +420,29 @@ etd_status step_once(etd_plan* p, void* u, bool last) {
     return ETD_OK;
 }
 
+// Step a8 on the device: FP64 max |u| and non-finite count of the field u (the
+// plan's whole stacked field), then the bound check that raises ERR_DIVERGED.
+// Asynchronous; etd_sync reports the outcome.
+etd_status run_diag(etd_plan* p, const void* u) {
+    const long long count = (long long)p->ninst * p->ncomp * p->npts;
+    ETD_CUDA(cudaMemsetAsync(p->stats, 0, sizeof(double) * 2, p->stream));
+    if (p->elem == 8)
+        launch_stats_f64((const double*)u, count, p->stats, p->stream);
+    else
+        launch_stats_f32((const float*)u, count, p->stats, p->stream);
+    launch_diag_check(p->stats, p->diag_max, (unsigned)p->steps_done, p->err, p->stats + 4, p->stream);
+    ETD_CUDA(cudaGetLastError());
+    return ETD_OK;
+}
+
 template <typename T>
 etd_status step_impl(etd_plan* p, void* u, int n_steps) {
     etd_status s = ensure_state<T>(p, u);
-    for (int it = 0; it < n_steps && s == ETD_OK; ++it) s = step_once<T>(p, u, it == n_steps - 1);
+    for (int it = 0; it < n_steps && s == ETD_OK; ++it) {
+        s = step_once<T>(p, u, it == n_steps - 1);
+        ++p->steps_done;
+        if (s == ETD_OK && p->diag_every > 0 && p->steps_done % p->diag_every == 0) s = run_diag(p, u);
+    }
     return s;
 }
 
@@ -631,7 +653,7 @@ extern "C" {
 etd_status etd_options_default(etd_options* opt) {
     if (!opt) return fail(ETD_ERR_INVALID_ARG, "opt is NULL");
     std::memset(opt, 0, sizeof(*opt));
-    opt->precision = ETD_PREC_TF32X3;
+    opt->precision = ETD_PREC_BF16X6;
     opt->reaction = ETD_RX_ALLEN_CAHN;
     opt->n_comp = 1;
     return ETD_OK;
@@ -649,6 +671,8 @@ etd_status validate_options(int d, int m, int pade_order, const etd_options& opt
         return fail(ETD_ERR_INVALID_ARG, "pade_order must be 2, 4 or 0 (exact exponential)");
     if (opt.n_comp < 1 || opt.n_comp > 2) return fail(ETD_ERR_INVALID_ARG, "n_comp must be 1 or 2");
     if (opt.flags & ~ETD_FLAG_AUTOTUNE) return fail(ETD_ERR_INVALID_ARG, "unknown bits in flags (0x%x)", opt.flags);
+    if (opt.diag_every < 0) return fail(ETD_ERR_INVALID_ARG, "diag_every must be >= 0");
+    if (std::isnan(opt.diag_max_abs)) return fail(ETD_ERR_INVALID_ARG, "diag_max_abs is NaN");
     if (opt.reaction < ETD_RX_NONE || opt.reaction > ETD_RX_AC_FORCED)
         return fail(ETD_ERR_INVALID_ARG, "unknown reaction");
     if (opt.reaction == ETD_RX_FHN && opt.n_comp != 2)
@@ -774,6 +798,8 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     p->q = qv[0];
     p->tau = dtv[0];
     p->stream = (cudaStream_t)opt.stream;
+    p->diag_every = opt.diag_every;
+    p->diag_max = opt.diag_max_abs;
     p->elem = (opt.precision == ETD_PREC_FP64) ? 8 : 4;
     p->bf16 = (opt.precision == ETD_PREC_BF16X3 || opt.precision == ETD_PREC_BF16X6);
     p->use_tc = p->bf16 || opt.precision == ETD_PREC_TF32 || opt.precision == ETD_PREC_TF32X3 ||
@@ -854,7 +880,7 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     for (int i = 0; i < 2 && s == ETD_OK; ++i)
         for (int j = 0; j < p->pieces && s == ETD_OK; ++j) s = dalloc(p, &p->op[i][j], op_bytes);
     if (s == ETD_OK) s = dalloc(p, (void**)&p->err, sizeof(unsigned) * 4);
-    if (s == ETD_OK) s = dalloc(p, (void**)&p->stats, sizeof(double) * 4);
+    if (s == ETD_OK) s = dalloc(p, (void**)&p->stats, sizeof(double) * 8);
     if (s != ETD_OK) {
         free_plan(p);
         return s;
@@ -1130,6 +1156,10 @@ etd_status etd_batch_step(etd_plan* B, void* const* u_dev, int n_steps) {
         char* gf = static_cast<char*>(B->gfield[gi]);
         ETD_CUDA(cudaStreamWaitEvent(g->stream, B->ev_start, 0));
         etd_status s = group_step_once(g, gf, true);
+        if (s == ETD_OK && g->diag_every > 0) {
+            g->steps_done += n_steps;
+            s = run_diag(g, gf);
+        }
         if (s != ETD_OK) return s;
         for (size_t li = 0; li < B->members[gi].size(); ++li)
             ETD_CUDA(cudaMemcpyAsync(u_dev[B->members[gi][li]], gf + li * inst_bytes, inst_bytes,
@@ -1220,13 +1250,19 @@ etd_status etd_sync(etd_plan* p) {
     }
     ETD_CUDA(cudaStreamSynchronize(p->stream));
     if (p->is_batch) return ETD_OK;
-    unsigned flags = 0;
-    ETD_CUDA(cudaMemcpy(&flags, p->err, sizeof flags, cudaMemcpyDeviceToHost));
-    if (flags) {
-        ETD_CUDA(cudaMemset(p->err, 0, sizeof(unsigned)));
+    unsigned flags[2] = {0, 0};
+    ETD_CUDA(cudaMemcpy(flags, p->err, sizeof flags, cudaMemcpyDeviceToHost));
+    if (flags[0]) {
+        double saved[2] = {0, 0};
+        if (flags[0] & ERR_DIVERGED) ETD_CUDA(cudaMemcpy(saved, p->stats + 4, sizeof saved, cudaMemcpyDeviceToHost));
+        ETD_CUDA(cudaMemset(p->err, 0, sizeof(unsigned) * 2));
         p->uhat_valid = false;
-        if (flags & ERR_TIMEOUT) return fail(ETD_ERR_TIMEOUT, "a device-side wait exceeded its time limit");
-        return fail(ETD_ERR_CUDA, "device error flags 0x%x", flags);
+        if (flags[0] & ERR_TIMEOUT) return fail(ETD_ERR_TIMEOUT, "a device-side wait exceeded its time limit");
+        if (flags[0] & ERR_DIVERGED)
+            return fail(ETD_ERR_DIVERGED,
+                        "in-step field check after step %u: max |u| = %.6g (bound %.6g), %.0f non-finite values",
+                        flags[1], saved[0], p->diag_max, saved[1]);
+        return fail(ETD_ERR_CUDA, "device error flags 0x%x", flags[0]);
     }
     return ETD_OK;
 }

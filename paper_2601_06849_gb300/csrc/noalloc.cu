@@ -13,9 +13,12 @@
 // The workspace is g_noalloc_scratch below: ETD_NOALLOC_MAX_ELEMS floats
 // (16 MiB). Every GPU that loads the library holds it until the process exits.
 // In host code the name of a __device__ array is only a host-side stand-in, so
-// the entry point looks up its device address once per device with
-// cudaGetSymbolAddress (with that device current) and passes that pointer to
-// the kernels.
+// the entry point looks up its device address once per device and CUDA context
+// with cudaGetSymbolAddress (with that device current) and passes that pointer
+// to the kernels. The context's unique id (cuCtxGetId) is kept with the address:
+// after cudaDeviceReset the runtime creates a new context, the module and its
+// array are loaded again at a new address, and the next call repeats the set-up.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -32,6 +35,35 @@ __device__ __align__(256) float g_noalloc_scratch[ETD_NOALLOC_MAX_ELEMS];
 constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 float* g_scratch_ptr[MAX_DEVICES] = {nullptr};
+unsigned long long g_scratch_ctx[MAX_DEVICES] = {0};  // context id the address belongs to (0: unknown)
+
+// Unique id of the current context through the driver entry points (no link
+// against libcuda); 0 when the driver does not offer them.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) == cudaSuccess &&
+            qa == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) == cudaSuccess &&
+            qb == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+            get_id = reinterpret_cast<CtxGetIdFn>(b);
+        }
+        looked_up = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
 
 // P[j][k] = sqrt(2/(n+1)) sin(pi (j+1)(k+1)/(n+1)), the orthonormal sine
 // eigenvectors of the 1D Dirichlet second difference (Section 3.3.2's P_x).
@@ -130,8 +162,9 @@ extern "C" etd_status etd_transform_noalloc(int d, int n, int n_comp, const void
     float* base = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_ptr[dev]) {
-            // first call on this device: device address of the static workspace
+        const unsigned long long ctx = current_context_id();
+        if (!g_scratch_ptr[dev] || ctx != g_scratch_ctx[dev]) {
+            // set-up, once per device and context: device address of the static workspace
             void* ptr = nullptr;
             ce = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
             if (ce != cudaSuccess) {
@@ -141,6 +174,8 @@ extern "C" etd_status etd_transform_noalloc(int d, int n, int n_comp, const void
                 return fail_noalloc(ETD_ERR_CUDA, msg);
             }
             g_scratch_ptr[dev] = static_cast<float*>(ptr);
+            // the lookup made the device's context current if none was: record that one
+            g_scratch_ctx[dev] = current_context_id();
         }
         base = g_scratch_ptr[dev];
     }
@@ -154,18 +189,22 @@ extern "C" etd_status etd_transform_noalloc(int d, int n, int n_comp, const void
     // nothing has to be cleared
     long long pblocks = ((long long)n * n + 255) / 256;
     if (pblocks > 4096) pblocks = 4096;
-    noalloc_build_p<<<(unsigned)pblocks, 256, 0, st>>>(P, n);
+    // Each launch is checked through its own return code (cudaLaunchKernel), so
+    // an error some earlier work of the caller left pending is neither reported
+    // as this call's failure nor cleared.
+    int nn = n;
+    void* pargs[] = {&P, &nn};
+    ce = cudaLaunchKernel((const void*)noalloc_build_p, dim3((unsigned)pblocks), dim3(256), pargs, 0, st);
     const dim3 grid((M + TB - 1) / TB, (n + TB - 1) / TB, n_comp);
-    const float* src = static_cast<const float*>(in_dev);
-    if (d == 2) {
-        noalloc_pass<<<grid, 256, 0, st>>>(src, P, buf0, M, n, mq);
-        noalloc_pass<<<grid, 256, 0, st>>>(buf0, P, static_cast<float*>(out_dev), M, n, mq);
-    } else {
-        noalloc_pass<<<grid, 256, 0, st>>>(src, P, buf0, M, n, mq);
-        noalloc_pass<<<grid, 256, 0, st>>>(buf0, P, buf1, M, n, mq);
-        noalloc_pass<<<grid, 256, 0, st>>>(buf1, P, static_cast<float*>(out_dev), M, n, mq);
+    const float* chain[4] = {static_cast<const float*>(in_dev), buf0, d == 2 ? static_cast<float*>(out_dev) : buf1,
+                             static_cast<float*>(out_dev)};
+    int MM = M, mqq = mq;
+    for (int pass = 0; pass < d && ce == cudaSuccess; ++pass) {
+        const float* a = chain[pass];
+        float* o = const_cast<float*>(chain[pass + 1]);
+        void* args[] = {&a, &P, &o, &MM, &nn, &mqq};
+        ce = cudaLaunchKernel((const void*)noalloc_pass, grid, dim3(256), args, 0, st);
     }
-    ce = cudaGetLastError();
     if (ce != cudaSuccess) {
         char msg[256];
         snprintf(msg, sizeof msg, "etd_transform_noalloc: launch failed: %s", cudaGetErrorString(ce));

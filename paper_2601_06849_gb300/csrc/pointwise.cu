@@ -2,7 +2,8 @@
 //   - the reaction f(t, u) of all components at one grid point (steps a1 and
 //     a5: f(t_n, U) in eq. (13), f(t_{n+1}, W) in eq. (14)), written straight
 //     into the operand planes of the next transform pass;
-//   - FP64 field diagnostics (step a8): max |u| and the count of non-finite values.
+//   - FP64 field diagnostics (step a8): max |u| and the count of non-finite values,
+//     and the in-step check of those against the plan's bound.
 // Both are bandwidth-bound: one read of each component and one write of each
 // operand plane per point.
 #include "etd_internal.cuh"
@@ -292,6 +293,25 @@ void launch_differ(const void* a, const void* b, size_t bytes, unsigned* flag, c
     const uint32_t* tb = reinterpret_cast<const uint32_t*>(static_cast<const char*>(b) + n16 * 16);
     differ_kernel<<<grid_for(n16, 256), 256, 0, st>>>(static_cast<const uint4*>(a), static_cast<const uint4*>(b), n16,
                                                        ta, tb, tail, flag);
+}
+
+// One thread: compare the reduced statistics with the bound (step a8).
+__global__ void diag_check_kernel(const unsigned long long* __restrict__ acc, double limit, unsigned step,
+                                  unsigned* err, double* saved) {
+    const double m = __longlong_as_double((long long)acc[0]);
+    const unsigned long long bad = acc[1];
+    if (bad != 0ull || (limit > 0.0 && m > limit)) {
+        if ((atomicOr(err, ERR_DIVERGED) & ERR_DIVERGED) == 0u) {  // the first failure since the last sync
+            err[1] = step;
+            saved[0] = m;
+            saved[1] = (double)bad;
+        }
+    }
+}
+
+void launch_diag_check(const double* acc, double limit, unsigned step, unsigned* err, double* saved,
+                       cudaStream_t st) {
+    diag_check_kernel<<<1, 1, 0, st>>>(reinterpret_cast<const unsigned long long*>(acc), limit, step, err, saved);
 }
 
 void launch_stats_f32(const float* u, long long count, double* acc, cudaStream_t st) {

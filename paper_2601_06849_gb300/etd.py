@@ -49,6 +49,8 @@ class etd_options(ctypes.Structure):
         ("kappa_comp", ctypes.c_double * 2),
         ("stream", ctypes.c_void_p),
         ("flags", ctypes.c_int),
+        ("diag_every", ctypes.c_int),
+        ("diag_max_abs", ctypes.c_double),
     ]
 
 
@@ -227,8 +229,8 @@ class Batch:
     ``n``, ``kappa``, ``q``, ``dt`` are per-instance sequences; the reaction,
     precision, Pade order and component count are shared."""
 
-    def __init__(self, d, n, kappa, q, dt, pade=2, precision="tf32x3", reaction="fhn", rx_params=(), n_comp=2,
-                 kappa_v=None, stream=None, autotune=False):
+    def __init__(self, d, n, kappa, q, dt, pade=2, precision="bf16x6", reaction="fhn", rx_params=(), n_comp=2,
+                 kappa_v=None, stream=None, autotune=False, diag_every=0, diag_max_abs=0.0):
         import torch
 
         count = len(n)
@@ -245,6 +247,8 @@ class Batch:
             opt.kappa_comp[1] = float(kappa_v)
         if autotune:
             opt.flags |= ETD_FLAG_AUTOTUNE
+        opt.diag_every = int(diag_every)
+        opt.diag_max_abs = float(diag_max_abs)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -292,11 +296,14 @@ class Plan:
 
     ``pade``: 2 (P_{0,2}), 4 (P_{0,4}) or "exact" (eq. (9)-(10)).
     ``precision``: one of PRECISION; fields are float64 for "fp64", else float32.
+    ``diag_every``, ``diag_max_abs``: the in-step field check of etd_options
+    (0 = off); a failed check makes the next ``sync()`` raise ETD_ERR_DIVERGED.
     """
 
-    def __init__(self, d: int, n: int, kappa: float, q: float, dt: float, pade=2, precision: str = "tf32x3",
+    def __init__(self, d: int, n: int, kappa: float, q: float, dt: float, pade=2, precision: str = "bf16x6",
                  reaction: str = "allen_cahn", rx_params: Sequence[float] = (), n_comp: int = 1,
-                 kappa_comp: Optional[Sequence[float]] = None, stream=None, autotune: bool = False):
+                 kappa_comp: Optional[Sequence[float]] = None, stream=None, autotune: bool = False,
+                 diag_every: int = 0, diag_max_abs: float = 0.0):
         import torch
 
         self.d, self.n, self.dt, self.n_comp = d, n, dt, n_comp
@@ -313,6 +320,8 @@ class Plan:
                 opt.kappa_comp[i] = float(v)
         if autotune:
             opt.flags |= ETD_FLAG_AUTOTUNE
+        opt.diag_every = int(diag_every)
+        opt.diag_max_abs = float(diag_max_abs)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -93,3 +93,15 @@ def test_plan_info_layout_matches_header():
             tok = re.findall(r"([A-Za-z_]\w*)\s*(?:\[\d+\])?\s*$", part.strip())
             names.append(tok[-1])
     assert names == [f[0] for f in etd.etd_plan_info._fields_]
+
+
+def test_options_defaults_and_diag_validation(lib):
+    """Defaults: split BF16 x6 (the mode held to the 1e-6 bar), in-step check off;
+    a negative check interval is rejected before any device work."""
+    o = etd.etd_options_default()
+    assert o.precision == etd.PRECISION["bf16x6"]
+    assert o.diag_every == 0 and o.diag_max_abs == 0.0
+    o.diag_every = -1
+    with pytest.raises(etd.EtdError) as ei:
+        etd.etd_plan_create(2, 64, 0.1, 0.0, 1e-3, 2, o)
+    assert ei.value.status == etd.ETD_ERR_INVALID_ARG

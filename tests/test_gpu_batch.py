@@ -45,6 +45,34 @@ def test_mixed_grid_ensemble_matches_oracle(precision):
 
 
 @pytest.mark.gpu
+def test_ensemble_over_the_workload_grid_range():
+    """The batched workload's instances: one member of each of its 15 grid
+    sizes (n = 64, 96, .., 512), each with its own kappa_u and tau, stepped
+    together in split BF16 x6 and checked one by one against the oracle."""
+    torch = need_gpu()
+    members = inputs.fhn_ensemble(512, workload=3)
+    seen, chosen = set(), []
+    for m in members:
+        if m.n not in seen:
+            seen.add(m.n)
+            chosen.append(m)
+    assert sorted(seen) == list(range(64, 513, 32))
+    batch = etd.Batch(2, [m.n for m in chosen], [m.kappa_u for m in chosen], [0.0] * len(chosen),
+                      [m.tau for m in chosen], precision="bf16x6", reaction="fhn", rx_params=FHN, n_comp=2,
+                      kappa_v=KV)
+    fields = [torch.tensor(m.u0, dtype=torch.float32, device="cuda") for m in chosen]
+    steps = 10
+    batch.step(fields, steps)
+    batch.sync()
+    for i, m in enumerate(chosen):
+        ref = oracle_instance(2, m.n, m.kappa_u, m.tau, m.u0, steps)
+        got = fields[i].double().cpu().numpy()
+        for c in range(2):
+            assert rel_err(got[c], ref[c]) < 1e-6, (m.n, c)
+    batch.close()
+
+
+@pytest.mark.gpu
 def test_ensemble_with_2d_and_3d_instances_resumes():
     torch = need_gpu()
     d = [2, 3, 2, 3]

@@ -1,8 +1,8 @@
 """Parity at the workload sizes, in the launch configuration bench.py times.
 
-- 2D FitzHugh-Nagumo n = 4096 (two fields) and 3D Allen-Cahn n = 256, in the
-  split BF16 x6 precision bench.py times by default and in split TF32: two steps
-  against the full FP64 oracle field.
+- 2D FitzHugh-Nagumo n = 4096 (two fields) and 3D Allen-Cahn n = 256 and
+  n = 384, in the split BF16 x6 precision bench.py times by default and in split
+  TF32: two steps against the full FP64 oracle field.
 - Maximum sizes (2D n = 16384, 3D n = 512): no oracle run at that size; the
   f = 0 closed form holds at any size: a sine mode prod sin(k pi x) is
   multiplied per step by prod E_1(tau lambda_k) (Section 3.1 with the
@@ -39,10 +39,10 @@ def test_fhn_2d_n4096_bench_configuration(precision):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["bf16x6", "tf32x3"])
-def test_allen_cahn_3d_n256(precision):
+@pytest.mark.parametrize("precision,n", [("bf16x6", 256), ("tf32x3", 256), ("bf16x6", 384)])
+def test_allen_cahn_3d_workload_sizes(precision, n):
     torch = need_gpu()
-    n, steps, tau = 256, 2, 5e-3
+    steps, tau = 2, 5e-3
     u0 = inputs.gaussian_bump(n, 3)
     plan = etd.Plan(3, n, 1e-3, 0.1, tau, pade=2, precision=precision, reaction="allen_cahn")
     u = torch.tensor(u0, dtype=torch.float32, device="cuda")
