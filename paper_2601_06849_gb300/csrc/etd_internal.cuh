@@ -17,6 +17,8 @@
 
 #include <type_traits>
 
+#include "../../include/etd.h"
+
 namespace etd {
 
 enum EpiMode : int {
@@ -24,8 +26,37 @@ enum EpiMode : int {
     EPI_CARRY = 1,   // store the carried spectral state  U^ = value
     EPI_STAGE1 = 2,  // eq. (13) in the spectral basis -> W^, F^q, operand(W^)
     EPI_STAGE2 = 3,  // eq. (14) in the spectral basis -> U^+, operand(U^+)
-    EPI_PLAIN = 4    // store the physical field (rows of length n, own pitch)
+    EPI_PLAIN = 4,   // store the physical field (rows of length n, own pitch)
+    // Reaction fused into the epilogue (reactions that act on each component at a
+    // point on its own, rx_fusable): the value is a physical field value w, and
+    EPI_REACT = 5,       // f(w) is written as the next pass's operand (step a5 from a4)
+    EPI_PLAIN_REACT = 6  // w is stored as EPI_PLAIN does, and f(w) as the operand (a1 of the
+                         // next step from a7)
 };
+
+// Reactions the epilogue can evaluate: f at a point depends only on the same
+// component's value there (f = 0, c u, u - u^3, rho u / (1 - u)), so the thread
+// that holds one output value has all it needs. FitzHugh-Nagumo couples the two
+// components (held by different CTAs) and the manufactured forcing needs FP64
+// coordinates: those keep the reaction kernel.
+__host__ __device__ __forceinline__ bool rx_fusable(int kind) {
+    return kind == ETD_RX_NONE || kind == ETD_RX_LINEAR || kind == ETD_RX_ALLEN_CAHN || kind == ETD_RX_SINGULAR;
+}
+
+// f(w) of a fusable reaction, in the arithmetic of the reaction kernel.
+template <typename T>
+__device__ __forceinline__ T rx_point(int kind, T c, T w) {
+    switch (kind) {
+        case ETD_RX_LINEAR:
+            return c * w;
+        case ETD_RX_ALLEN_CAHN:
+            return w - w * w * w;
+        case ETD_RX_SINGULAR:
+            return c * w / ((T)1 - w);
+        default:
+            return (T)0;
+    }
+}
 
 // How an operand is written for the tensor-core products.
 enum SplitKind : int {
@@ -150,6 +181,8 @@ struct Epi {
     St* uhat;        // carried spectral state U^   (internal layout)
     St* zhat;        // Z of the current step (stage 1 -> stage 2)
     const St* grid;  // [comp][3][n]: E_1, tau E_2, tau E_3 at tau * lambda_k
+    int rx;          // EPI_REACT / EPI_PLAIN_REACT: the reaction (rx_fusable)
+    T rx_c;          // its parameter (c of ETD_RX_LINEAR, rho of ETD_RX_SINGULAR)
 
     __device__ __forceinline__ void write_operand(long long o, double v) const {
         op_hi[o] = (T)v;  // FP64 path: one plane, CUDA-core products
@@ -220,19 +253,25 @@ __device__ __forceinline__ void epi_apply_batch(const Epi<float>& e, int b, int 
                                                 int count, const float2 (&st)[N]) {
     const long long base = (long long)b * e.bs + (long long)mh * e.ld + ml;
     const long long step = (long long)e.mq * e.ld;  // offset between consecutive nn
-    if (e.mode == EPI_PLAIN) {
+    if (e.mode == EPI_PLAIN || e.mode == EPI_PLAIN_REACT) {
         float* d = e.dst + (long long)b * e.bs_dst + ((long long)nn0 * e.mq + mh) * e.ld_dst + ml;
         const long long sd = (long long)e.mq * e.ld_dst;
 #pragma unroll
         for (int j = 0; j < N; ++j)
             if (j < count) d[j * sd] = v[j];
-        return;
+        if (e.mode == EPI_PLAIN) return;
     }
     const long long o0 = base + (long long)nn0 * step;
     if (e.mode == EPI_SPLIT) {
 #pragma unroll
         for (int j = 0; j < N; ++j)
             if (j < count) e.write_operand_f(o0 + j * step, v[j]);
+        return;
+    }
+    if (e.mode == EPI_REACT || e.mode == EPI_PLAIN_REACT) {  // f(w) as the next pass's operand
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+            if (j < count) e.write_operand_f(o0 + j * step, rx_point<float>(e.rx, e.rx_c, v[j]));
         return;
     }
     if (e.mode == EPI_CARRY) {
@@ -295,7 +334,9 @@ inline bool epi_rows8_ok(const Epi<float>& e) {
     if (e.n % 8 != 0 || e.ld % 8 != 0 || e.bs % 8 != 0) return false;
     if (!aligned16(e.op_hi) || !aligned16(e.op_lo) || !aligned16(e.op_lo2)) return false;
     if (!aligned16(e.uhat) || !aligned16(e.zhat) || !aligned16(e.grid)) return false;
-    if (e.mode == EPI_PLAIN && (e.ld_dst % 8 != 0 || e.bs_dst % 8 != 0 || !aligned16(e.dst))) return false;
+    if ((e.mode == EPI_PLAIN || e.mode == EPI_PLAIN_REACT) &&
+        (e.ld_dst % 8 != 0 || e.bs_dst % 8 != 0 || !aligned16(e.dst)))
+        return false;
     return true;
 }
 
@@ -366,12 +407,18 @@ __device__ __forceinline__ void write_operand_ff8(const Epi<float>& e, long long
 
 __device__ __forceinline__ void epi_apply_rows8(const Epi<float>& e, int b, int mh, int ml0, int nn, const float (&v)[8],
                                                 const float4 (&st4)[4]) {
-    if (e.mode == EPI_PLAIN) {
+    if (e.mode == EPI_PLAIN || e.mode == EPI_PLAIN_REACT) {
         store8(e.dst + (long long)b * e.bs_dst + ((long long)nn * e.mq + mh) * e.ld_dst + ml0, v);
-        return;
+        if (e.mode == EPI_PLAIN) return;
     }
     const long long o = (long long)b * e.bs + ((long long)nn * e.mq + mh) * e.ld + ml0;
     float2 w[8];
+    if (e.mode == EPI_REACT || e.mode == EPI_PLAIN_REACT) {  // f(w) as the next pass's operand
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[i] = make_float2(rx_point<float>(e.rx, e.rx_c, v[i]), 0.f);
+        write_operand_ff8(e, o, w);
+        return;
+    }
     if (e.mode == EPI_SPLIT || e.mode == EPI_CARRY) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) w[i] = make_float2(v[i], 0.f);
@@ -425,11 +472,15 @@ __device__ __forceinline__ void Epi<T>::apply(int b, int mh, int ml, int nn, T v
         epi_load_state<1>(*this, b, mh, ml, nn, 1, st);
         epi_apply_batch<1>(*this, b, mh, ml, nn, &v, 1, st);
     } else {
-        if (mode == EPI_PLAIN) {
+        if (mode == EPI_PLAIN || mode == EPI_PLAIN_REACT) {
             dst[b * bs_dst + ((long long)nn * mq + mh) * ld_dst + ml] = v;
-            return;
+            if (mode == EPI_PLAIN) return;
         }
         const long long o = b * bs + ((long long)nn * mq + mh) * ld + ml;
+        if (mode == EPI_REACT || mode == EPI_PLAIN_REACT) {
+            write_operand(o, rx_point<double>(rx, rx_c, v));
+            return;
+        }
         const double* g = grid + (long long)b * 3 * n;
         switch (mode) {
             case EPI_SPLIT:

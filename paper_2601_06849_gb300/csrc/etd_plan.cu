@@ -86,6 +86,11 @@ struct etd_plan {
     // carried spectral state
     bool uhat_valid = false;
     const void* uhat_src = nullptr;
+    // fused reaction (rx_fusable): the last step's final epilogue left the operand
+    // pieces of f(U) for the next step in op[rx_cur] (for the field rx_src)
+    bool rx_ready = false;
+    int rx_cur = 0;
+    const void* rx_src = nullptr;
     // tensor-core pass: slot 0 = every internal pass, slot 1 = the output transform
     TcConfig tc[2] = {};
     TcMaps* maps = nullptr;
@@ -301,6 +306,8 @@ etd_status run_pass(etd_plan* p, int cur, int slot, int mode, int out_split, voi
     e.dst = (T*)dst;
     e.ld_dst = ld_dst;
     e.bs_dst = bs_dst;
+    e.rx = p->reaction;
+    e.rx_c = (T)p->rp[0];
     TimerScope ts(p, slot == p->out_slot && p->out_slot != 0 ? 2 : 0);
     if constexpr (sizeof(T) == 8) {
         launch_gemm_simt_f64((const double*)p->op[cur][0], (const double*)p->P[0], p->M, p->n, p->ninst * p->ncomp,
@@ -386,6 +393,7 @@ etd_status run_react(etd_plan* p, int kind, const void* in, int ld_in, long long
 template <typename T>
 etd_status ensure_state(etd_plan* p, void* u) {
     if (p->uhat_valid && p->uhat_src == u) return ETD_OK;
+    p->rx_ready = false;  // the rebuild below overwrites the operand buffers
     const int spo = split_for(p, p->out_slot);
     etd_status s = run_react<T>(p, -1, u, p->n, p->npts, p->t, spo);
     int cur = 0;
@@ -398,24 +406,46 @@ etd_status ensure_state(etd_plan* p, void* u) {
 
 // One time step from the carried state. Every transform runs with config slot 0
 // except, when `last`, the one that produces the field handed back to the
-// caller, which runs with p->out_slot (the accurate six-product kernel in
-// TF32X3 mode). Errors of the other transforms reach the state only through
-// f(U) and f(W), scaled by tau.
+// caller, which runs with p->out_slot (the accurate kernel of the split modes).
+// Errors of the other transforms reach the state only through f(U) and f(W),
+// scaled by tau.
+// Reactions that act on each component at a point alone (rx_fusable) are
+// evaluated in transform epilogues instead of the reaction kernel: f(t_{n+1}, W)
+// (step a5) in the epilogue of the pass that produces W, and, when chain_rx,
+// f(U+) of the next step (its a1) in the epilogue of the pass that returns U+;
+// the next step then starts from those operand pieces.
 template <typename T>
-etd_status step_once(etd_plan* p, void* u, bool last) {
+etd_status step_once(etd_plan* p, void* u, bool last, bool chain_rx) {
     const int n = p->n;
     const long long N = p->npts;
     const int sp0 = split_for(p, 0), spo = split_for(p, p->out_slot);
+    const bool fuse = rx_fusable(p->reaction);
     etd_status s;
     int cur = 0;
-    if ((s = run_react<T>(p, p->reaction, u, n, N, p->t, sp0)) != ETD_OK) return s;
-    cur = 0;
+    if (fuse && p->rx_ready && p->rx_src == u) {
+        cur = p->rx_cur;  // f(t_n, U) pieces from the previous step's last epilogue
+    } else if ((s = run_react<T>(p, p->reaction, u, n, N, p->t, sp0)) != ETD_OK) {
+        return s;
+    }
+    p->rx_ready = false;
     if ((s = run_chain<T>(p, cur, 0, EPI_STAGE1, sp0, nullptr, 0, 0)) != ETD_OK) return s;
-    if ((s = run_chain<T>(p, cur, 0, EPI_PLAIN, sp0, p->wphys, p->ld, p->bs)) != ETD_OK) return s;
-    if ((s = run_react<T>(p, p->reaction, p->wphys, p->ld, p->bs, p->t + p->tau, sp0)) != ETD_OK) return s;
-    cur = 0;
+    if (fuse) {
+        if ((s = run_chain<T>(p, cur, 0, EPI_REACT, sp0, nullptr, 0, 0)) != ETD_OK) return s;
+    } else {
+        if ((s = run_chain<T>(p, cur, 0, EPI_PLAIN, sp0, p->wphys, p->ld, p->bs)) != ETD_OK) return s;
+        if ((s = run_react<T>(p, p->reaction, p->wphys, p->ld, p->bs, p->t + p->tau, sp0)) != ETD_OK) return s;
+        cur = 0;
+    }
     if ((s = run_chain<T>(p, cur, 0, EPI_STAGE2, last ? spo : sp0, nullptr, 0, 0)) != ETD_OK) return s;
-    if ((s = run_chain<T>(p, cur, last ? p->out_slot : 0, EPI_PLAIN, sp0, u, n, N)) != ETD_OK) return s;
+    const bool chain = fuse && chain_rx;
+    if ((s = run_chain<T>(p, cur, last ? p->out_slot : 0, chain ? EPI_PLAIN_REACT : EPI_PLAIN, sp0, u, n, N)) !=
+        ETD_OK)
+        return s;
+    if (chain) {
+        p->rx_ready = true;
+        p->rx_cur = cur;
+        p->rx_src = u;
+    }
     p->t += p->tau;
     return ETD_OK;
 }
@@ -439,7 +469,7 @@ template <typename T>
 etd_status step_impl(etd_plan* p, void* u, int n_steps) {
     etd_status s = ensure_state<T>(p, u);
     for (int it = 0; it < n_steps && s == ETD_OK; ++it) {
-        s = step_once<T>(p, u, it == n_steps - 1);
+        s = step_once<T>(p, u, it == n_steps - 1, true);
         ++p->steps_done;
         if (s == ETD_OK && p->diag_every > 0 && p->steps_done % p->diag_every == 0) s = run_diag(p, u);
     }
@@ -450,8 +480,10 @@ etd_status group_ensure_state(etd_plan* g, void* u) {
     return g->elem == 8 ? ensure_state<double>(g, u) : ensure_state<float>(g, u);
 }
 
+// Ensemble groups do not chain f(U+) across steps (a captured inner step must
+// not depend on the step before it); f(W) is fused within each step.
 etd_status group_step_once(etd_plan* g, void* u, bool last) {
-    return g->elem == 8 ? step_once<double>(g, u, last) : step_once<float>(g, u, last);
+    return g->elem == 8 ? step_once<double>(g, u, last, false) : step_once<float>(g, u, last, false);
 }
 
 // d E_l / dx of the factor family at x >= 0 (for the kappa gradients).
@@ -495,6 +527,7 @@ void factor_grid_derivs(int family, double x, double* de) {
 // out = T(in) (layouts of the caller, rows of n); kind >= 0 transforms f(in).
 template <typename T>
 etd_status xform(etd_plan* p, int kind, const void* in, void* out) {
+    p->rx_ready = false;  // overwrites the operand buffers
     const int sp = split_for(p, p->out_slot);
     etd_status s = run_react<T>(p, kind, in, p->n, p->npts, p->t, sp);
     int cur = 0;
@@ -1257,6 +1290,7 @@ etd_status etd_sync(etd_plan* p) {
         if (flags[0] & ERR_DIVERGED) ETD_CUDA(cudaMemcpy(saved, p->stats + 4, sizeof saved, cudaMemcpyDeviceToHost));
         ETD_CUDA(cudaMemset(p->err, 0, sizeof(unsigned) * 2));
         p->uhat_valid = false;
+        p->rx_ready = false;
         if (flags[0] & ERR_TIMEOUT) return fail(ETD_ERR_TIMEOUT, "a device-side wait exceeded its time limit");
         if (flags[0] & ERR_DIVERGED)
             return fail(ETD_ERR_DIVERGED,
@@ -1315,6 +1349,7 @@ etd_status etd_transform(etd_plan* p, const void* in_dev, void* out_dev) {
     if (s != ETD_OK) return s;
     int cur = 0;
     const int sp = split_for(p, p->out_slot);
+    p->rx_ready = false;  // overwrites the operand buffers
     if (p->elem == 8) {
         if ((s = run_react<double>(p, -1, in_dev, p->n, p->npts, p->t, sp)) != ETD_OK) return s;
         s = run_chain<double>(p, cur, p->out_slot, EPI_PLAIN, sp, out_dev, p->n, p->npts);
@@ -1331,6 +1366,7 @@ etd_status etd_plan_invalidate(etd_plan* p) {
     p->last_ptrs.clear();
     p->uhat_valid = false;
     p->uhat_src = nullptr;
+    p->rx_ready = false;
     return ETD_OK;
 }
 

@@ -238,3 +238,28 @@ def test_bad_field_arguments():
         etd.etd_step(plan.handle, host.data_ptr(), 1)
     assert ei.value.status == etd.ETD_ERR_INVALID_ARG
     plan.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["bf16x6", "fp64"])
+@pytest.mark.parametrize("d,n", [(2, 96), (3, 40)])
+def test_fused_reaction_across_calls_and_interleaved_transforms(precision, d, n):
+    """Allen-Cahn is evaluated in the transform epilogues (f(W) in the pass that
+    makes W, f(U+) for the next step in the pass that returns U+, also across
+    calls on the same field). Calls that overwrite the plan's operand buffers
+    in between (etd_transform) must make the next step evaluate f(U) afresh:
+    3 + 2 + 3 steps with a transform between the calls equal 8 steps of the oracle."""
+    torch = need_gpu()
+    u0 = inputs.allen_cahn_2d(n, workload=13) if d == 2 else inputs.gaussian_bump(n, 3)
+    tau = 1e-3 if d == 2 else 5e-3
+    plan = etd.Plan(d, n, 0.01, 0.1, tau, precision=precision, reaction="allen_cahn")
+    u = torch.tensor(u0, dtype=plan.dtype, device="cuda")
+    other = torch.tensor(inputs.random_field(u0.shape, workload=14), dtype=plan.dtype, device="cuda")
+    plan.step(u, 3)
+    plan.step(u, 2)
+    plan.transform(other)
+    plan.step(u, 3)
+    plan.sync()
+    ref = oracle_ref(d, n, (0.01,), 0.1, tau, u0, 8, "allen_cahn")
+    assert rel_err(u.double().cpu().numpy(), ref) < tol(precision, n)
+    plan.close()
