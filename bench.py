@@ -60,6 +60,15 @@ WORKLOADS = {
 RUN_STEPS = {"fhn2d_4096": 1000, "fhn2d_2048": 1000, "fhn2d_4095": 1000, "ac3d_256": 200, "ac3d_384": 200,
              "ac3d_255": 200, "ac2d_64": 100, "ensemble512": 500, "adjoint3d_128": 400}
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
+F64_PRECISIONS = ("fp64", "fp64split")  # precisions with FP64 fields
+# the arithmetic each precision computes in
+DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32 (f32 fields)",
+         "tf32x3": "tf32x3 (f32 fields, double-float spectral state)",
+         "tf32x6": "tf32x6 (f32 fields, double-float spectral state)",
+         "bf16x3": "bf16x3 (f32 fields, double-float spectral state)",
+         "bf16x6": "bf16x6 (f32 fields, double-float spectral state)",
+         "fp64split": "f64 (f64 fields and state; products as 28 exact bf16 slice products)",
+         "dst32": "f32 (fast sine transforms)"}
 KERNEL_FILES = ["paper_2601_06849_gb300/csrc/gemm_tc.cu", "paper_2601_06849_gb300/csrc/etd_internal.cuh"]
 L2_BYTES = 129e6
 
@@ -79,7 +88,7 @@ def run_adjoint(args, world, rank, local):
     torch.cuda.set_device(local)
     d, n, ku, kv, q, tau, rx, desc = WORKLOADS[args.workload]
     window, every = 400, 20
-    fdt = torch.float64 if args.precision == "fp64" else torch.float32  # the plan's field type
+    fdt = torch.float64 if args.precision in F64_PRECISIONS else torch.float32  # the plan's field type
     u0 = torch.tensor(inputs.fhn_uniform(n, d, workload=4), dtype=fdt, device="cuda")
     target = u0.clone()
     tplan = etd.Plan(d, n, ku * (1 + 1e-2), q, tau, precision=args.precision, reaction="fhn", rx_params=FHN, n_comp=2,
@@ -126,7 +135,8 @@ def run_adjoint(args, world, rank, local):
     # transform flops of an iteration: forward (4d passes per step), the recomputed
     # forward and the adjoint's 9 transforms (d passes each) per step, 2 n^(d+1) per
     # pass and component, times the split products
-    products = {"fp64": 1, "fp32": 1, "tf32": 1, "tf32x3": 3, "bf16x3": 3, "bf16x6": 6, "tf32x6": 6}.get(
+    products = {"fp64": 1, "fp32": 1, "tf32": 1, "tf32x3": 3, "bf16x3": 3, "bf16x6": 6, "tf32x6": 6,
+                "fp64split": 28}.get(
         args.precision, 1)
     passes = window * (4 * d + 4 * d + 9 * d)
     flops = passes * 2.0 * n ** (d + 1) * 2 * products * iters
@@ -138,7 +148,7 @@ def run_adjoint(args, world, rank, local):
         "unit": "unknown-updates/s", "n_gpus": world, "steps": iters, "warmup": args.warmup,
         "ms_per_step": el_max / iters / window * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": ("fp64" if args.precision == "fp64" else f"{args.precision} (f32 fields, double-float spectral state)"),
+        "dtype": DTYPE.get(args.precision, args.precision),
         "data": "synthetic",
         "config": {"workload": desc, "d": d, "n": n, "window": window, "checkpoint_every": every,
                    "precision": args.precision, "step": "one forward + backward solve over the window",
@@ -366,7 +376,7 @@ def run_accuracy(args, world, rank, local):
             batch = etd.Batch(2, [m.n for m in members], [m.kappa_u for m in members], [q] * len(members),
                               [m.tau for m in members], precision=prec, reaction="fhn", rx_params=FHN, n_comp=2,
                               kappa_v=kv)
-            ref = ref64 if prec == "fp64" else ref32
+            ref = ref64 if prec in F64_PRECISIONS else ref32
             fields = [torch.tensor(m.u0, dtype=batch.dtype, device="cuda") for m in members]
             prev, per = 0, []
             for j, k in enumerate(marks):
@@ -409,7 +419,7 @@ def run_accuracy(args, world, rank, local):
     errors = {}
     for prec in precisions:
         plan = make_plan(name, prec)
-        ref = ref64 if prec == "fp64" else ref32
+        ref = ref64 if prec in F64_PRECISIONS else ref32
         x = torch.tensor(u0, dtype=plan.dtype, device="cuda")
         prev, per = 0, []
         t0 = time.perf_counter()
@@ -458,7 +468,7 @@ def tensor_peak(peaks, src, precision, timed_s):
     the sustained rate for longer ones; TF32 products at the nominal TF32/BF16
     ratio of it."""
     key = "bf16_tflops" if timed_s < 2.0 else "bf16_tflops_sustained"
-    bf16_mode = precision.startswith("bf16")
+    bf16_mode = precision.startswith("bf16") or precision == "fp64split"  # the slices are BF16
     peak = peaks[key] * (1.0 if bf16_mode else TF32_OVER_BF16)
     return peak, f"{src}: {key}" + ("" if bf16_mode else " x 1.1/2.25 (TF32/BF16 nominal)")
 
@@ -800,10 +810,7 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"tf32x3": "tf32x3 (f32 fields, double-float spectral state)", "tf32": "tf32 (f32 fields)", "fp32": "f32",
-                  "fp64": "f64", "bf16x3": "bf16x3 (f32 fields, double-float spectral state)",
-                  "bf16x6": "bf16x6 (f32 fields, double-float spectral state)",
-                  "tf32x6": "tf32x6 (f32 fields, double-float spectral state)"}.get(args.precision, args.precision),
+        "dtype": DTYPE.get(args.precision, args.precision),
         "data": "synthetic",
         "config": {"workload": desc, "d": d, "n": n, "n_comp": info.n_comp, "precision": args.precision,
                    "pass_kernel": {"persistent": list(info.pass_persistent), "tile_n": list(info.pass_tile_n),
@@ -812,9 +819,10 @@ def main():
                    "l2": f"working set {info.workspace_bytes / 1e9:.2f} GB > 129 MB L2: inputs larger than L2, no flush",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
-        # every pass and reaction launch of the timed steps, as counted by the plan's
-        # per-launch timing events (reactions fused into the pass epilogues add none)
-        "gpu_launches": gemm_n + rx_n + acc_n,
+        # every kernel launch of the timed steps: the passes and reaction kernels the
+        # plan's per-launch timing events counted (reactions fused into the pass
+        # epilogues add none), times the kernels one pass launches
+        "gpu_launches": (gemm_n + acc_n) * info.kernels_per_pass + rx_n,
         "kernel_ms": {"transform_passes": gemm_ms, "transform_launches": gemm_n, "reaction_ms": rx_ms,
                       "reaction_launches": rx_n, "accurate_transform_ms": acc_ms, "accurate_transform_launches": acc_n},
         "e2e": {"value": world * unknowns * e2e_steps / e2e_s, "unit": "unknown-updates/s",

@@ -15,7 +15,8 @@
  * Conventions shared by every call:
  *   - Field layout: [comp][z][y][x], x fastest, contiguous, no boundary values
  *     (the Dirichlet zeros are implicit; Section 2.1 vectorisation order).
- *     Element type: double for ETD_PREC_FP64, float for every other precision.
+ *     Element type: double for ETD_PREC_FP64 and ETD_PREC_FP64_SPLIT, float for every
+ *     other precision.
  *   - Device pointers must be 16-byte aligned device memory of at least
  *     n_comp * n^d elements; host pointers any host memory of that size.
  *   - The caller owns every field pointer. The plan owns P, the grids, all
@@ -57,10 +58,14 @@ enum {
                             correction products in their own accumulator (default; the most
                             accurate tensor-core mode) */
     ETD_PREC_TF32X6 = 6, /* float fields, TF32 hi/mid/lo split, six products, as BF16X6 */
-    ETD_PREC_DST32 = 7   /* float fields, every transform as fast sine transforms (FFT-based DST-I
+    ETD_PREC_DST32 = 7,  /* float fields, every transform as fast sine transforms (FFT-based DST-I
                             in FP32 on CUDA cores) instead of the dense product with P: a
                             comparison path, not the paper's dense-eigenbasis method; needs
                             m + 1 a power of two, 16 <= m + 1 <= 8192 */
+    ETD_PREC_FP64_SPLIT = 8 /* double fields and state; every product with P in FP64 accuracy on the
+                            BF16 tensor cores: each operand row cut into seven 7-bit integer slices below
+                            a power-of-two scale (P likewise), the 28 slice products of weight >= 2^-42
+                            accumulated exactly, the result formed in FP64 */
 };
 /* In every split mode (X3, X6) the two transforms whose error stays in the
  * result, U -> U^ when the carried spectral state is (re)built and the
@@ -133,7 +138,8 @@ typedef struct {
 /* Performance-relevant facts of a plan (for benchmarks and roofline figures). */
 typedef struct {
     int d, n, n_comp, precision;
-    int products;                /* tensor-core products per MMA tile (1, 3 or 6; 0 for CUDA cores) */
+    int products;                /* tensor-core products per MMA tile (1, 3, 6, or 28 slice products for
+                                    ETD_PREC_FP64_SPLIT; 0 for CUDA cores) */
     int gemms_per_step;          /* transform passes per time step (8 in 2D, 12 in 3D) */
     long long unknowns;          /* n_comp * n^d */
     double gemm_flops;           /* algorithmic flops of one pass, all components: 2 n^(d+1) n_comp */
@@ -146,6 +152,8 @@ typedef struct {
     double step_bytes;           /* algorithmic DRAM bytes of one time step's transform passes: every operand
                                     piece, basis piece, spectral state value and output field value read or
                                     written once per pass (reaction kernels not included) */
+    int kernels_per_pass;        /* kernel launches of one transform pass: 1, or 2 (ETD_PREC_DST32: row FFTs
+                                    and the transposing epilogue; ETD_PREC_FP64_SPLIT: slices, products) */
 } etd_plan_info;
 
 /* Fill *opt with the defaults listed above. */

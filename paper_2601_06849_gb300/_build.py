@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libetd.so")
-SOURCES = ["etd_plan.cu", "gemm_simt.cu", "gemm_tc.cu", "pointwise.cu", "noalloc.cu", "adjoint.cu", "dst.cu"]
-HEADERS = ["etd_internal.cuh"]
+SOURCES = ["etd_plan.cu", "gemm_simt.cu", "gemm_tc.cu", "ozaki.cu", "pointwise.cu", "noalloc.cu", "adjoint.cu", "dst.cu"]
+HEADERS = ["etd_internal.cuh", "tc_ptx.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -649,6 +649,24 @@ void tc_maps_destroy(TcMaps* m);
 cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, int a_index, int M, int n, int nbatch,
                            const Epi<float>& e, unsigned* err, cudaStream_t st);
 const char* tc_last_driver_error();
+
+// ETD_PREC_FP64_SPLIT transform pass (ozaki.cu): FP64 operands cut into OZ_S
+// BF16 slices of 7 bits below a per-row power-of-two scale, exact slice
+// products on the tensor cores, FP64 result through the Epi<double> epilogue.
+constexpr int OZ_S = 7;
+constexpr int OZ_PAIRS = OZ_S * (OZ_S + 1) / 2;  // slice products per MMA tile and k-step
+struct OzMaps;  // opaque holder of the slice planes' tensor maps (ozaki.cu)
+cudaError_t oz_maps_create(OzMaps** out, int M, int n, int nbatch, int ld, void* const slices[OZ_S],
+                           void* const pslices[OZ_S]);
+void oz_maps_destroy(OzMaps* m);
+// P's slices on the host (n x n, written into planes of pitch ld); returns P's
+// scale exponent e_P (max |P| < 2^e_P)
+int oz_slice_host(const double* P, int n, int ld, uint16_t* const planes[OZ_S]);
+// The pass: A's row scales into rexp (nbatch * M ints) and its slices into
+// `slices`, then the products and the epilogue.
+cudaError_t launch_ozaki_pass(const OzMaps* maps, int p_exp, const double* A, int M, int n, int nbatch, int ld,
+                              void* const slices[OZ_S], int* rexp, const Epi<double>& e, unsigned* err,
+                              cudaStream_t st);
 cudaError_t launch_wait_timeout_probe(unsigned* err, double limit_ms, cudaStream_t st);
 
 }  // namespace etd

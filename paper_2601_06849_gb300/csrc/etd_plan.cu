@@ -62,6 +62,12 @@ struct etd_plan {
     bool dst = false;         // ETD_PREC_DST32: FFT-based sine transforms instead of products with P
     float2* dst_tw = nullptr; // its FFT twiddles by stage (N - 1 of them, N = 2(n+1))
     void* dst_tmp = nullptr;  // its natural-order scratch rows
+    bool ozaki = false;       // ETD_PREC_FP64_SPLIT: FP64 products as exact BF16 slice products
+    void* oz_slices[OZ_S] = {nullptr};  // the operand's BF16 slices (one set, refilled before every pass)
+    void* oz_P[OZ_S] = {nullptr};       // P's slices
+    int* oz_rexp = nullptr;             // per operand row: the slices' scale exponent
+    OzMaps* oz_maps = nullptr;
+    int oz_pexp = 0;                    // P's scale exponent
     bool bf16 = false;  // BF16 operand pieces (ETD_PREC_BF16X3 / X6)
     size_t op_elem = 4; // bytes per operand-plane value
     int pieces = 1;     // operand planes allocated per buffer
@@ -231,6 +237,12 @@ void free_plan(etd_plan* p) {
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->maps) tc_maps_destroy(p->maps);
+    for (int i = 0; i < OZ_S; ++i) {
+        if (p->oz_slices[i]) cudaFree(p->oz_slices[i]);
+        if (p->oz_P[i]) cudaFree(p->oz_P[i]);
+    }
+    if (p->oz_rexp) cudaFree(p->oz_rexp);
+    if (p->oz_maps) oz_maps_destroy(p->oz_maps);
     for (auto& tl : p->timed) {
         cudaEventDestroy(tl.a);
         cudaEventDestroy(tl.b);
@@ -310,6 +322,13 @@ etd_status run_pass(etd_plan* p, int cur, int slot, int mode, int out_split, voi
     e.rx_c = (T)p->rp[0];
     TimerScope ts(p, slot == p->out_slot && p->out_slot != 0 ? 2 : 0);
     if constexpr (sizeof(T) == 8) {
+        if (p->ozaki) {
+            cudaError_t ce = launch_ozaki_pass(p->oz_maps, p->oz_pexp, (const double*)p->op[cur][0], p->M, p->n,
+                                               p->ninst * p->ncomp, p->ld, p->oz_slices, p->oz_rexp, e, p->err,
+                                               p->stream);
+            if (ce != cudaSuccess) return fail(ETD_ERR_CUDA, "FP64-split pass launch: %s", cudaGetErrorString(ce));
+            return ETD_OK;
+        }
         launch_gemm_simt_f64((const double*)p->op[cur][0], (const double*)p->P[0], p->M, p->n, p->ninst * p->ncomp,
                              e, p->stream);
     } else {
@@ -718,7 +737,7 @@ etd_status validate_options(int d, int m, int pade_order, const etd_options& opt
         if (N < 16 || N > 8192 || (N & (N - 1)))
             return fail(ETD_ERR_UNSUPPORTED, "ETD_PREC_DST32 needs m + 1 a power of two in [16, 8192] (m = %d)", m);
     }
-    if (opt.precision < ETD_PREC_FP64 || opt.precision > ETD_PREC_DST32)
+    if (opt.precision < ETD_PREC_FP64 || opt.precision > ETD_PREC_FP64_SPLIT)
         return fail(ETD_ERR_INVALID_ARG, "unknown precision");
     return ETD_OK;
 }
@@ -833,7 +852,8 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     p->stream = (cudaStream_t)opt.stream;
     p->diag_every = opt.diag_every;
     p->diag_max = opt.diag_max_abs;
-    p->elem = (opt.precision == ETD_PREC_FP64) ? 8 : 4;
+    p->elem = (opt.precision == ETD_PREC_FP64 || opt.precision == ETD_PREC_FP64_SPLIT) ? 8 : 4;
+    p->ozaki = opt.precision == ETD_PREC_FP64_SPLIT;
     p->bf16 = (opt.precision == ETD_PREC_BF16X3 || opt.precision == ETD_PREC_BF16X6);
     p->use_tc = p->bf16 || opt.precision == ETD_PREC_TF32 || opt.precision == ETD_PREC_TF32X3 ||
                 opt.precision == ETD_PREC_TF32X6;
@@ -902,7 +922,13 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     const size_t pbytes = (size_t)n * p->ld * p->op_elem;
     const size_t op_bytes = (size_t)nb * p->bs * p->op_elem;
     // the sine-transform path needs no P: its twiddles and a scratch field instead
-    for (int j = 0; j < (p->dst ? 0 : p->pieces) && s == ETD_OK; ++j) s = dalloc(p, &p->P[j], pbytes);
+    for (int j = 0; j < (p->dst || p->ozaki ? 0 : p->pieces) && s == ETD_OK; ++j) s = dalloc(p, &p->P[j], pbytes);
+    // FP64-split: the operand's slice planes, P's slice planes, the scale words
+    for (int i = 0; i < (p->ozaki ? OZ_S : 0) && s == ETD_OK; ++i) {
+        s = dalloc(p, &p->oz_slices[i], (size_t)nb * p->bs * 2);
+        if (s == ETD_OK) s = dalloc(p, &p->oz_P[i], (size_t)n * p->ld * 2);
+    }
+    if (s == ETD_OK && p->ozaki) s = dalloc(p, (void**)&p->oz_rexp, sizeof(int) * (size_t)nb * p->M);
     if (s == ETD_OK && p->dst) s = dalloc(p, (void**)&p->dst_tw, sizeof(float2) * (size_t)(2 * (n + 1) - 1));
     if (s == ETD_OK && p->dst) s = dalloc(p, &p->dst_tmp, field_bytes);
     if (s == ETD_OK) s = dalloc(p, &p->grid, (size_t)nb * 3 * n * sizeof(double));
@@ -932,7 +958,17 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
             }
         ce = cudaMemcpy(p->dst_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
     }
-    for (int j = 0; j < (p->dst ? 0 : p->pieces) && ce == cudaSuccess; ++j) {
+    if (p->ozaki && ce == cudaSuccess) {
+        std::vector<uint16_t> planes((size_t)OZ_S * n * p->ld, 0);
+        uint16_t* ptrs[OZ_S];
+        for (int i = 0; i < OZ_S; ++i) ptrs[i] = planes.data() + (size_t)i * n * p->ld;
+        p->oz_pexp = oz_slice_host(P.data(), n, p->ld, ptrs);
+        for (int i = 0; i < OZ_S && ce == cudaSuccess; ++i)
+            ce = cudaMemcpy(p->oz_P[i], ptrs[i], (size_t)n * p->ld * 2, cudaMemcpyHostToDevice);
+        for (int i = 0; i < OZ_S && ce == cudaSuccess; ++i) ce = cudaMemset(p->oz_slices[i], 0, (size_t)nb * p->bs * 2);
+        if (ce == cudaSuccess) ce = oz_maps_create(&p->oz_maps, p->M, n, nb, p->ld, p->oz_slices, p->oz_P);
+    }
+    for (int j = 0; j < (p->dst || p->ozaki ? 0 : p->pieces) && ce == cudaSuccess; ++j) {
         std::vector<char> hostbuf(pbytes, 0);
         for (int r = 0; r < n; ++r)
             for (int k = 0; k < n; ++k) {
@@ -1046,7 +1082,7 @@ etd_status etd_batch_create(etd_plan** out, int count, const int* d, const int* 
     B->count = count;
     B->ncomp = opt.n_comp;
     B->precision = opt.precision;
-    B->elem = (opt.precision == ETD_PREC_FP64) ? 8 : 4;
+    B->elem = (opt.precision == ETD_PREC_FP64 || opt.precision == ETD_PREC_FP64_SPLIT) ? 8 : 4;
     B->stream = (cudaStream_t)opt.stream;
     // group the instances by grid (d, n), in order of first appearance
     std::vector<std::pair<int, int>> keys;
@@ -1425,7 +1461,8 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
     info->n = p->n;
     info->n_comp = p->ncomp;
     info->precision = p->precision;
-    info->products = p->use_tc ? p->tc[0].products : 0;
+    info->products = p->use_tc ? p->tc[0].products : (p->ozaki ? OZ_PAIRS : 0);
+    info->kernels_per_pass = (p->ozaki || p->dst) ? 2 : 1;
     info->gemms_per_step = 4 * p->d;
     info->unknowns = (long long)p->ninst * p->ncomp * p->npts;
     info->gemm_flops = 2.0 * (double)p->npts * (double)p->n * p->ncomp * p->ninst;
@@ -1442,9 +1479,16 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
     const double vals = (double)p->ninst * p->ncomp * p->npts;
     const double pin = p->use_tc ? p->tc[0].pieces : 1;
     const double opb = vals * (double)p->op_elem;
-    const double basis = p->dst ? 0.0 : (double)p->n * p->n * (double)p->op_elem * pin;  // DST32 reads no P
+    double basis = p->dst ? 0.0 : (double)p->n * p->n * (double)p->op_elem * pin;  // DST32 reads no P
+    double slicing = 0.0;
+    if (p->ozaki) {
+        // FP64-split: P's slices, and per pass the operand read once more (the
+        // row's max before its slices), its slices written and read (2 bytes each)
+        basis = (double)p->n * p->n * 2.0 * OZ_S;
+        slicing = vals * (8.0 + 2.0 * 2.0 * OZ_S);
+    }
     const double st = 8.0, fe = (double)p->elem;
-    const double pass_in = pin * opb + basis;
+    const double pass_in = pin * opb + basis + slicing;
     const double split_out = pin * opb;
     const double chains = 4.0;
     info->step_bytes = chains * p->d * pass_in + chains * (p->d - 1) * split_out +

@@ -1,0 +1,450 @@
+// FP64-split transform pass (ETD_PREC_FP64_SPLIT): the dense product with P of
+// Section 3.3.2 in FP64 accuracy on the BF16 tensor cores, by error-free
+// splitting into integer slices (the splitting scheme of Ozaki et al. for
+// accurate matrix products on low-precision units).
+//
+//     out(b, mm, nn) = sum_k A[b][mm][k] P[nn][k]          (FP64 fields, FP64 result)
+//
+// Slices. Every operand value x of row r (the n values one output row contracts)
+// is written as a fixed-point number below the power of two 2^e_r > max |x| over the row:
+//     x ~ 2^(e_r - 49) t,   t = round(x 2^(49 - e_r)),  |t| <= 2^49,
+// and t is cut into OZ_S = 7 slices of 7 bits, most significant first,
+//     t = sum_i a_i 2^(7 (6 - i)),   |a_0| <= 128, |a_i| <= 127, all with the sign of x.
+// P is cut the same way below its own scale 2^e_P > max |P| (about sqrt(2/(n+1)):
+// a fixed scale of 1 would leave its top slices nearly empty), once per plan on
+// the host. Every
+// slice is an integer of at most 8 significant bits, exact in BF16, and every
+// slice product is an integer of magnitude below 2^14.
+//
+// Products. The product of slices a_i and p_j carries the weight 2^(-7 (i + j));
+// all pairs (i, j) of one level l = i + j <= 6 (28 pairs) accumulate in one
+// TMEM accumulator per k-block of 32 values: at most 7 pairs x 32 products x
+// 2^14 < 2^22 in magnitude, so the FP32 accumulation of these integers is exact
+// whatever the order of the additions inside the tensor core. The k-block sums
+// S_l are added in int32 registers (exact up to K = 16384), and at the end
+//     out = 2^(e_r + e_P - 28) (G_0 + G_1 2^-21 + G_2 2^-42),
+//     G_g = S_3g 2^14 + S_3g+1 2^7 + S_3g+2       (int64, exact; missing levels 0)
+// is formed in FP64 (two roundings). What is left out: the rounding of each
+// operand to 49 bits below its row's scale (2^-50 relative to the row's max) and
+// the pairs with i + j >= 7 (each below 2^-49 of the scales' product per term): a
+// few 2^-47 relative to the row's max |out| for sums of random signs. The scale
+// is per row, not per component: the spectral coefficients of a field dominated
+// by a constant (FitzHugh-Nagumo's v, driven by eps b) are large in a few modes,
+// and the back-transform recovers the field through heavy cancellation; with one
+// scale per component that lost 40x more (CPU emulation of this arithmetic, n =
+// 512: 7.3e-11 against 1.9e-12). Six slices were short of 1e-10 on the same
+// structure, hence seven.
+//
+// Per pass: a slicing kernel (one warp per operand row: the row's scale, then its
+// seven BF16 slice planes in the layout of the FP64 operand buffer) and the
+// product kernel, one 128 x 32 tile per CTA:
+//   warps 0-7  drain: per k-block, tcgen05.ld of the seven level accumulators of
+//              their TMEM lane quarter and 16-column half, integer sums; at the
+//              end the FP64 result and the fused epilogue (Epi<double>, the
+//              Hadamard stages and outputs of the FP64 path);
+//   warp 8     TMA producer (one lane) and TMEM allocator;
+//   warp 9     MMA issuer (one lane): 56 tcgen05.mma.kind::f16 per k-block.
+// Shared memory holds three pipeline stages of 32 K-values (64-byte rows,
+// 64-byte swizzle) of the seven A slices and the seven P slices (70 KB per stage).
+// TMEM holds two k-block buffers of seven 32-column level accumulators.
+// Every wait is bounded (tc_ptx.cuh); on expiry the CTA raises ERR_TIMEOUT and
+// returns after its copies and products have completed (bounded as well).
+#include <cuda.h>
+#include <stdio.h>
+
+#include "etd_internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace etd {
+
+struct OzMaps {
+    CUtensorMap a[OZ_S];  // the operand's slice planes (box 32 values x 128 rows)
+    CUtensorMap p[OZ_S];  // P's slice planes (box 32 values x 32 rows)
+};
+
+namespace {
+
+constexpr int OZ_BM = 128;
+constexpr int OZ_BN = 32;
+constexpr int OZ_KV = 32;   // BF16 values of K per pipeline stage (one k-block)
+constexpr int OZ_ROW = 64;  // bytes of K per operand row in a stage
+constexpr int OZ_A_BYTES = OZ_BM * OZ_ROW;
+constexpr int OZ_B_BYTES = OZ_BN * OZ_ROW;
+constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_BYTES + OZ_B_BYTES);
+constexpr int OZ_STAGES = 3;
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024;  // + alignment slack
+constexpr int OZ_DRAIN_WARPS = 8;
+constexpr int OZ_WARP_TMA = 8;
+constexpr int OZ_WARP_MMA = 9;
+constexpr int OZ_THREADS = 320;
+constexpr uint32_t OZ_TMEM_COLS = 512;  // 2 buffers x 7 levels x 32 columns = 448, allocated as 512
+constexpr int OZ_BITS = 7;
+constexpr int OZ_FRAC = OZ_S * OZ_BITS;  // 49 bits below the scale
+static_assert(2 * OZ_S * OZ_BN <= (int)OZ_TMEM_COLS, "level accumulators exceed the TMEM allocation");
+static_assert(OZ_SMEM <= 227 * 1024, "pipeline stages exceed the shared memory of a CTA");
+
+struct OzPlanes {
+    __nv_bfloat16* s[OZ_S];
+};
+
+struct OzParams {
+    int M, n, nbatch, tiles_m, tiles_n;
+    int p_exp;                       // P's scale exponent e_P
+    const int* rexp;                 // per row of the stacked entries: its scale exponent or code
+    unsigned* err;
+    Epi<double> e;
+};
+
+// 2^k as a double, for -1022 <= k <= 1023 (built from its bits: exact, no libm).
+__device__ __forceinline__ double pow2(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+
+// Row exponent codes besides a finite scale exponent (|e| < 1100).
+constexpr int OZ_EXP_ZERO = -4096;       // row of zeros: zero slices, zero result
+constexpr int OZ_EXP_NONFINITE = 4096;   // row with NaN or Inf: NaN result
+
+}  // namespace
+
+namespace {
+
+// The seven BF16 slice planes of A and each row's scale exponent, one warp per
+// row of the stacked batch entries (row r at r * ld; only its n values are
+// written, TMA reads zeros beyond): the warp reduces max |x| over the row, then
+// cuts every value below 2^e_r > max |x| (the row is read again from L1/L2).
+// rexp[r] = e_r; OZ_EXP_ZERO for a row of zeros (or below 1e-250: its slices
+// are zero), OZ_EXP_NONFINITE for a row with NaN or Inf (its first slice
+// carries them, so the products and the result of the row are NaN).
+__global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ A, long long rows, int n, int ld,
+                                                      int* __restrict__ rexp, OzPlanes out) {
+    const int lane = threadIdx.x & 31;
+    const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += wstride) {
+        const double* row = A + r * ld;
+        double m = 0.0;
+        bool bad = false;
+        for (int k = lane; k < n; k += 32) {
+            const double v = fabs(row[k]);
+            if (v <= 1.7976931348623157e308)
+                m = fmax(m, v);
+            else
+                bad = true;
+        }
+        for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+        bad = __any_sync(0xffffffffu, bad);
+        int e = 0;
+        int code;
+        if (bad) {
+            code = OZ_EXP_NONFINITE;
+        } else if (m < 1e-250) {
+            code = OZ_EXP_ZERO;
+        } else {
+            frexp(m, &e);
+            code = e;
+        }
+        if (lane == 0) rexp[r] = code;
+        const double scale = pow2(OZ_FRAC - e);  // x * scale = t, |t| <= 2^49
+        const long long o0 = r * ld;
+        for (int k = lane; k < n; k += 32) {
+            const double x = row[k];
+            float a[OZ_S];
+#pragma unroll
+            for (int i = 0; i < OZ_S; ++i) a[i] = 0.f;
+            if (code == OZ_EXP_NONFINITE) {
+                if (!(fabs(x) <= 1.7976931348623157e308)) a[0] = (float)x;  // NaN / Inf into the products
+            } else if (code != OZ_EXP_ZERO) {
+                const long long t = __double2ll_rn(x * scale);  // exact power-of-two scaling, one rounding
+                const unsigned long long u = (unsigned long long)(t < 0 ? -t : t);
+                const float sg = t < 0 ? -1.f : 1.f;
+#pragma unroll
+                for (int i = 0; i < OZ_S; ++i) {
+                    const unsigned long long d = u >> (OZ_BITS * (OZ_S - 1 - i));
+                    a[i] = sg * (float)(i == 0 ? d : (d & ((1ull << OZ_BITS) - 1)));
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < OZ_S; ++i) out.s[i][o0 + k] = __float2bfloat16_rn(a[i]);  // exact: |a_i| <= 128
+        }
+    }
+}
+
+}  // namespace
+
+namespace {
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_constant__ OzMaps maps, const OzParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ int s_skip;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    __shared__ int s_consumed;
+    __shared__ int s_issued;
+    // full[3], empty[3] (shared-memory ring), acc_full[2], acc_empty[2] (TMEM ring), done
+    __shared__ __align__(8) uint64_t s_bar[2 * OZ_STAGES + 5];
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) s_skip = (*(volatile unsigned*)p.err != 0u);
+    __syncthreads();
+    if (s_skip) return;
+
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    volatile int* abort_flag = &s_abort;
+    const uint32_t bar_full = smem_u32(&s_bar[0]);
+    const uint32_t bar_empty = smem_u32(&s_bar[OZ_STAGES]);
+    const uint32_t bar_acc_full = smem_u32(&s_bar[2 * OZ_STAGES]);
+    const uint32_t bar_acc_empty = smem_u32(&s_bar[2 * OZ_STAGES + 2]);
+    const uint32_t bar_done = smem_u32(&s_bar[2 * OZ_STAGES + 4]);
+
+    int tm, tn;
+    tile_coords(blockIdx.x, p.tiles_m, p.tiles_n, 8, tm, tn);
+    const int nk = (p.n + OZ_KV - 1) / OZ_KV;  // k-blocks (one pipeline stage each)
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < OZ_STAGES; ++s) {
+            mbar_init(bar_full + 8 * s, 1);
+            mbar_init(bar_empty + 8 * s, 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(bar_acc_full + 8 * a, 1);
+            mbar_init(bar_acc_empty + 8 * a, OZ_DRAIN_WARPS);
+        }
+        mbar_init(bar_done, 1);
+        s_abort = 0;
+        s_consumed = 0;
+        s_issued = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == OZ_WARP_TMA) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(OZ_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s_tmem;
+
+    if (warp == OZ_WARP_TMA && lane == 0) {
+        // ---------------- TMA producer: the six A and six P slices of each k-block ----------------
+        const int arow = tm * OZ_BM, prow = tn * OZ_BN;
+        int issued = 0;
+        for (int q = 0; q < nk; ++q) {
+            const int s = q % OZ_STAGES;
+            if (!mbar_wait(bar_empty + 8 * s, (uint32_t)(((q / OZ_STAGES) & 1) ^ 1), abort_flag, p.err)) break;
+            const uint32_t st = smem_u32(smem + (size_t)s * OZ_STAGE_BYTES);
+            const uint32_t fb = bar_full + 8 * s;
+            mbar_expect_tx(fb, (uint32_t)OZ_STAGE_BYTES);
+            const int k0 = q * OZ_KV;
+#pragma unroll
+            for (int i = 0; i < OZ_S; ++i) tma_load_2d(st + (uint32_t)(i * OZ_A_BYTES), &maps.a[i], fb, k0, arow);
+#pragma unroll
+            for (int j = 0; j < OZ_S; ++j)
+                tma_load_2d(st + (uint32_t)(OZ_S * OZ_A_BYTES + j * OZ_B_BYTES), &maps.p[j], fb, k0, prow);
+            issued = q + 1;
+        }
+        s_issued = issued;
+    } else if (warp == OZ_WARP_MMA && lane == 0) {
+        // ---------------- MMA issuer: the 28 slice pairs of levels 0-6 ----------------
+        const uint32_t idesc = idesc_bf16(OZ_BM, OZ_BN);
+        const uint64_t desc0 = sdesc_kmajor(smem_u32(smem), OZ_ROW);
+        for (int q = 0; q < nk; ++q) {
+            const int s = q % OZ_STAGES, a = q & 1;
+            if (!mbar_wait(bar_full + 8 * s, (uint32_t)((q / OZ_STAGES) & 1), abort_flag, p.err)) break;
+            if (q >= 2 && !mbar_wait(bar_acc_empty + 8 * a, (uint32_t)(((q >> 1) - 1) & 1), abort_flag, p.err)) break;
+            tc_fence_after();
+            const uint64_t dA = desc0 + (uint64_t)(s * (OZ_STAGE_BYTES >> 4));
+            const uint64_t dB = dA + (uint64_t)(OZ_S * (OZ_A_BYTES >> 4));
+            const uint32_t d = tmem + (uint32_t)(a * OZ_S * OZ_BN);
+#pragma unroll
+            for (int i = 0; i < OZ_S; ++i) {
+#pragma unroll
+                for (int j = 0; j < OZ_S - i; ++j) {
+#pragma unroll
+                    for (int kk = 0; kk < OZ_ROW / 32; ++kk) {  // 16 BF16 values (32 bytes) of K per MMA
+                        // the level's first product of the k-block overwrites its accumulator
+                        mma_bf16(d + (uint32_t)((i + j) * OZ_BN), dA + (uint64_t)(i * (OZ_A_BYTES >> 4) + 2 * kk),
+                                 dB + (uint64_t)(j * (OZ_B_BYTES >> 4) + 2 * kk), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                    }
+                }
+            }
+            mma_commit(bar_empty + 8 * s);     // the stage may be refilled once these products finish
+            mma_commit(bar_acc_full + 8 * a);  // the k-block's level sums are ready
+            s_consumed = q + 1;
+        }
+        mma_commit(bar_done);
+    } else if (warp < OZ_DRAIN_WARPS) {
+        // ---------------- drain: exact integer level sums, then the FP64 epilogue ----------------
+        const int quarter = warp & 3, half = warp >> 2;  // TMEM lanes 32 quarter.., columns 16 half..
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 16);
+        int acc[OZ_S][16];
+#pragma unroll
+        for (int l = 0; l < OZ_S; ++l)
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[l][c] = 0;
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int a = kb & 1;
+            if (!mbar_wait(bar_acc_full + 8 * a, (uint32_t)((kb >> 1) & 1), abort_flag, p.err)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int l = 0; l < OZ_S; ++l) {
+                uint32_t r[16];
+                tmem_ld16(lane_base + (uint32_t)((a * OZ_S + l) * OZ_BN), r);
+                tmem_wait16(r);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) acc[l][c] += __float2int_rn(__uint_as_float(r[c]));  // exact integers
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_acc_empty + 8 * a);
+        }
+        const int grow = tm * OZ_BM + quarter * 32 + lane;  // row of the stacked batch entries
+        if (ok && !*abort_flag && grow < p.nbatch * p.M) {
+            const int b = grow / p.M, mm = grow - b * p.M;
+            const int mh = mm / p.n, ml = mm - mh * p.n;
+            const int code = p.rexp[grow];
+            const bool nan_out = code == OZ_EXP_NONFINITE;
+            const double scale = pow2((code == OZ_EXP_ZERO || nan_out ? 0 : code) + p.p_exp - 28);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const int nn = tn * OZ_BN + half * 16 + c;
+                if (nn >= p.n) continue;
+                long long G[(OZ_S + 2) / 3];  // three levels per group (7 bits apart), exact in int64
+#pragma unroll
+                for (int g = 0; g < (OZ_S + 2) / 3; ++g) {
+                    G[g] = 0;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        if (3 * g + j < OZ_S) G[g] += (long long)acc[3 * g + j][c] << (OZ_BITS * (2 - j));
+                }
+                double v = (double)G[(OZ_S + 2) / 3 - 1];
+#pragma unroll
+                for (int g = (OZ_S + 2) / 3 - 2; g >= 0; --g) v = fma(v, 0x1p-21, (double)G[g]);
+                v *= scale;
+                if (nan_out) v = __longlong_as_double(0x7ff8000000000000ll);
+                p.e.apply(b, mh, ml, nn, v);
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == OZ_WARP_TMA && lane == 0) {
+        if (*abort_flag) {
+            // copies still in flight after an abort: wait for them (bounded) before exit
+            for (int q = s_consumed; q < s_issued; ++q) {
+                const int s = q % OZ_STAGES;
+                const unsigned long long t0 = globaltimer();
+                while (!mbar_try(bar_full + 8 * s, (uint32_t)((q / OZ_STAGES) & 1)) &&
+                       globaltimer() - t0 < 100000000ull) {
+                }
+            }
+        }
+        const unsigned long long t0 = globaltimer();  // every product has completed
+        while (!mbar_try(bar_done, 0u) && globaltimer() - t0 < 200000000ull) {
+        }
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (warp == OZ_WARP_TMA) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// One 2D tensor map of a BF16 slice plane: inner dimension n (values), `rows`
+// rows of pitch ld values, box of 32 values (64 bytes, 64-byte swizzle) x box_rows.
+bool oz_map(CUtensorMap* map, const void* base, int n, long long rows, int ld, int box_rows) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)OZ_KV, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t oz_maps_create(OzMaps** out, int M, int n, int nbatch, int ld, void* const slices[OZ_S],
+                           void* const pslices[OZ_S]) {
+    *out = nullptr;
+    OzMaps* m = new OzMaps();
+    bool ok = true;
+    for (int i = 0; i < OZ_S && ok; ++i) {
+        ok = oz_map(&m->a[i], slices[i], n, (long long)nbatch * M, ld, OZ_BM);
+        ok = ok && oz_map(&m->p[i], pslices[i], n, n, ld, OZ_BN);
+    }
+    if (!ok) {
+        delete m;
+        return cudaErrorInvalidValue;
+    }
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute((const void*)ozaki_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             OZ_SMEM);
+        if (e != cudaSuccess) {
+            delete m;
+            return e;
+        }
+        attr_set = true;
+    }
+    *out = m;
+    return cudaSuccess;
+}
+
+void oz_maps_destroy(OzMaps* m) { delete m; }
+
+// P's slices below its scale 2^e_P > max |P| (returned), each value rounded once
+// to 42 bits below the scale and cut into 7-bit integers, as BF16 bit patterns
+// (exact: |a_i| <= 128).
+int oz_slice_host(const double* P, int n, int ld, uint16_t* const planes[OZ_S]) {
+    double pmax = 0.0;
+    for (size_t i = 0; i < (size_t)n * n; ++i) pmax = fabs(P[i]) > pmax ? fabs(P[i]) : pmax;
+    int ep = 0;
+    frexp(pmax, &ep);
+    for (int r = 0; r < n; ++r)
+        for (int k = 0; k < n; ++k) {
+            const double x = P[(size_t)r * n + k];
+            const long long t = llrint(ldexp(x, OZ_FRAC - ep));
+            const unsigned long long u = (unsigned long long)(t < 0 ? -t : t);
+            for (int i = 0; i < OZ_S; ++i) {
+                const unsigned long long d = u >> (OZ_BITS * (OZ_S - 1 - i));
+                const float v = (t < 0 ? -1.f : 1.f) * (float)(i == 0 ? d : (d & ((1ull << OZ_BITS) - 1)));
+                uint32_t bits;
+                memcpy(&bits, &v, 4);
+                planes[i][(size_t)r * ld + k] = (uint16_t)(bits >> 16);  // exact: at most 8 significant bits
+            }
+        }
+    return ep;
+}
+
+cudaError_t launch_ozaki_pass(const OzMaps* maps, int p_exp, const double* A, int M, int n, int nbatch, int ld,
+                              void* const slices[OZ_S], int* rexp, const Epi<double>& e, unsigned* err,
+                              cudaStream_t st) {
+    OzPlanes planes;
+    for (int i = 0; i < OZ_S; ++i) planes.s[i] = static_cast<__nv_bfloat16*>(slices[i]);
+    const long long rows = (long long)nbatch * M;
+    long long blocks = (rows + 7) / 8;  // one warp per row
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    oz_slice_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, rows, n, ld, rexp, planes);
+    OzParams p;
+    p.M = M;
+    p.n = n;
+    p.nbatch = nbatch;
+    p.p_exp = p_exp;
+    p.tiles_m = (int)(((long long)nbatch * M + OZ_BM - 1) / OZ_BM);
+    p.tiles_n = (n + OZ_BN - 1) / OZ_BN;
+    p.rexp = rexp;
+    p.err = err;
+    p.e = e;
+    ozaki_pass_kernel<<<(unsigned)((long long)p.tiles_m * p.tiles_n), OZ_THREADS, OZ_SMEM, st>>>(*maps, p);
+    return cudaGetLastError();
+}
+
+}  // namespace etd

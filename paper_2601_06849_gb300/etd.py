@@ -18,7 +18,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libetd.so")
 
 ETD_OK, ETD_ERR_INVALID_ARG, ETD_ERR_OOM, ETD_ERR_CUDA, ETD_ERR_UNSUPPORTED, ETD_ERR_DIVERGED, ETD_ERR_TIMEOUT = range(7)
-PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4, "bf16x6": 5, "tf32x6": 6, "dst32": 7}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4, "bf16x6": 5, "tf32x6": 6, "dst32": 7,
+             "fp64split": 8}
 REACTION = {"none": 0, "linear": 1, "allen_cahn": 2, "fhn": 3, "singular": 4, "ac_forced": 5}
 FAMILY = {"exact": 0, 2: 2, 4: 4, 0: 0}
 
@@ -60,7 +61,7 @@ class etd_plan_info(ctypes.Structure):
         ("products", ctypes.c_int), ("gemms_per_step", ctypes.c_int),
         ("unknowns", ctypes.c_longlong), ("gemm_flops", ctypes.c_double), ("step_flops", ctypes.c_double),
         ("workspace_bytes", ctypes.c_longlong), ("pass_persistent", ctypes.c_int * 2),
-        ("pass_tile_n", ctypes.c_int * 2), ("step_bytes", ctypes.c_double),
+        ("pass_tile_n", ctypes.c_int * 2), ("step_bytes", ctypes.c_double), ("kernels_per_pass", ctypes.c_int),
     ]
 
 
@@ -236,7 +237,7 @@ class Batch:
         count = len(n)
         d = [d] * count if isinstance(d, int) else list(d)
         self.n, self.d, self.n_comp = list(n), d, n_comp
-        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.dtype = torch.float64 if precision in ("fp64", "fp64split") else torch.float32
         opt = etd_options_default()
         opt.precision = PRECISION[precision]
         opt.reaction = REACTION[reaction]
@@ -295,7 +296,7 @@ class Plan:
     """One ETD2RK-DS problem on (0,1)^d with n interior points per axis.
 
     ``pade``: 2 (P_{0,2}), 4 (P_{0,4}) or "exact" (eq. (9)-(10)).
-    ``precision``: one of PRECISION; fields are float64 for "fp64", else float32.
+    ``precision``: one of PRECISION; fields are float64 for "fp64" and "fp64split", else float32.
     ``diag_every``, ``diag_max_abs``: the in-step field check of etd_options
     (0 = off); a failed check makes the next ``sync()`` raise ETD_ERR_DIVERGED.
     """
@@ -308,7 +309,7 @@ class Plan:
 
         self.d, self.n, self.dt, self.n_comp = d, n, dt, n_comp
         self.precision = precision
-        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.dtype = torch.float64 if precision in ("fp64", "fp64split") else torch.float32
         opt = etd_options_default()
         opt.precision = PRECISION[precision]
         opt.reaction = REACTION[reaction]

@@ -21,7 +21,7 @@ def setup(d, n, kind, precision, pade=2):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision,bar", [("fp64", 1e-9), ("tf32x3", 1e-5), ("bf16x6", 1e-5)])
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-9), ("fp64split", 1e-9), ("tf32x3", 1e-5), ("bf16x6", 1e-5)])
 @pytest.mark.parametrize("d,n,kind,pade", [(2, 20, "fhn", 2), (3, 10, "allen_cahn", 2), (2, 33, "linear", 4),
                                            (3, 12, "fhn", 4)])
 def test_adjoint_matches_fp64_oracle(precision, bar, d, n, kind, pade):

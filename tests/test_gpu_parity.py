@@ -10,6 +10,7 @@ returned field is set by the transforms:
   fp32    4 sqrt(n) 2^-24       FP32 round-to-nearest sums of n terms in each output pass
   tf32    3e-3                  one TF32 product: 11-bit operands (2^-11 = 4.9e-4 per pass)
   bf16x6  1e-6                  three BF16 pieces (24 bits) in every pass
+  fp64split 1e-10               FP64 fields; products of six 7-bit slices, exact accumulation
   bf16x3  3e-6                  two BF16 pieces (16 bits, 2^-17 = 7.6e-6 per operand) in the
                                 per-step passes, reaching the state through tau f: over the
                                 N tau <= 0.2 of these runs <= 0.2 * 7.6e-6 on top of the 1e-6 bar
@@ -23,7 +24,8 @@ from oracle import oracle as O
 from oracle import spectral as S
 from paper_2601_06849_gb300 import etd, inputs
 
-TOL = {"fp64": 1e-10, "tf32x3": 1e-6, "tf32x6": 1e-6, "tf32": 3e-3, "bf16x6": 1e-6, "bf16x3": 3e-6}
+TOL = {"fp64": 1e-10, "fp64split": 1e-10, "tf32x3": 1e-6, "tf32x6": 1e-6, "tf32": 3e-3, "bf16x6": 1e-6,
+       "bf16x3": 3e-6}
 
 
 def tol(precision, n):
@@ -51,7 +53,7 @@ def oracle_ref(d, n, kappa, q, tau, u0, steps, reaction, rp=(), pade=2):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "tf32x6", "fp32", "tf32", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64split", "tf32x3", "tf32x6", "fp32", "tf32", "bf16x3", "bf16x6"])
 def test_allen_cahn_2d_n64_100_steps(precision):
     """2D Allen-Cahn, n = 64, kappa = 0.01, q = 0, tau = 1e-3, 100 steps."""
     torch = need_gpu()
@@ -63,7 +65,7 @@ def test_allen_cahn_2d_n64_100_steps(precision):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "tf32x6", "fp32", "tf32", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64split", "tf32x3", "tf32x6", "fp32", "tf32", "bf16x3", "bf16x6"])
 @pytest.mark.parametrize("n", [300, 129])
 def test_fhn_2d_ragged(precision, n):
     """2D FitzHugh-Nagumo with the workload's parameters on grids with ragged tiles."""
@@ -76,7 +78,7 @@ def test_fhn_2d_ragged(precision, n):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "fp32", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64split", "tf32x3", "fp32", "bf16x3", "bf16x6"])
 @pytest.mark.parametrize("n", [48, 33])
 def test_allen_cahn_3d(precision, n):
     """3D Allen-Cahn, kappa = 1e-3, q = 0.1, tau = 5e-3, Gaussian bump."""
@@ -88,7 +90,7 @@ def test_allen_cahn_3d(precision, n):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "tf32x6", "bf16x6"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64split", "tf32x3", "tf32x6", "bf16x6"])
 def test_fhn_3d_two_components(precision):
     torch = need_gpu()
     n = 40
@@ -100,7 +102,7 @@ def test_fhn_3d_two_components(precision):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64split", "tf32x3"])
 @pytest.mark.parametrize("d,n", [(2, 96), (3, 30)])
 def test_pade04(precision, d, n):
     torch = need_gpu()
@@ -111,7 +113,7 @@ def test_pade04(precision, d, n):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64split", "tf32x3", "bf16x6"])
 @pytest.mark.parametrize("d,n", [(2, 80), (3, 36)])
 def test_exact_exponential(precision, d, n):
     """eq. (9)-(10) with exact exponentials against the FP64 Sylvester oracle
@@ -128,7 +130,7 @@ def test_exact_exponential(precision, d, n):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64split", "tf32x3"])
 @pytest.mark.parametrize("d", [2, 3])
 def test_smallest_grid(precision, d):
     torch = need_gpu()
@@ -241,7 +243,7 @@ def test_bad_field_arguments():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["bf16x6", "fp64"])
+@pytest.mark.parametrize("precision", ["bf16x6", "fp64", "fp64split"])
 @pytest.mark.parametrize("d,n", [(2, 96), (3, 40)])
 def test_fused_reaction_across_calls_and_interleaved_transforms(precision, d, n):
     """Allen-Cahn is evaluated in the transform epilogues (f(W) in the pass that
@@ -263,3 +265,16 @@ def test_fused_reaction_across_calls_and_interleaved_transforms(precision, d, n)
     ref = oracle_ref(d, n, (0.01,), 0.1, tau, u0, 8, "allen_cahn")
     assert rel_err(u.double().cpu().numpy(), ref) < tol(precision, n)
     plan.close()
+
+
+@pytest.mark.gpu
+def test_fp64split_2d_n1024_fhn():
+    """The FP64-split tensor-core path on a 2D FitzHugh-Nagumo grid of n = 1024
+    (K = 1024: 32 k-blocks of exact level sums per tile) within the FP64 bar."""
+    torch = need_gpu()
+    n, steps = 1024, 10
+    u0 = inputs.fhn_uniform(n, 2, workload=15)
+    ref = oracle_ref(2, n, (1e-3, 5e-3), 0.0, 1e-2, u0, steps, "fhn", FHN)
+    got = run_gpu(torch, 2, n, 1e-3, 0.0, 1e-2, u0, steps, "fp64split", "fhn", FHN, kappa_comp=(1e-3, 5e-3))
+    for c in range(2):
+        assert rel_err(got[c], ref[c]) < 1e-10

@@ -7,7 +7,13 @@ from gpu_util import need_gpu, rel_err, sine_basis
 from paper_2601_06849_gb300 import etd, inputs
 
 # bound on max|T_gpu - T| / max|T| for one transform (2 or 3 chained passes)
-TOL = {"fp64": 1e-13, "fp32": 1e-5, "tf32x3": 2e-6, "tf32x6": 2e-6, "tf32": 5e-3, "bf16x3": 2e-6, "bf16x6": 2e-6}
+# fp64split: operands rounded to 49 bits below their component's power-of-two
+# scale (2^-50 relative to max), products below level 7 dropped (each term under
+# 2^-49 of the scales' product): up to about 8 x 2^-47 = 5.7e-14 relative to
+# max |T| per pass (a CPU emulation of the same arithmetic gives 1.6e-14 at
+# n = 37 to 4.6e-14 at n = 1024), 1e-13 per pass allowed, d passes
+TOL = {"fp64": 1e-13, "fp32": 1e-5, "tf32x3": 2e-6, "tf32x6": 2e-6, "tf32": 5e-3, "bf16x3": 2e-6, "bf16x6": 2e-6,
+       "fp64split": 1e-13}
 
 
 def reference(x, d):
@@ -30,20 +36,45 @@ def test_sine_basis_diagonalises_operator():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32x3", "tf32x6", "tf32", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "tf32x3", "tf32x6", "tf32", "bf16x3", "bf16x6", "fp64split"])
 @pytest.mark.parametrize("d,n,ncomp", [(2, 64, 1), (2, 200, 2), (2, 37, 1), (3, 24, 1), (3, 45, 2), (2, 520, 1),
                                        (2, 2, 1)])
 def test_transform_matches_definition(precision, d, n, ncomp):
     torch = need_gpu()
     x = inputs.random_field((ncomp,) + (n,) * d, workload=40, sub=n)
     plan = etd.Plan(d, n, 0.01, 0.0, 1e-3, precision=precision, reaction="linear", n_comp=ncomp)
-    dt = torch.float64 if precision == "fp64" else torch.float32
+    dt = plan.dtype
     xt = torch.tensor(x, dtype=dt, device="cuda")
     out = plan.transform(xt)
     plan.sync()
     ref = reference(xt.double().cpu().numpy(), d)
-    assert rel_err(out.cpu().numpy(), ref) < TOL[precision]
+    bound = TOL[precision] * (d if precision == "fp64split" else 1)
+    assert rel_err(out.cpu().numpy(), ref) < bound
     back = plan.transform(out)
     plan.sync()
-    assert rel_err(back.cpu().numpy(), xt.double().cpu().numpy()) < 2 * TOL[precision]
+    assert rel_err(back.cpu().numpy(), xt.double().cpu().numpy()) < 2 * bound
+    plan.close()
+
+
+@pytest.mark.gpu
+def test_fp64split_scales_per_component_and_keeps_nan():
+    """The slices' scale is per operand row: a component a million times smaller
+    than the other keeps its own relative accuracy; a NaN in one component
+    makes that component's transform NaN and leaves the other intact."""
+    torch = need_gpu()
+    n = 96
+    x = inputs.random_field((2, n, n), workload=41)
+    x[1] *= 1e-6
+    plan = etd.Plan(2, n, 0.01, 0.0, 1e-3, precision="fp64split", reaction="linear", n_comp=2)
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda")
+    out = plan.transform(xt)
+    plan.sync()
+    ref = reference(x, 2)
+    for c in range(2):
+        assert rel_err(out[c].cpu().numpy(), ref[c]) < 2 * TOL["fp64split"]
+    xt[0, 5, 7] = float("nan")
+    out = plan.transform(xt)
+    plan.sync()
+    assert torch.isnan(out[0]).all()
+    assert rel_err(out[1].cpu().numpy(), ref[1]) < 2 * TOL["fp64split"]
     plan.close()
