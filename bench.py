@@ -67,7 +67,7 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32 (f32 fields)",
          "tf32x6": "tf32x6 (f32 fields, double-float spectral state)",
          "bf16x3": "bf16x3 (f32 fields, double-float spectral state)",
          "bf16x6": "bf16x6 (f32 fields, double-float spectral state)",
-         "fp64split": "f64 (f64 fields and state; products as 28 exact bf16 slice products)",
+         "fp64split": "f64 (f64 fields and state; products as 21 exact bf16 slice products)",
          "dst32": "f32 (fast sine transforms)"}
 KERNEL_FILES = ["paper_2601_06849_gb300/csrc/gemm_tc.cu", "paper_2601_06849_gb300/csrc/etd_internal.cuh"]
 L2_BYTES = 129e6
@@ -136,7 +136,7 @@ def run_adjoint(args, world, rank, local):
     # forward and the adjoint's 9 transforms (d passes each) per step, 2 n^(d+1) per
     # pass and component, times the split products
     products = {"fp64": 1, "fp32": 1, "tf32": 1, "tf32x3": 3, "bf16x3": 3, "bf16x6": 6, "tf32x6": 6,
-                "fp64split": 28}.get(
+                "fp64split": 21}.get(
         args.precision, 1)
     passes = window * (4 * d + 4 * d + 9 * d)
     flops = passes * 2.0 * n ** (d + 1) * 2 * products * iters

@@ -7,46 +7,53 @@
 //
 // Slices. Every operand value x of row r (the n values one output row contracts)
 // is written as a fixed-point number below the power of two 2^e_r > max |x| over the row:
-//     x ~ 2^(e_r - 49) t,   t = round(x 2^(49 - e_r)),  |t| <= 2^49,
-// and t is cut into OZ_S = 7 slices of 7 bits, most significant first,
-//     t = sum_i a_i 2^(7 (6 - i)),   |a_0| <= 128, |a_i| <= 127, all with the sign of x.
+//     x ~ 2^(e_r - 48) t,   t = round(x 2^(48 - e_r)),  |t| <= 2^48,
+// and t is cut into OZ_S = 6 slices of 8 bits, most significant first,
+//     t = sum_i a_i 2^(8 (5 - i)),   |a_0| <= 256, |a_i| <= 255, all with the sign of x.
 // P is cut the same way below its own scale 2^e_P > max |P| (about sqrt(2/(n+1)):
 // a fixed scale of 1 would leave its top slices nearly empty), once per plan on
-// the host. Every
-// slice is an integer of at most 8 significant bits, exact in BF16, and every
-// slice product is an integer of magnitude below 2^14.
+// the host. Every slice is an integer of at most 8 significant bits (256 = 2^8
+// included), exact in BF16, and every slice product an integer of at most 2^16.
 //
-// Products. The product of slices a_i and p_j carries the weight 2^(-7 (i + j));
-// all pairs (i, j) of one level l = i + j <= 6 (28 pairs) accumulate in one
-// TMEM accumulator per k-block of 32 values: at most 7 pairs x 32 products x
-// 2^14 < 2^22 in magnitude, so the FP32 accumulation of these integers is exact
-// whatever the order of the additions inside the tensor core. The k-block sums
-// S_l are added in int32 registers (exact up to K = 16384), and at the end
-//     out = 2^(e_r + e_P - 28) (G_0 + G_1 2^-21 + G_2 2^-42),
-//     G_g = S_3g 2^14 + S_3g+1 2^7 + S_3g+2       (int64, exact; missing levels 0)
+// Products. The product of slices a_i and p_j carries the weight 2^(-8 (i + j));
+// all pairs (i, j) of one level l = i + j <= 5 (21 pairs) accumulate in one
+// TMEM accumulator per k-block of 32 values: at most 6 pairs x 32 products x
+// 2^16 < 2^24 in magnitude (6 x 2^21), so the FP32 accumulation of these
+// integers is exact whatever the order of the additions inside the tensor core.
+// The k-block sums S_l are added in int32 registers, exact for K <= 4096
+// (128 k-blocks x 6 x 2^21 < 2^31; the plan rejects larger grids), and at the end
+//     out = 2^(e_r + e_P - 32) (G_0 + G_1 2^-24),
+//     G_g = S_3g 2^16 + S_3g+1 2^8 + S_3g+2       (int64, exact)
 // is formed in FP64 (two roundings). What is left out: the rounding of each
-// operand to 49 bits below its row's scale (2^-50 relative to the row's max) and
-// the pairs with i + j >= 7 (each below 2^-49 of the scales' product per term): a
-// few 2^-47 relative to the row's max |out| for sums of random signs. The scale
+// operand to 48 bits below its row's scale (2^-49 relative to the row's max) and
+// the pairs with i + j >= 6 (each below 2^-48 of the scales' product per term): a
+// few 2^-46 relative to the row's max |out| for sums of random signs. The scale
 // is per row, not per component: the spectral coefficients of a field dominated
 // by a constant (FitzHugh-Nagumo's v, driven by eps b) are large in a few modes,
 // and the back-transform recovers the field through heavy cancellation; with one
 // scale per component that lost 40x more (CPU emulation of this arithmetic, n =
-// 512: 7.3e-11 against 1.9e-12). Six slices were short of 1e-10 on the same
-// structure, hence seven.
+// 512: 7.3e-11 against 1.9e-12). 42 bits (six 7-bit slices) were short of 1e-10
+// on the same structure; 48 bits in 8-bit slices take no more products.
 //
 // Per pass: a slicing kernel (one warp per operand row: the row's scale, then its
-// seven BF16 slice planes in the layout of the FP64 operand buffer) and the
+// six BF16 slice planes in the layout of the FP64 operand buffer) and the
 // product kernel, one 128 x 32 tile per CTA:
-//   warps 0-7  drain: per k-block, tcgen05.ld of the seven level accumulators of
+//   warps 0-7  drain: per k-block, tcgen05.ld of the six level accumulators of
 //              their TMEM lane quarter and 16-column half, integer sums; at the
 //              end the FP64 result and the fused epilogue (Epi<double>, the
 //              Hadamard stages and outputs of the FP64 path);
 //   warp 8     TMA producer (one lane) and TMEM allocator;
-//   warp 9     MMA issuer (one lane): 56 tcgen05.mma.kind::f16 per k-block.
+//   warp 9     MMA issuer (one lane): per k-step of 16 values, one product per A
+//              slice i with all P slices j <= 5 - i at once. The six level
+//              accumulators of a buffer are consecutive 32-column TMEM blocks and
+//              the P slices consecutive 32-row blocks of shared memory, so the
+//              product of A slice i (M = 128, K = 16) with P slices 0 .. 5 - i
+//              (N = 32 (6 - i)), written from level block i on, adds a_i p_j to
+//              level block i + j: 6 products per k-step instead of 21, each A
+//              chunk read from shared memory once per k-step.
 // Shared memory holds three pipeline stages of 32 K-values (64-byte rows,
-// 64-byte swizzle) of the seven A slices and the seven P slices (70 KB per stage).
-// TMEM holds two k-block buffers of seven 32-column level accumulators.
+// 64-byte swizzle) of the six A slices and the six P slices (60 KB per stage).
+// TMEM holds two k-block buffers of six 32-column level accumulators.
 // Every wait is bounded (tc_ptx.cuh); on expiry the CTA raises ERR_TIMEOUT and
 // returns after its copies and products have completed (bounded as well).
 #include <cuda.h>
@@ -77,9 +84,9 @@ constexpr int OZ_DRAIN_WARPS = 8;
 constexpr int OZ_WARP_TMA = 8;
 constexpr int OZ_WARP_MMA = 9;
 constexpr int OZ_THREADS = 320;
-constexpr uint32_t OZ_TMEM_COLS = 512;  // 2 buffers x 7 levels x 32 columns = 448, allocated as 512
-constexpr int OZ_BITS = 7;
-constexpr int OZ_FRAC = OZ_S * OZ_BITS;  // 49 bits below the scale
+constexpr uint32_t OZ_TMEM_COLS = 512;  // 2 buffers x 6 levels x 32 columns = 384, allocated as 512
+constexpr int OZ_BITS = 8;
+constexpr int OZ_FRAC = OZ_S * OZ_BITS;  // 48 bits below the scale
 static_assert(2 * OZ_S * OZ_BN <= (int)OZ_TMEM_COLS, "level accumulators exceed the TMEM allocation");
 static_assert(OZ_SMEM <= 227 * 1024, "pipeline stages exceed the shared memory of a CTA");
 
@@ -106,7 +113,7 @@ constexpr int OZ_EXP_NONFINITE = 4096;   // row with NaN or Inf: NaN result
 
 namespace {
 
-// The seven BF16 slice planes of A and each row's scale exponent, one warp per
+// The six BF16 slice planes of A and each row's scale exponent, one warp per
 // row of the stacked batch entries (row r at r * ld; only its n values are
 // written, TMA reads zeros beyond): the warp reduces max |x| over the row, then
 // cuts every value below 2^e_r > max |x| (the row is read again from L1/L2).
@@ -141,7 +148,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
             code = e;
         }
         if (lane == 0) rexp[r] = code;
-        const double scale = pow2(OZ_FRAC - e);  // x * scale = t, |t| <= 2^49
+        const double scale = pow2(OZ_FRAC - e);  // x * scale = t, |t| <= 2^48
         const long long o0 = r * ld;
         for (int k = lane; k < n; k += 32) {
             const double x = row[k];
@@ -161,7 +168,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
                 }
             }
 #pragma unroll
-            for (int i = 0; i < OZ_S; ++i) out.s[i][o0 + k] = __float2bfloat16_rn(a[i]);  // exact: |a_i| <= 128
+            for (int i = 0; i < OZ_S; ++i) out.s[i][o0 + k] = __float2bfloat16_rn(a[i]);  // exact: |a_i| <= 256
         }
     }
 }
@@ -244,8 +251,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
         }
         s_issued = issued;
     } else if (warp == OZ_WARP_MMA && lane == 0) {
-        // ---------------- MMA issuer: the 28 slice pairs of levels 0-6 ----------------
-        const uint32_t idesc = idesc_bf16(OZ_BM, OZ_BN);
+        // ---------------- MMA issuer: the 21 slice pairs of levels 0-5 as 6 products ----------------
         const uint64_t desc0 = sdesc_kmajor(smem_u32(smem), OZ_ROW);
         for (int q = 0; q < nk; ++q) {
             const int s = q % OZ_STAGES, a = q & 1;
@@ -256,15 +262,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
             const uint64_t dB = dA + (uint64_t)(OZ_S * (OZ_A_BYTES >> 4));
             const uint32_t d = tmem + (uint32_t)(a * OZ_S * OZ_BN);
 #pragma unroll
-            for (int i = 0; i < OZ_S; ++i) {
+            for (int kk = 0; kk < OZ_ROW / 32; ++kk) {  // 16 BF16 values (32 bytes) of K per product
 #pragma unroll
-                for (int j = 0; j < OZ_S - i; ++j) {
-#pragma unroll
-                    for (int kk = 0; kk < OZ_ROW / 32; ++kk) {  // 16 BF16 values (32 bytes) of K per MMA
-                        // the level's first product of the k-block overwrites its accumulator
-                        mma_bf16(d + (uint32_t)((i + j) * OZ_BN), dA + (uint64_t)(i * (OZ_A_BYTES >> 4) + 2 * kk),
-                                 dB + (uint64_t)(j * (OZ_B_BYTES >> 4) + 2 * kk), idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                    }
+                for (int i = 0; i < OZ_S; ++i) {
+                    // A slice i times P slices 0 .. OZ_S-1-i into level blocks i .. OZ_S-1; the
+                    // first product of the k-block (i = 0, all six blocks) overwrites them
+                    mma_bf16(d + (uint32_t)(i * OZ_BN), dA + (uint64_t)(i * (OZ_A_BYTES >> 4) + 2 * kk),
+                             dB + (uint64_t)(2 * kk), idesc_bf16(OZ_BM, OZ_BN * (OZ_S - i)),
+                             (i > 0 || kk > 0) ? 1u : 0u);
                 }
             }
             mma_commit(bar_empty + 8 * s);     // the stage may be refilled once these products finish
@@ -307,12 +312,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
             const int mh = mm / p.n, ml = mm - mh * p.n;
             const int code = p.rexp[grow];
             const bool nan_out = code == OZ_EXP_NONFINITE;
-            const double scale = pow2((code == OZ_EXP_ZERO || nan_out ? 0 : code) + p.p_exp - 28);
+            const double scale = pow2((code == OZ_EXP_ZERO || nan_out ? 0 : code) + p.p_exp - 4 * OZ_BITS);
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
                 const int nn = tn * OZ_BN + half * 16 + c;
                 if (nn >= p.n) continue;
-                long long G[(OZ_S + 2) / 3];  // three levels per group (7 bits apart), exact in int64
+                long long G[(OZ_S + 2) / 3];  // three levels per group (8 bits apart), exact in int64
 #pragma unroll
                 for (int g = 0; g < (OZ_S + 2) / 3; ++g) {
                     G[g] = 0;
@@ -322,7 +327,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
                 }
                 double v = (double)G[(OZ_S + 2) / 3 - 1];
 #pragma unroll
-                for (int g = (OZ_S + 2) / 3 - 2; g >= 0; --g) v = fma(v, 0x1p-21, (double)G[g]);
+                for (int g = (OZ_S + 2) / 3 - 2; g >= 0; --g) v = fma(v, pow2(-3 * OZ_BITS), (double)G[g]);
                 v *= scale;
                 if (nan_out) v = __longlong_as_double(0x7ff8000000000000ll);
                 p.e.apply(b, mh, ml, nn, v);
@@ -401,8 +406,8 @@ cudaError_t oz_maps_create(OzMaps** out, int M, int n, int nbatch, int ld, void*
 void oz_maps_destroy(OzMaps* m) { delete m; }
 
 // P's slices below its scale 2^e_P > max |P| (returned), each value rounded once
-// to 42 bits below the scale and cut into 7-bit integers, as BF16 bit patterns
-// (exact: |a_i| <= 128).
+// to 48 bits below the scale and cut into 8-bit integers, as BF16 bit patterns
+// (exact: |a_i| <= 256).
 int oz_slice_host(const double* P, int n, int ld, uint16_t* const planes[OZ_S]) {
     double pmax = 0.0;
     for (size_t i = 0; i < (size_t)n * n; ++i) pmax = fabs(P[i]) > pmax ? fabs(P[i]) : pmax;
