@@ -82,3 +82,75 @@ def test_adjoint_matches_gpu_finite_differences_3d_fhn():
         v = torch.tensor(inputs.random_field(tuple(u0.shape), workload=114), dtype=torch.float64, device="cuda")
         fd = (loss(u0 + h * v, kap, rp) - loss(u0 - h * v, kap, rp)).item() / (2 * h)
         assert (u0r.grad * v).sum().item() == pytest.approx(fd, rel=1e-5)
+
+
+def fhn_window_grads(torch, n, steps, precision, u0, target, every=20):
+    """Gradients of 0.5 ||u(T) - target||^2 over a 3D FitzHugh-Nagumo window (the
+    bench's adjoint workload parameters) through autograd.solve."""
+    from paper_2601_06849_gb300 import autograd as AG
+
+    dt = torch.float64 if precision in ("fp64", "fp64split") else torch.float32
+    u0r = torch.tensor(u0, dtype=dt, device="cuda").requires_grad_(True)
+    kr = torch.tensor([1e-3, 5e-3], dtype=torch.float64, requires_grad=True)
+    rr = torch.tensor([1.0, 0.01, 0.5, 0.1], dtype=torch.float64, requires_grad=True)
+    u = AG.solve(u0r, kr, rr, d=3, n=n, q=0.0, dt=1e-2, n_steps=steps, precision=precision, reaction="fhn",
+                 checkpoint_every=every)
+    loss = 0.5 * ((u - torch.tensor(target, dtype=dt, device="cuda")) ** 2).sum()
+    loss.backward()
+    return kr.grad.numpy(), rr.grad.numpy(), u0r.grad.double().cpu().numpy()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,bar", [("fp64split", 1e-8), ("bf16x6", 3e-4), ("tf32x3", 3e-3)])
+def test_adjoint_long_window_against_fp64(precision, bar):
+    """200 steps (10 checkpoint segments) of 3D FitzHugh-Nagumo, n = 24: each
+    gradient (dL/dkappa, dL/d eps, dL/du0) against the FP64 path, relative to its
+    largest entry. The FP32-field paths carry FP32 fields through the window and
+    the adjoint, so their bounds here are stated errors, not the 1e-5 bar; for
+    scale, rounding u0 to FP32 alone moves dL/du0 of the FP64 path by 5e-6 to
+    1.4e-5 on this problem, so no FP32-field path can reach 1e-5 on u0 over such
+    a window. The FP64-split path (FP64 fields) is held to 1e-8."""
+    torch = need_gpu()
+    n, steps = 24, 200
+    u0 = inputs.fhn_uniform(n, 3, workload=115)
+    target = inputs.fhn_uniform(n, 3, workload=116, lo=-0.05, hi=0.05)
+    ref = fhn_window_grads(torch, n, steps, "fp64", u0, target)
+    got = fhn_window_grads(torch, n, steps, precision, u0, target)
+    assert rel_err(got[0], ref[0]) < bar  # kappa_u, kappa_v
+    assert abs(got[1][1] - ref[1][1]) < bar * abs(ref[1][1])  # eps
+    assert rel_err(got[2], ref[2]) < bar  # u0
+
+
+@pytest.mark.gpu
+def test_adjoint_fp64split_matches_finite_differences():
+    """The FP64-split path: adjoint gradients against central differences of its
+    own forward run (3D FitzHugh-Nagumo, 40 steps, two checkpoint segments)."""
+    torch = need_gpu()
+    from paper_2601_06849_gb300 import autograd as AG
+
+    n, steps, tau = 16, 40, 1e-2
+    rp = torch.tensor([1.0, 0.01, 0.5, 0.1], dtype=torch.float64)
+    kap = torch.tensor([1e-3, 5e-3], dtype=torch.float64)
+    u0 = torch.tensor(inputs.fhn_uniform(n, 3, workload=112), dtype=torch.float64, device="cuda")
+    target = torch.tensor(inputs.fhn_uniform(n, 3, workload=113), dtype=torch.float64, device="cuda")
+
+    def loss(u0_, kap_, rp_):
+        u = AG.solve(u0_, kap_, rp_, d=3, n=n, q=0.0, dt=tau, n_steps=steps, precision="fp64split", reaction="fhn",
+                     checkpoint_every=20)
+        return 0.5 * ((u - target) ** 2).sum()
+
+    u0r = u0.clone().requires_grad_(True)
+    kr = kap.clone().requires_grad_(True)
+    rr = rp.clone().requires_grad_(True)
+    loss(u0r, kr, rr).backward()
+    h = 1e-5
+    with torch.no_grad():
+        for c in range(2):
+            kp, km = kap.clone(), kap.clone()
+            kp[c] *= 1 + h
+            km[c] *= 1 - h
+            fd = (loss(u0, kp, rp) - loss(u0, km, rp)).item() / (2 * h * kap[c].item())
+            assert kr.grad[c].item() == pytest.approx(fd, rel=1e-5, abs=1e-12)
+        v = torch.tensor(inputs.random_field(tuple(u0.shape), workload=114), dtype=torch.float64, device="cuda")
+        fd = (loss(u0 + h * v, kap, rp) - loss(u0 - h * v, kap, rp)).item() / (2 * h)
+        assert (u0r.grad * v).sum().item() == pytest.approx(fd, rel=1e-5)
