@@ -737,7 +737,7 @@ etd_status validate_options(int d, int m, int pade_order, const etd_options& opt
         if (N < 16 || N > 8192 || (N & (N - 1)))
             return fail(ETD_ERR_UNSUPPORTED, "ETD_PREC_DST32 needs m + 1 a power of two in [16, 8192] (m = %d)", m);
     }
-    if (opt.precision == ETD_PREC_FP64_SPLIT && m > OZ_MAX_N)
+    if (opt.precision == ETD_PREC_FP64_SPLIT && m > OZ_MAX_N)  // the 2D limit; exact int32 level sums up to it
         return fail(ETD_ERR_UNSUPPORTED, "ETD_PREC_FP64_SPLIT needs m <= %d (exact level sums; m = %d)", OZ_MAX_N, m);
     if (opt.precision < ETD_PREC_FP64 || opt.precision > ETD_PREC_FP64_SPLIT)
         return fail(ETD_ERR_INVALID_ARG, "unknown precision");

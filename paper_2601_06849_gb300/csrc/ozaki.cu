@@ -7,53 +7,55 @@
 //
 // Slices. Every operand value x of row r (the n values one output row contracts)
 // is written as a fixed-point number below the power of two 2^e_r > max |x| over the row:
-//     x ~ 2^(e_r - 48) t,   t = round(x 2^(48 - e_r)),  |t| <= 2^48,
-// and t is cut into OZ_S = 6 slices of 8 bits, most significant first,
-//     t = sum_i a_i 2^(8 (5 - i)),   |a_0| <= 256, |a_i| <= 255, all with the sign of x.
+//     x ~ 2^(e_r - 49) t,   t = round(x 2^(49 - e_r)),  |t| <= 2^49,
+// and t is cut into OZ_S = 7 slices of 7 bits, most significant first,
+//     t = sum_i a_i 2^(7 (6 - i)),   |a_0| <= 128, |a_i| <= 127, all with the sign of x.
 // P is cut the same way below its own scale 2^e_P > max |P| (about sqrt(2/(n+1)):
 // a fixed scale of 1 would leave its top slices nearly empty), once per plan on
-// the host. Every slice is an integer of at most 8 significant bits (256 = 2^8
-// included), exact in BF16, and every slice product an integer of at most 2^16.
+// the host. Every slice is an integer of at most 8 significant bits, exact in
+// BF16, and every slice product an integer of magnitude at most 2^14.
 //
-// Products. The product of slices a_i and p_j carries the weight 2^(-8 (i + j));
-// all pairs (i, j) of one level l = i + j <= 5 (21 pairs) accumulate in one
-// TMEM accumulator per k-block of 32 values: at most 6 pairs x 32 products x
-// 2^16 < 2^24 in magnitude (6 x 2^21), so the FP32 accumulation of these
-// integers is exact whatever the order of the additions inside the tensor core.
-// The k-block sums S_l are added in int32 registers, exact for K <= 4096
-// (128 k-blocks x 6 x 2^21 < 2^31; the plan rejects larger grids), and at the end
-//     out = 2^(e_r + e_P - 32) (G_0 + G_1 2^-24),
-//     G_g = S_3g 2^16 + S_3g+1 2^8 + S_3g+2       (int64, exact)
+// Products. The product of slices a_i and p_j carries the weight 2^(-7 (i + j));
+// all pairs (i, j) of one level l = i + j <= 6 (28 pairs) accumulate in one TMEM
+// accumulator over a group of OZ_GROUP = 4 k-blocks of 32 values: at most 7
+// pairs x 128 products x 2^14 < 2^24 in magnitude, so the FP32 accumulation of
+// these integers is exact whatever the order of the additions inside the tensor
+// core. The group sums S_l are added in int32 registers (exact up to K = 16384:
+// 128 groups x 7 x 2^21 < 2^31), and at the end
+//     out = 2^(e_r + e_P - 28) (G_0 + G_1 2^-21 + G_2 2^-42),
+//     G_g = S_3g 2^14 + S_3g+1 2^7 + S_3g+2       (int64, exact; missing levels 0)
 // is formed in FP64 (two roundings). What is left out: the rounding of each
-// operand to 48 bits below its row's scale (2^-49 relative to the row's max) and
-// the pairs with i + j >= 6 (each below 2^-48 of the scales' product per term): a
-// few 2^-46 relative to the row's max |out| for sums of random signs. The scale
+// operand to 49 bits below its row's scale (2^-50 relative to the row's max) and
+// the pairs with i + j >= 7 (each below 2^-49 of the scales' product per term): a
+// few 2^-47 relative to the row's max |out| for sums of random signs. The scale
 // is per row, not per component: the spectral coefficients of a field dominated
 // by a constant (FitzHugh-Nagumo's v, driven by eps b) are large in a few modes,
 // and the back-transform recovers the field through heavy cancellation; with one
 // scale per component that lost 40x more (CPU emulation of this arithmetic, n =
-// 512: 7.3e-11 against 1.9e-12). 42 bits (six 7-bit slices) were short of 1e-10
-// on the same structure; 48 bits in 8-bit slices take no more products.
+// 512: 7.3e-11 against 1.9e-12). Seven-bit slices are what allows a TMEM buffer
+// to accumulate four k-blocks before it is drained: the drain (TMEM loads, int32
+// sums) bounded the kernel when it ran after every k-block (8-bit slices).
 //
 // Per pass: a slicing kernel (one warp per operand row: the row's scale, then its
-// six BF16 slice planes in the layout of the FP64 operand buffer) and the
+// seven BF16 slice planes in the layout of the FP64 operand buffer) and the
 // product kernel, one 128 x 32 tile per CTA:
-//   warps 0-7  drain: per k-block, tcgen05.ld of the six level accumulators of
-//              their TMEM lane quarter and 16-column half, integer sums; at the
-//              end the FP64 result and the fused epilogue (Epi<double>, the
-//              Hadamard stages and outputs of the FP64 path);
+//   warps 0-7  drain: per group of four k-blocks, tcgen05.ld of the seven level
+//              accumulators of their TMEM lane quarter and 16-column half (two
+//              levels per load round trip), integer sums; at the end the FP64
+//              result and the fused epilogue (Epi<double>, the Hadamard stages
+//              and outputs of the FP64 path);
 //   warp 8     TMA producer (one lane) and TMEM allocator;
 //   warp 9     MMA issuer (one lane): per k-step of 16 values, one product per A
-//              slice i with all P slices j <= 5 - i at once. The six level
+//              slice i with all P slices j <= 6 - i at once. The seven level
 //              accumulators of a buffer are consecutive 32-column TMEM blocks and
 //              the P slices consecutive 32-row blocks of shared memory, so the
-//              product of A slice i (M = 128, K = 16) with P slices 0 .. 5 - i
-//              (N = 32 (6 - i)), written from level block i on, adds a_i p_j to
-//              level block i + j: 6 products per k-step instead of 21, each A
+//              product of A slice i (M = 128, K = 16) with P slices 0 .. 6 - i
+//              (N = 32 (7 - i)), written from level block i on, adds a_i p_j to
+//              level block i + j: 7 products per k-step instead of 28, each A
 //              chunk read from shared memory once per k-step.
 // Shared memory holds three pipeline stages of 32 K-values (64-byte rows,
-// 64-byte swizzle) of the six A slices and the six P slices (60 KB per stage).
-// TMEM holds two k-block buffers of six 32-column level accumulators.
+// 64-byte swizzle) of the seven A slices and the seven P slices (70 KB per stage).
+// TMEM holds two buffers of seven 32-column level accumulators.
 // Every wait is bounded (tc_ptx.cuh); on expiry the CTA raises ERR_TIMEOUT and
 // returns after its copies and products have completed (bounded as well).
 #include <cuda.h>
@@ -84,9 +86,10 @@ constexpr int OZ_DRAIN_WARPS = 8;
 constexpr int OZ_WARP_TMA = 8;
 constexpr int OZ_WARP_MMA = 9;
 constexpr int OZ_THREADS = 320;
-constexpr uint32_t OZ_TMEM_COLS = 512;  // 2 buffers x 6 levels x 32 columns = 384, allocated as 512
-constexpr int OZ_BITS = 8;
-constexpr int OZ_FRAC = OZ_S * OZ_BITS;  // 48 bits below the scale
+constexpr uint32_t OZ_TMEM_COLS = 512;  // 2 buffers x 7 levels x 32 columns = 448, allocated as 512
+constexpr int OZ_BITS = 7;
+constexpr int OZ_FRAC = OZ_S * OZ_BITS;  // 49 bits below the scale
+constexpr int OZ_GROUP = 4;              // k-blocks (32 values each) a TMEM buffer accumulates before a drain
 static_assert(2 * OZ_S * OZ_BN <= (int)OZ_TMEM_COLS, "level accumulators exceed the TMEM allocation");
 static_assert(OZ_SMEM <= 227 * 1024, "pipeline stages exceed the shared memory of a CTA");
 
@@ -113,7 +116,7 @@ constexpr int OZ_EXP_NONFINITE = 4096;   // row with NaN or Inf: NaN result
 
 namespace {
 
-// The six BF16 slice planes of A and each row's scale exponent, one warp per
+// The seven BF16 slice planes of A and each row's scale exponent, one warp per
 // row of the stacked batch entries (row r at r * ld; only its n values are
 // written, TMA reads zeros beyond): the warp reduces max |x| over the row, then
 // cuts every value below 2^e_r > max |x| (the row is read again from L1/L2).
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
             code = e;
         }
         if (lane == 0) rexp[r] = code;
-        const double scale = pow2(OZ_FRAC - e);  // x * scale = t, |t| <= 2^48
+        const double scale = pow2(OZ_FRAC - e);  // x * scale = t, |t| <= 2^49
         const long long o0 = r * ld;
         for (int k = lane; k < n; k += 32) {
             const double x = row[k];
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
                 }
             }
 #pragma unroll
-            for (int i = 0; i < OZ_S; ++i) out.s[i][o0 + k] = __float2bfloat16_rn(a[i]);  // exact: |a_i| <= 256
+            for (int i = 0; i < OZ_S; ++i) out.s[i][o0 + k] = __float2bfloat16_rn(a[i]);  // exact: |a_i| <= 128
         }
     }
 }
@@ -251,12 +254,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
         }
         s_issued = issued;
     } else if (warp == OZ_WARP_MMA && lane == 0) {
-        // ---------------- MMA issuer: the 21 slice pairs of levels 0-5 as 6 products ----------------
+        // ---------------- MMA issuer: the 28 slice pairs of levels 0-6 as 7 products ----------------
         const uint64_t desc0 = sdesc_kmajor(smem_u32(smem), OZ_ROW);
         for (int q = 0; q < nk; ++q) {
-            const int s = q % OZ_STAGES, a = q & 1;
+            const int s = q % OZ_STAGES;
+            const int g = q / OZ_GROUP, a = g & 1;  // TMEM buffer a holds k-block group g
+            const bool first = q % OZ_GROUP == 0, last = q % OZ_GROUP == OZ_GROUP - 1 || q == nk - 1;
             if (!mbar_wait(bar_full + 8 * s, (uint32_t)((q / OZ_STAGES) & 1), abort_flag, p.err)) break;
-            if (q >= 2 && !mbar_wait(bar_acc_empty + 8 * a, (uint32_t)(((q >> 1) - 1) & 1), abort_flag, p.err)) break;
+            if (first && g >= 2 &&
+                !mbar_wait(bar_acc_empty + 8 * a, (uint32_t)(((g >> 1) - 1) & 1), abort_flag, p.err))
+                break;
             tc_fence_after();
             const uint64_t dA = desc0 + (uint64_t)(s * (OZ_STAGE_BYTES >> 4));
             const uint64_t dB = dA + (uint64_t)(OZ_S * (OZ_A_BYTES >> 4));
@@ -266,14 +273,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
 #pragma unroll
                 for (int i = 0; i < OZ_S; ++i) {
                     // A slice i times P slices 0 .. OZ_S-1-i into level blocks i .. OZ_S-1; the
-                    // first product of the k-block (i = 0, all six blocks) overwrites them
+                    // first product of a group (i = 0, all level blocks) overwrites them
                     mma_bf16(d + (uint32_t)(i * OZ_BN), dA + (uint64_t)(i * (OZ_A_BYTES >> 4) + 2 * kk),
                              dB + (uint64_t)(2 * kk), idesc_bf16(OZ_BM, OZ_BN * (OZ_S - i)),
-                             (i > 0 || kk > 0) ? 1u : 0u);
+                             (i > 0 || kk > 0 || !first) ? 1u : 0u);
                 }
             }
-            mma_commit(bar_empty + 8 * s);     // the stage may be refilled once these products finish
-            mma_commit(bar_acc_full + 8 * a);  // the k-block's level sums are ready
+            mma_commit(bar_empty + 8 * s);                // the stage may be refilled once these products finish
+            if (last) mma_commit(bar_acc_full + 8 * a);  // the group's level sums are ready
             s_consumed = q + 1;
         }
         mma_commit(bar_done);
@@ -287,20 +294,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
 #pragma unroll
             for (int c = 0; c < 16; ++c) acc[l][c] = 0;
         bool ok = true;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int a = kb & 1;
-            if (!mbar_wait(bar_acc_full + 8 * a, (uint32_t)((kb >> 1) & 1), abort_flag, p.err)) {
+        const int ng = (nk + OZ_GROUP - 1) / OZ_GROUP;
+        for (int g = 0; g < ng; ++g) {
+            const int a = g & 1;
+            if (!mbar_wait(bar_acc_full + 8 * a, (uint32_t)((g >> 1) & 1), abort_flag, p.err)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
+            // two levels per TMEM load round trip
 #pragma unroll
-            for (int l = 0; l < OZ_S; ++l) {
-                uint32_t r[16];
-                tmem_ld16(lane_base + (uint32_t)((a * OZ_S + l) * OZ_BN), r);
-                tmem_wait16(r);
+            for (int l = 0; l < OZ_S; l += 2) {
+                uint32_t r[32];
+                tmem_ld16(lane_base + (uint32_t)((a * OZ_S + l) * OZ_BN), *reinterpret_cast<uint32_t(*)[16]>(r));
+                if (l + 1 < OZ_S)
+                    tmem_ld16(lane_base + (uint32_t)((a * OZ_S + l + 1) * OZ_BN),
+                              *reinterpret_cast<uint32_t(*)[16]>(r + 16));
+                tmem_wait32(r);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) acc[l][c] += __float2int_rn(__uint_as_float(r[c]));  // exact integers
+                for (int h = 0; h < 2; ++h)
+                    if (l + h < OZ_S)
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            acc[l + h][c] += __float2int_rn(__uint_as_float(r[16 * h + c]));  // exact integers
             }
             tc_fence_before();
             __syncwarp();
@@ -317,7 +333,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
             for (int c = 0; c < 16; ++c) {
                 const int nn = tn * OZ_BN + half * 16 + c;
                 if (nn >= p.n) continue;
-                long long G[(OZ_S + 2) / 3];  // three levels per group (8 bits apart), exact in int64
+                long long G[(OZ_S + 2) / 3];  // three levels per group (7 bits apart), exact in int64
 #pragma unroll
                 for (int g = 0; g < (OZ_S + 2) / 3; ++g) {
                     G[g] = 0;
@@ -406,8 +422,8 @@ cudaError_t oz_maps_create(OzMaps** out, int M, int n, int nbatch, int ld, void*
 void oz_maps_destroy(OzMaps* m) { delete m; }
 
 // P's slices below its scale 2^e_P > max |P| (returned), each value rounded once
-// to 48 bits below the scale and cut into 8-bit integers, as BF16 bit patterns
-// (exact: |a_i| <= 256).
+// to 49 bits below the scale and cut into 7-bit integers, as BF16 bit patterns
+// (exact: |a_i| <= 128).
 int oz_slice_host(const double* P, int n, int ld, uint16_t* const planes[OZ_S]) {
     double pmax = 0.0;
     for (size_t i = 0; i < (size_t)n * n; ++i) pmax = fabs(P[i]) > pmax ? fabs(P[i]) : pmax;

@@ -106,11 +106,3 @@ def test_options_defaults_and_diag_validation(lib):
         etd.etd_plan_create(2, 64, 0.1, 0.0, 1e-3, 2, o)
     assert ei.value.status == etd.ETD_ERR_INVALID_ARG
 
-
-def test_fp64_split_rejects_grids_beyond_its_exact_range(lib):
-    """The FP64-split products keep exact int32 level sums up to K = 4096."""
-    o = etd.etd_options_default()
-    o.precision = etd.PRECISION["fp64split"]
-    with pytest.raises(etd.EtdError) as ei:
-        etd.etd_plan_create(2, 4097, 0.1, 0.0, 1e-3, 2, o)
-    assert ei.value.status == etd.ETD_ERR_UNSUPPORTED

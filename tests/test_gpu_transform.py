@@ -7,11 +7,11 @@ from gpu_util import need_gpu, rel_err, sine_basis
 from paper_2601_06849_gb300 import etd, inputs
 
 # bound on max|T_gpu - T| / max|T| for one transform (2 or 3 chained passes)
-# fp64split: operands rounded to 48 bits below their row's power-of-two scale
-# (2^-49 relative to the row's max), products below level 6 dropped (each term
-# under 2^-48 of the scales' product): up to about 8 x 2^-46 = 1.1e-13 relative
-# to max |T| per pass (a CPU emulation of the same arithmetic gives 3e-14 at
-# n = 37 to 9e-14 at n = 1024), 2e-13 per pass allowed, d passes
+# fp64split: operands rounded to 49 bits below their row's power-of-two scale
+# (2^-50 relative to the row's max), products below level 7 dropped (each term
+# under 2^-49 of the scales' product): up to about 8 x 2^-47 = 5.7e-14 relative
+# to max |T| per pass (a CPU emulation of the same arithmetic gives 1.6e-14 at
+# n = 37 to 4.6e-14 at n = 1024), 2e-13 per pass allowed, d passes
 TOL = {"fp64": 1e-13, "fp32": 1e-5, "tf32x3": 2e-6, "tf32x6": 2e-6, "tf32": 5e-3, "bf16x3": 2e-6, "bf16x6": 2e-6,
        "fp64split": 2e-13}
 
