@@ -422,12 +422,15 @@ def run_accuracy(args, world, rank, local):
             out.append(np.asarray(u, dtype=np.float64))
             prev = k
         return out
+    need32 = args.floors or any(pr not in F64_PRECISIONS for pr in precisions)
+    need64 = args.floors or any(pr in F64_PRECISIONS for pr in precisions)
     t0 = time.perf_counter()
-    ref32 = oracle_checkpoints(u0f)
-    oracle_s = time.perf_counter() - t0
-    ref64 = oracle_checkpoints(u0)
-    floor_in = [max(rel_errs(a, b)) for a, b in zip(ref64, ref32)]
-    floor_sh = [max(rel_errs(a, b)) for a, b in zip(oracle_checkpoints(u0f, "f32"), ref32)]
+    ref32 = oracle_checkpoints(u0f) if need32 else None
+    ref64 = oracle_checkpoints(u0) if need64 else None
+    oracle_s = (time.perf_counter() - t0) / (int(need32) + int(need64))
+    floor_in = [max(rel_errs(a, b)) for a, b in zip(ref64, ref32)] if args.floors else None
+    floor_sh = ([max(rel_errs(a, b)) for a, b in zip(oracle_checkpoints(u0f, "f32"), ref32)]
+                if args.floors else None)
     errors = {}
     for prec in precisions:
         plan = make_plan(name, prec)
@@ -445,8 +448,8 @@ def run_accuracy(args, world, rank, local):
         plan.close()
     line = {"metric": "max rel err vs FP64 oracle over the run", "workload": desc, "steps": total,
             "checkpoints": marks, "errors": errors,
-            "floors": {"fp32_input_rounding": {"max": max(floor_in), "per_checkpoint": floor_in},
-                       "fp32_shadow": {"max": max(floor_sh), "per_checkpoint": floor_sh}},
+            "floors": ({"fp32_input_rounding": {"max": max(floor_in), "per_checkpoint": floor_in},
+                        "fp32_shadow": {"max": max(floor_sh), "per_checkpoint": floor_sh}} if args.floors else None),
             "oracle": {"seconds_per_run": oracle_s, "cores": O.max_threads()},
             "error_metric": "max over checkpoints and components of max|U - U_ref| / max|U_ref|"}
     print(json.dumps(line), flush=True)
@@ -696,6 +699,8 @@ def main():
                     help="error vs the FP64 oracle over the workload's whole run length, with floors")
     ap.add_argument("--precisions", default="bf16x6,tf32x3", help="--accuracy: comma-separated precisions")
     ap.add_argument("--accuracy-steps", type=int, default=None, help="--accuracy: override the run length")
+    ap.add_argument("--no-floors", dest="floors", action="store_false",
+                    help="--accuracy: skip the FP32-shadow and input-rounding floors (two oracle runs fewer)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
