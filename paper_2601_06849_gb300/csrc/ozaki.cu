@@ -38,7 +38,9 @@
 //
 // Per pass: a slicing kernel (one warp per operand row: the row's scale, then its
 // seven BF16 slice planes in the layout of the FP64 operand buffer) and the
-// product kernel, one 128 x 32 tile per CTA:
+// product kernel, persistent (one CTA per SM walks the 128 x 32 tiles; the MMA
+// warp fills the two TMEM buffers with the next tile's first groups while the
+// drain warps run the previous tile's epilogue):
 //   warps 0-7  drain: per group of four k-blocks, tcgen05.ld of the seven level
 //              accumulators of their TMEM lane quarter and 16-column half (two
 //              levels per load round trip), integer sums; at the end the FP64
@@ -123,20 +125,43 @@ namespace {
 // rexp[r] = e_r; OZ_EXP_ZERO for a row of zeros (or below 1e-250: its slices
 // are zero), OZ_EXP_NONFINITE for a row with NaN or Inf (its first slice
 // carries them, so the products and the result of the row are NaN).
+// Slices of one value below the scale: t = round(x 2^(49 - e)) as 7-bit integers,
+// extracted from the two 32-bit halves of |t| (bits 21-48 and 0-20).
+__device__ __forceinline__ void oz_cut(double x, double scale, float (&a)[OZ_S]) {
+    const long long t = __double2ll_rn(x * scale);  // exact power-of-two scaling, one rounding
+    const unsigned long long u = (unsigned long long)(t < 0 ? -t : t);
+    const float sg = t < 0 ? -1.f : 1.f;
+    const uint32_t hi = (uint32_t)(u >> 21), lo = (uint32_t)(u & 0x1FFFFFu);
+    a[0] = sg * (float)(hi >> 21);  // up to 128 (t rounded up to 2^49)
+    a[1] = sg * (float)((hi >> 14) & 127u);
+    a[2] = sg * (float)((hi >> 7) & 127u);
+    a[3] = sg * (float)(hi & 127u);
+    a[4] = sg * (float)(lo >> 14);
+    a[5] = sg * (float)((lo >> 7) & 127u);
+    a[6] = sg * (float)(lo & 127u);
+}
+static_assert(OZ_S == 7 && OZ_BITS == 7, "oz_cut is written for seven 7-bit slices");
+
 __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ A, long long rows, int n, int ld,
                                                       int* __restrict__ rexp, OzPlanes out) {
     const int lane = threadIdx.x & 31;
     const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+    const int npair = n >> 1;  // value pairs per row (rows start on even elements: ld is a multiple of 8)
     for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += wstride) {
         const double* row = A + r * ld;
+        const double2* row2 = reinterpret_cast<const double2*>(row);
         double m = 0.0;
         bool bad = false;
-        for (int k = lane; k < n; k += 32) {
-            const double v = fabs(row[k]);
-            if (v <= 1.7976931348623157e308)
-                m = fmax(m, v);
-            else
-                bad = true;
+        for (int k = lane; k < npair; k += 32) {
+            const double2 v = row2[k];
+            const double a = fabs(v.x), b = fabs(v.y);
+            bad |= !(a <= 1.7976931348623157e308) || !(b <= 1.7976931348623157e308);
+            m = fmax(m, fmax(a, b));
+        }
+        if ((n & 1) && lane == 0) {
+            const double a = fabs(row[n - 1]);
+            bad |= !(a <= 1.7976931348623157e308);
+            m = fmax(m, a);
         }
         for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
         bad = __any_sync(0xffffffffu, bad);
@@ -153,25 +178,32 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
         if (lane == 0) rexp[r] = code;
         const double scale = pow2(OZ_FRAC - e);  // x * scale = t, |t| <= 2^49
         const long long o0 = r * ld;
-        for (int k = lane; k < n; k += 32) {
-            const double x = row[k];
-            float a[OZ_S];
-#pragma unroll
-            for (int i = 0; i < OZ_S; ++i) a[i] = 0.f;
+        auto cut = [&](double x, float (&a)[OZ_S]) {
             if (code == OZ_EXP_NONFINITE) {
+#pragma unroll
+                for (int i = 0; i < OZ_S; ++i) a[i] = 0.f;
                 if (!(fabs(x) <= 1.7976931348623157e308)) a[0] = (float)x;  // NaN / Inf into the products
-            } else if (code != OZ_EXP_ZERO) {
-                const long long t = __double2ll_rn(x * scale);  // exact power-of-two scaling, one rounding
-                const unsigned long long u = (unsigned long long)(t < 0 ? -t : t);
-                const float sg = t < 0 ? -1.f : 1.f;
+            } else if (code == OZ_EXP_ZERO) {
 #pragma unroll
-                for (int i = 0; i < OZ_S; ++i) {
-                    const unsigned long long d = u >> (OZ_BITS * (OZ_S - 1 - i));
-                    a[i] = sg * (float)(i == 0 ? d : (d & ((1ull << OZ_BITS) - 1)));
-                }
+                for (int i = 0; i < OZ_S; ++i) a[i] = 0.f;
+            } else {
+                oz_cut(x, scale, a);
             }
+        };
+        for (int k = lane; k < npair; k += 32) {
+            const double2 v = row2[k];
+            float a[OZ_S], b[OZ_S];
+            cut(v.x, a);
+            cut(v.y, b);
 #pragma unroll
-            for (int i = 0; i < OZ_S; ++i) out.s[i][o0 + k] = __float2bfloat16_rn(a[i]);  // exact: |a_i| <= 128
+            for (int i = 0; i < OZ_S; ++i)  // exact: |a_i| <= 128
+                reinterpret_cast<__nv_bfloat162*>(out.s[i] + o0)[k] = __floats2bfloat162_rn(a[i], b[i]);
+        }
+        if ((n & 1) && lane == 0) {
+            float a[OZ_S];
+            cut(row[n - 1], a);
+#pragma unroll
+            for (int i = 0; i < OZ_S; ++i) out.s[i][o0 + n - 1] = __float2bfloat16_rn(a[i]);
         }
     }
 }
@@ -203,9 +235,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
     const uint32_t bar_acc_empty = smem_u32(&s_bar[2 * OZ_STAGES + 2]);
     const uint32_t bar_done = smem_u32(&s_bar[2 * OZ_STAGES + 4]);
 
-    int tm, tn;
-    tile_coords(blockIdx.x, p.tiles_m, p.tiles_n, 8, tm, tn);
-    const int nk = (p.n + OZ_KV - 1) / OZ_KV;  // k-blocks (one pipeline stage each)
+    const int nk = (p.n + OZ_KV - 1) / OZ_KV;  // k-blocks of a tile (one pipeline stage each)
+    const int ng = (nk + OZ_GROUP - 1) / OZ_GROUP;  // k-block groups of a tile (one TMEM buffer each)
+    const int ntiles = p.tiles_m * p.tiles_n;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OZ_STAGES; ++s) {
@@ -235,35 +267,47 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
     const uint32_t tmem = s_tmem;
 
     if (warp == OZ_WARP_TMA && lane == 0) {
-        // ---------------- TMA producer: the six A and six P slices of each k-block ----------------
-        const int arow = tm * OZ_BM, prow = tn * OZ_BN;
-        int issued = 0;
-        for (int q = 0; q < nk; ++q) {
-            const int s = q % OZ_STAGES;
-            if (!mbar_wait(bar_empty + 8 * s, (uint32_t)(((q / OZ_STAGES) & 1) ^ 1), abort_flag, p.err)) break;
-            const uint32_t st = smem_u32(smem + (size_t)s * OZ_STAGE_BYTES);
-            const uint32_t fb = bar_full + 8 * s;
-            mbar_expect_tx(fb, (uint32_t)OZ_STAGE_BYTES);
-            const int k0 = q * OZ_KV;
+        // ---------------- TMA producer: the A and P slices of each k-block, tile after tile ----------------
+        int gq = 0;  // k-blocks issued by this CTA so far (one ring across tiles)
+        bool stop = false;
+        for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+            int tm, tn;
+            tile_coords(t, p.tiles_m, p.tiles_n, 8, tm, tn);
+            const int arow = tm * OZ_BM, prow = tn * OZ_BN;
+            for (int q = 0; q < nk; ++q, ++gq) {
+                const int s = gq % OZ_STAGES;
+                if (!mbar_wait(bar_empty + 8 * s, (uint32_t)(((gq / OZ_STAGES) & 1) ^ 1), abort_flag, p.err)) {
+                    stop = true;
+                    break;
+                }
+                const uint32_t st = smem_u32(smem + (size_t)s * OZ_STAGE_BYTES);
+                const uint32_t fb = bar_full + 8 * s;
+                mbar_expect_tx(fb, (uint32_t)OZ_STAGE_BYTES);
+                const int k0 = q * OZ_KV;
 #pragma unroll
-            for (int i = 0; i < OZ_S; ++i) tma_load_2d(st + (uint32_t)(i * OZ_A_BYTES), &maps.a[i], fb, k0, arow);
+                for (int i = 0; i < OZ_S; ++i) tma_load_2d(st + (uint32_t)(i * OZ_A_BYTES), &maps.a[i], fb, k0, arow);
 #pragma unroll
-            for (int j = 0; j < OZ_S; ++j)
-                tma_load_2d(st + (uint32_t)(OZ_S * OZ_A_BYTES + j * OZ_B_BYTES), &maps.p[j], fb, k0, prow);
-            issued = q + 1;
+                for (int j = 0; j < OZ_S; ++j)
+                    tma_load_2d(st + (uint32_t)(OZ_S * OZ_A_BYTES + j * OZ_B_BYTES), &maps.p[j], fb, k0, prow);
+                s_issued = gq + 1;
+            }
         }
-        s_issued = issued;
     } else if (warp == OZ_WARP_MMA && lane == 0) {
         // ---------------- MMA issuer: the 28 slice pairs of levels 0-6 as 7 products ----------------
         const uint64_t desc0 = sdesc_kmajor(smem_u32(smem), OZ_ROW);
-        for (int q = 0; q < nk; ++q) {
-            const int s = q % OZ_STAGES;
-            const int g = q / OZ_GROUP, a = g & 1;  // TMEM buffer a holds k-block group g
+        int gq = 0, gg = 0;  // k-blocks and k-block groups of this CTA so far
+        bool stop = false;
+        for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+        for (int q = 0; q < nk; ++q, ++gq) {
+            const int s = gq % OZ_STAGES;
+            const int g = gg + q / OZ_GROUP, a = g & 1;  // TMEM buffer a holds k-block group g
             const bool first = q % OZ_GROUP == 0, last = q % OZ_GROUP == OZ_GROUP - 1 || q == nk - 1;
-            if (!mbar_wait(bar_full + 8 * s, (uint32_t)((q / OZ_STAGES) & 1), abort_flag, p.err)) break;
-            if (first && g >= 2 &&
-                !mbar_wait(bar_acc_empty + 8 * a, (uint32_t)(((g >> 1) - 1) & 1), abort_flag, p.err))
+            if (!mbar_wait(bar_full + 8 * s, (uint32_t)((gq / OZ_STAGES) & 1), abort_flag, p.err) ||
+                (first && g >= 2 &&
+                 !mbar_wait(bar_acc_empty + 8 * a, (uint32_t)(((g >> 1) - 1) & 1), abort_flag, p.err))) {
+                stop = true;
                 break;
+            }
             tc_fence_after();
             const uint64_t dA = desc0 + (uint64_t)(s * (OZ_STAGE_BYTES >> 4));
             const uint64_t dB = dA + (uint64_t)(OZ_S * (OZ_A_BYTES >> 4));
@@ -281,72 +325,80 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
             }
             mma_commit(bar_empty + 8 * s);                // the stage may be refilled once these products finish
             if (last) mma_commit(bar_acc_full + 8 * a);  // the group's level sums are ready
-            s_consumed = q + 1;
+            s_consumed = gq + 1;
+        }
+        gg += ng;
         }
         mma_commit(bar_done);
     } else if (warp < OZ_DRAIN_WARPS) {
         // ---------------- drain: exact integer level sums, then the FP64 epilogue ----------------
         const int quarter = warp & 3, half = warp >> 2;  // TMEM lanes 32 quarter.., columns 16 half..
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 16);
-        int acc[OZ_S][16];
-#pragma unroll
-        for (int l = 0; l < OZ_S; ++l)
-#pragma unroll
-            for (int c = 0; c < 16; ++c) acc[l][c] = 0;
+        int gg = 0;  // k-block groups drained by this CTA so far
         bool ok = true;
-        const int ng = (nk + OZ_GROUP - 1) / OZ_GROUP;
-        for (int g = 0; g < ng; ++g) {
-            const int a = g & 1;
-            if (!mbar_wait(bar_acc_full + 8 * a, (uint32_t)((g >> 1) & 1), abort_flag, p.err)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            // two levels per TMEM load round trip
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            int tm, tn;
+            tile_coords(t, p.tiles_m, p.tiles_n, 8, tm, tn);
+            int acc[OZ_S][16];
 #pragma unroll
-            for (int l = 0; l < OZ_S; l += 2) {
-                uint32_t r[32];
-                tmem_ld16(lane_base + (uint32_t)((a * OZ_S + l) * OZ_BN), *reinterpret_cast<uint32_t(*)[16]>(r));
-                if (l + 1 < OZ_S)
-                    tmem_ld16(lane_base + (uint32_t)((a * OZ_S + l + 1) * OZ_BN),
-                              *reinterpret_cast<uint32_t(*)[16]>(r + 16));
-                tmem_wait32(r);
+            for (int l = 0; l < OZ_S; ++l)
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
-                    if (l + h < OZ_S)
-#pragma unroll
-                        for (int c = 0; c < 16; ++c)
-                            acc[l + h][c] += __float2int_rn(__uint_as_float(r[16 * h + c]));  // exact integers
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar_acc_empty + 8 * a);
-        }
-        const int grow = tm * OZ_BM + quarter * 32 + lane;  // row of the stacked batch entries
-        if (ok && !*abort_flag && grow < p.nbatch * p.M) {
-            const int b = grow / p.M, mm = grow - b * p.M;
-            const int mh = mm / p.n, ml = mm - mh * p.n;
-            const int code = p.rexp[grow];
-            const bool nan_out = code == OZ_EXP_NONFINITE;
-            const double scale = pow2((code == OZ_EXP_ZERO || nan_out ? 0 : code) + p.p_exp - 4 * OZ_BITS);
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                const int nn = tn * OZ_BN + half * 16 + c;
-                if (nn >= p.n) continue;
-                long long G[(OZ_S + 2) / 3];  // three levels per group (7 bits apart), exact in int64
-#pragma unroll
-                for (int g = 0; g < (OZ_S + 2) / 3; ++g) {
-                    G[g] = 0;
-#pragma unroll
-                    for (int j = 0; j < 3; ++j)
-                        if (3 * g + j < OZ_S) G[g] += (long long)acc[3 * g + j][c] << (OZ_BITS * (2 - j));
+                for (int c = 0; c < 16; ++c) acc[l][c] = 0;
+            for (int q = 0; q < ng; ++q, ++gg) {
+                const int a = gg & 1;
+                if (!mbar_wait(bar_acc_full + 8 * a, (uint32_t)((gg >> 1) & 1), abort_flag, p.err)) {
+                    ok = false;
+                    break;
                 }
-                double v = (double)G[(OZ_S + 2) / 3 - 1];
+                tc_fence_after();
+                // two levels per TMEM load round trip
 #pragma unroll
-                for (int g = (OZ_S + 2) / 3 - 2; g >= 0; --g) v = fma(v, pow2(-3 * OZ_BITS), (double)G[g]);
-                v *= scale;
-                if (nan_out) v = __longlong_as_double(0x7ff8000000000000ll);
-                p.e.apply(b, mh, ml, nn, v);
+                for (int l = 0; l < OZ_S; l += 2) {
+                    uint32_t r[32];
+                    tmem_ld16(lane_base + (uint32_t)((a * OZ_S + l) * OZ_BN), *reinterpret_cast<uint32_t(*)[16]>(r));
+                    if (l + 1 < OZ_S)
+                        tmem_ld16(lane_base + (uint32_t)((a * OZ_S + l + 1) * OZ_BN),
+                                  *reinterpret_cast<uint32_t(*)[16]>(r + 16));
+                    tmem_wait32(r);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        if (l + h < OZ_S)
+#pragma unroll
+                            for (int c = 0; c < 16; ++c)
+                                acc[l + h][c] += __float2int_rn(__uint_as_float(r[16 * h + c]));  // exact integers
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_acc_empty + 8 * a);
+            }
+            // the tile's FP64 results and epilogue; meanwhile the MMA warp fills the
+            // freed TMEM buffers with the next tile's first groups
+            const int grow = tm * OZ_BM + quarter * 32 + lane;  // row of the stacked batch entries
+            if (ok && !*abort_flag && grow < p.nbatch * p.M) {
+                const int b = grow / p.M, mm = grow - b * p.M;
+                const int mh = mm / p.n, ml = mm - mh * p.n;
+                const int code = p.rexp[grow];
+                const bool nan_out = code == OZ_EXP_NONFINITE;
+                const double scale = pow2((code == OZ_EXP_ZERO || nan_out ? 0 : code) + p.p_exp - 4 * OZ_BITS);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int nn = tn * OZ_BN + half * 16 + c;
+                    if (nn >= p.n) continue;
+                    long long G[(OZ_S + 2) / 3];  // three levels per group (7 bits apart), exact in int64
+#pragma unroll
+                    for (int g = 0; g < (OZ_S + 2) / 3; ++g) {
+                        G[g] = 0;
+#pragma unroll
+                        for (int j = 0; j < 3; ++j)
+                            if (3 * g + j < OZ_S) G[g] += (long long)acc[3 * g + j][c] << (OZ_BITS * (2 - j));
+                    }
+                    double v = (double)G[(OZ_S + 2) / 3 - 1];
+#pragma unroll
+                    for (int g = (OZ_S + 2) / 3 - 2; g >= 0; --g) v = fma(v, pow2(-3 * OZ_BITS), (double)G[g]);
+                    v *= scale;
+                    if (nan_out) v = __longlong_as_double(0x7ff8000000000000ll);
+                    p.e.apply(b, mh, ml, nn, v);
+                }
             }
         }
     }
@@ -464,7 +516,15 @@ cudaError_t launch_ozaki_pass(const OzMaps* maps, int p_exp, const double* A, in
     p.rexp = rexp;
     p.err = err;
     p.e = e;
-    ozaki_pass_kernel<<<(unsigned)((long long)p.tiles_m * p.tiles_n), OZ_THREADS, OZ_SMEM, st>>>(*maps, p);
+    // persistent: one CTA per SM walks the tiles (grid = min(tiles, SMs))
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+    }
+    const long long ntiles = (long long)p.tiles_m * p.tiles_n;
+    ozaki_pass_kernel<<<(unsigned)(ntiles < sms ? ntiles : sms), OZ_THREADS, OZ_SMEM, st>>>(*maps, p);
     return cudaGetLastError();
 }
 
