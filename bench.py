@@ -4,7 +4,7 @@ Default workload (N = 1): 2D FitzHugh-Nagumo, n = 4096 interior points per axis,
 two fields, kappa_u = 1e-3, kappa_v = 5e-3, eps = 0.01, a = 0.5, b = 0.1,
 tau = 1e-2, Pade P_{0,2}, seeded U[-0.1, 0.1] fields, in the FP64-split
 precision: FP64 fields and state, every product with P as exact products of
-7-bit integer slices on the BF16 tensor cores. It is the precision that stays
+balanced 8-bit integer slices on the BF16 tensor cores. It is the precision that stays
 within 1e-6 of the FP64 oracle over this configuration's whole run of 1000 steps
 (9.5e-11 measured); split BF16 x6 (--precision bf16x6) is about six times faster
 and within 1e-6 for the first 100 steps, 4.6e-6 over the 1000.
@@ -70,7 +70,7 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32 (f32 fields)",
          "tf32x6": "tf32x6 (f32 fields, double-float spectral state)",
          "bf16x3": "bf16x3 (f32 fields, double-float spectral state)",
          "bf16x6": "bf16x6 (f32 fields, double-float spectral state)",
-         "fp64split": "f64 (f64 fields and state; products as 28 exact bf16 slice products)",
+         "fp64split": "f64 (f64 fields and state; products as 21 exact bf16 slice products)",
          "dst32": "f32 (fast sine transforms)"}
 # DRAM traffic records (ncu, per launch of the per-step pass) of the default
 # workload, with the kernel sources they are valid for
@@ -148,7 +148,7 @@ def run_adjoint(args, world, rank, local):
     # forward and the adjoint's 9 transforms (d passes each) per step, 2 n^(d+1) per
     # pass and component, times the split products
     products = {"fp64": 1, "fp32": 1, "tf32": 1, "tf32x3": 3, "bf16x3": 3, "bf16x6": 6, "tf32x6": 6,
-                "fp64split": 28}.get(
+                "fp64split": 21}.get(
         args.precision, 1)
     passes = window * (4 * d + 4 * d + 9 * d)
     flops = passes * 2.0 * n ** (d + 1) * 2 * products * iters

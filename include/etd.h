@@ -63,9 +63,9 @@ enum {
                             comparison path, not the paper's dense-eigenbasis method; needs
                             m + 1 a power of two, 16 <= m + 1 <= 8192 */
     ETD_PREC_FP64_SPLIT = 8 /* double fields and state; every product with P in FP64 accuracy on the
-                            BF16 tensor cores: each operand row cut into seven 7-bit integer slices below
-                            a power-of-two scale (P likewise), the 28 slice products of weight >= 2^-42
-                            accumulated exactly, the result formed in FP64 */
+                            BF16 tensor cores: each operand row cut into six balanced 8-bit integer
+                            slices below a power-of-two scale (P likewise), the 21 slice products of
+                            weight >= 2^-40 accumulated exactly, the result formed in FP64 */
 };
 /* In every split mode (X3, X6) the two transforms whose error stays in the
  * result, U -> U^ when the carried spectral state is (re)built and the
@@ -138,7 +138,7 @@ typedef struct {
 /* Performance-relevant facts of a plan (for benchmarks and roofline figures). */
 typedef struct {
     int d, n, n_comp, precision;
-    int products;                /* tensor-core products per MMA tile (1, 3, 6, or 28 slice products for
+    int products;                /* tensor-core products per MMA tile (1, 3, 6, or 21 slice products for
                                     ETD_PREC_FP64_SPLIT; 0 for CUDA cores) */
     int gemms_per_step;          /* transform passes per time step (8 in 2D, 12 in 3D) */
     long long unknowns;          /* n_comp * n^d */

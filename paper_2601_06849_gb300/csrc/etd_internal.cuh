@@ -651,9 +651,9 @@ cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, in
 const char* tc_last_driver_error();
 
 // ETD_PREC_FP64_SPLIT transform pass (ozaki.cu): FP64 operands cut into OZ_S
-// BF16 slices of 7 bits below a per-row power-of-two scale, exact slice
-// products on the tensor cores, FP64 result through the Epi<double> epilogue.
-constexpr int OZ_S = 7;
+// balanced 8-bit digits (BF16 slices) below a per-row power-of-two scale, exact
+// slice products on the tensor cores, FP64 result through the Epi<double> epilogue.
+constexpr int OZ_S = 6;
 constexpr int OZ_MAX_N = 16384;  // K <= 16384 keeps the int32 level sums exact
 constexpr int OZ_PAIRS = OZ_S * (OZ_S + 1) / 2;  // slice products per MMA tile and k-step
 struct OzMaps;  // opaque holder of the slice planes' tensor maps (ozaki.cu)

@@ -7,34 +7,38 @@
 //
 // Slices. Every operand value x of row r (the n values one output row contracts)
 // is written as a fixed-point number below the power of two 2^e_r > max |x| over the row:
-//     x ~ 2^(e_r - 49) t,   t = round(x 2^(49 - e_r)),  |t| <= 2^49,
-// and t is cut into OZ_S = 7 slices of 7 bits, most significant first,
-//     t = sum_i a_i 2^(7 (6 - i)),   |a_0| <= 128, |a_i| <= 127, all with the sign of x.
+//     x ~ 2^(e_r - 48) t,   t = round(x 2^(48 - e_r)),  |t| <= 2^48,
+// and t is cut into OZ_S = 6 balanced base-256 digits, most significant first,
+//     t = sum_i a_i 2^(8 (5 - i)),   a_1 .. a_5 in [-128, 128],  |a_0| <= 256.
 // P is cut the same way below its own scale 2^e_P > max |P| (about sqrt(2/(n+1)):
 // a fixed scale of 1 would leave its top slices nearly empty), once per plan on
-// the host. Every slice is an integer of at most 8 significant bits, exact in
-// BF16, and every slice product an integer of magnitude at most 2^14.
+// the host, with one bit less (t_P = round(p 2^(47 - e_P)), so |p_0| <= 128 too).
+// Every slice is an integer of at most 8 significant bits, exact in BF16; a slice
+// product is at most 2^15 in magnitude when it involves a_0, else 2^14. Balanced
+// digits carry 8 bits of the value in a slice of magnitude 2^7: the product bound
+// of 7-bit slices with the information of 8-bit ones.
 //
-// Products. The product of slices a_i and p_j carries the weight 2^(-7 (i + j));
-// all pairs (i, j) of one level l = i + j <= 6 (28 pairs) accumulate in one TMEM
-// accumulator over a group of OZ_GROUP = 4 k-blocks of 32 values: at most 7
-// pairs x 128 products x 2^14 < 2^24 in magnitude, so the FP32 accumulation of
-// these integers is exact whatever the order of the additions inside the tensor
-// core. The group sums S_l are added in int32 registers (exact up to K = 16384:
-// 128 groups x 7 x 2^21 < 2^31), and at the end
-//     out = 2^(e_r + e_P - 28) (G_0 + G_1 2^-21 + G_2 2^-42),
-//     G_g = S_3g 2^14 + S_3g+1 2^7 + S_3g+2       (int64, exact; missing levels 0)
+// Products. The product of slices a_i and p_j carries the weight 2^(-8 (i + j));
+// all pairs (i, j) of one level l = i + j <= 5 (21 pairs) accumulate in one TMEM
+// accumulator over a group of OZ_GROUP = 4 k-blocks of 32 values: at most
+// (2^15 + l 2^14) x 128 <= 7 x 2^21 < 2^24 in magnitude, so the FP32 accumulation
+// of these integers is exact whatever the order of the additions inside the
+// tensor core. The group sums S_l are added in int32 registers (exact up to
+// K = 16384: 128 groups x 7 x 2^21 < 2^31), and at the end
+//     out = 2^(e_r + e_P - 55) (J 2^16 + H_2),   J = H_0 2^16 + H_1,
+//     H_g = S_2g 2^8 + S_2g+1                     (int64, exact)
 // is formed in FP64 (two roundings). What is left out: the rounding of each
-// operand to 49 bits below its row's scale (2^-50 relative to the row's max) and
-// the pairs with i + j >= 7 (each below 2^-49 of the scales' product per term): a
-// few 2^-47 relative to the row's max |out| for sums of random signs. The scale
-// is per row, not per component: the spectral coefficients of a field dominated
-// by a constant (FitzHugh-Nagumo's v, driven by eps b) are large in a few modes,
-// and the back-transform recovers the field through heavy cancellation; with one
-// scale per component that lost 40x more (CPU emulation of this arithmetic, n =
-// 512: 7.3e-11 against 1.9e-12). Seven-bit slices are what allows a TMEM buffer
-// to accumulate four k-blocks before it is drained: the drain (TMEM loads, int32
-// sums) bounded the kernel when it ran after every k-block (8-bit slices).
+// operand to 48 bits below its row's scale (2^-49 relative to the row's max; P:
+// 2^-48) and the pairs with i + j >= 6 (each below 2^-49 of the scales' product
+// per term, of random sign): a few 2^-48 relative to the row's max |out|. The
+// scale is per row, not per component: the spectral coefficients of a field
+// dominated by a constant (FitzHugh-Nagumo's v, driven by eps b) are large in a
+// few modes, and the back-transform recovers the field through heavy
+// cancellation; with one scale per component that lost 40x more (CPU emulation
+// of this arithmetic, n = 512: 7.3e-11 against 1.9e-12). The small slices are
+// what allows a TMEM buffer to accumulate four k-blocks before it is drained: the
+// drain (TMEM loads, int32 sums) bounded the kernel when it ran after every
+// k-block (unbalanced 8-bit slices, products up to 2^16).
 //
 // Per pass: a slicing kernel (one warp per operand row: the row's scale, then its
 // seven BF16 slice planes in the layout of the FP64 operand buffer) and the
@@ -48,16 +52,16 @@
 //              and outputs of the FP64 path);
 //   warp 8     TMA producer (one lane) and TMEM allocator;
 //   warp 9     MMA issuer (one lane): per k-step of 16 values, one product per A
-//              slice i with all P slices j <= 6 - i at once. The seven level
+//              slice i with all P slices j <= 5 - i at once. The six level
 //              accumulators of a buffer are consecutive 32-column TMEM blocks and
 //              the P slices consecutive 32-row blocks of shared memory, so the
-//              product of A slice i (M = 128, K = 16) with P slices 0 .. 6 - i
-//              (N = 32 (7 - i)), written from level block i on, adds a_i p_j to
-//              level block i + j: 7 products per k-step instead of 28, each A
+//              product of A slice i (M = 128, K = 16) with P slices 0 .. 5 - i
+//              (N = 32 (6 - i)), written from level block i on, adds a_i p_j to
+//              level block i + j: 6 products per k-step instead of 21, each A
 //              chunk read from shared memory once per k-step.
 // Shared memory holds three pipeline stages of 32 K-values (64-byte rows,
-// 64-byte swizzle) of the seven A slices and the seven P slices (70 KB per stage).
-// TMEM holds two buffers of seven 32-column level accumulators.
+// 64-byte swizzle) of the six A slices and the six P slices (60 KB per stage).
+// TMEM holds two buffers of six 32-column level accumulators.
 // Every wait is bounded (tc_ptx.cuh); on expiry the CTA raises ERR_TIMEOUT and
 // returns after its copies and products have completed (bounded as well).
 #include <cuda.h>
@@ -88,9 +92,10 @@ constexpr int OZ_DRAIN_WARPS = 8;
 constexpr int OZ_WARP_TMA = 8;
 constexpr int OZ_WARP_MMA = 9;
 constexpr int OZ_THREADS = 320;
-constexpr uint32_t OZ_TMEM_COLS = 512;  // 2 buffers x 7 levels x 32 columns = 448, allocated as 512
-constexpr int OZ_BITS = 7;
-constexpr int OZ_FRAC = OZ_S * OZ_BITS;  // 49 bits below the scale
+constexpr uint32_t OZ_TMEM_COLS = 512;  // 2 buffers x 6 levels x 32 columns = 384, allocated as 512
+constexpr int OZ_BITS = 8;
+constexpr int OZ_FRAC = OZ_S * OZ_BITS;  // 48 bits below an operand row's scale
+constexpr int OZ_FRAC_P = OZ_FRAC - 1;   // 47 below P's (its top slice then stays within 128)
 constexpr int OZ_GROUP = 4;              // k-blocks (32 values each) a TMEM buffer accumulates before a drain
 static_assert(2 * OZ_S * OZ_BN <= (int)OZ_TMEM_COLS, "level accumulators exceed the TMEM allocation");
 static_assert(OZ_SMEM <= 227 * 1024, "pipeline stages exceed the shared memory of a CTA");
@@ -125,22 +130,23 @@ namespace {
 // rexp[r] = e_r; OZ_EXP_ZERO for a row of zeros (or below 1e-250: its slices
 // are zero), OZ_EXP_NONFINITE for a row with NaN or Inf (its first slice
 // carries them, so the products and the result of the row are NaN).
-// Slices of one value below the scale: t = round(x 2^(49 - e)) as 7-bit integers,
-// extracted from the two 32-bit halves of |t| (bits 21-48 and 0-20).
+// Balanced base-256 digits of one value below the scale: t = round(x 2^(48 - e)),
+// |t| <= 2^48, split once as t = hi 2^24 + lo with lo in [-2^23, 2^23), then each
+// half cut in 32-bit arithmetic: d = ((v + 128) & 255) - 128, v = (v - d) / 256.
+// The last digit of each half takes the rest: |a_3| <= 128, |a_0| <= 256.
 __device__ __forceinline__ void oz_cut(double x, double scale, float (&a)[OZ_S]) {
     const long long t = __double2ll_rn(x * scale);  // exact power-of-two scaling, one rounding
-    const unsigned long long u = (unsigned long long)(t < 0 ? -t : t);
-    const float sg = t < 0 ? -1.f : 1.f;
-    const uint32_t hi = (uint32_t)(u >> 21), lo = (uint32_t)(u & 0x1FFFFFu);
-    a[0] = sg * (float)(hi >> 21);  // up to 128 (t rounded up to 2^49)
-    a[1] = sg * (float)((hi >> 14) & 127u);
-    a[2] = sg * (float)((hi >> 7) & 127u);
-    a[3] = sg * (float)(hi & 127u);
-    a[4] = sg * (float)(lo >> 14);
-    a[5] = sg * (float)((lo >> 7) & 127u);
-    a[6] = sg * (float)(lo & 127u);
+    int lo = (int)(((t + (1ll << 23)) & ((1ll << 24) - 1)) - (1ll << 23));
+    int hi = (int)((t - lo) >> 24);
+    int d;
+    d = ((lo + 128) & 255) - 128, a[5] = (float)d, lo = (lo - d) >> 8;
+    d = ((lo + 128) & 255) - 128, a[4] = (float)d, lo = (lo - d) >> 8;
+    a[3] = (float)lo;
+    d = ((hi + 128) & 255) - 128, a[2] = (float)d, hi = (hi - d) >> 8;
+    d = ((hi + 128) & 255) - 128, a[1] = (float)d, hi = (hi - d) >> 8;
+    a[0] = (float)hi;
 }
-static_assert(OZ_S == 7 && OZ_BITS == 7, "oz_cut is written for seven 7-bit slices");
+static_assert(OZ_S == 6 && OZ_BITS == 8, "oz_cut is written for six balanced 8-bit slices");
 
 __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ A, long long rows, int n, int ld,
                                                       int* __restrict__ rexp, OzPlanes out) {
@@ -176,7 +182,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
             code = e;
         }
         if (lane == 0) rexp[r] = code;
-        const double scale = pow2(OZ_FRAC - e);  // x * scale = t, |t| <= 2^49
+        const double scale = pow2(OZ_FRAC - e);  // x * scale = t, |t| <= 2^48
         const long long o0 = r * ld;
         auto cut = [&](double x, float (&a)[OZ_S]) {
             if (code == OZ_EXP_NONFINITE) {
@@ -379,22 +385,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
                 const int mh = mm / p.n, ml = mm - mh * p.n;
                 const int code = p.rexp[grow];
                 const bool nan_out = code == OZ_EXP_NONFINITE;
-                const double scale = pow2((code == OZ_EXP_ZERO || nan_out ? 0 : code) + p.p_exp - 4 * OZ_BITS);
+                // 2^(e_r - 48) 2^(e_P - 47) 2^40 (sum_l S_l 2^(8 (5 - l)))
+                const double scale =
+                    pow2((code == OZ_EXP_ZERO || nan_out ? 0 : code) + p.p_exp - OZ_FRAC - OZ_FRAC_P + 5 * OZ_BITS);
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
                     const int nn = tn * OZ_BN + half * 16 + c;
                     if (nn >= p.n) continue;
-                    long long G[(OZ_S + 2) / 3];  // three levels per group (7 bits apart), exact in int64
-#pragma unroll
-                    for (int g = 0; g < (OZ_S + 2) / 3; ++g) {
-                        G[g] = 0;
-#pragma unroll
-                        for (int j = 0; j < 3; ++j)
-                            if (3 * g + j < OZ_S) G[g] += (long long)acc[3 * g + j][c] << (OZ_BITS * (2 - j));
-                    }
-                    double v = (double)G[(OZ_S + 2) / 3 - 1];
-#pragma unroll
-                    for (int g = (OZ_S + 2) / 3 - 2; g >= 0; --g) v = fma(v, pow2(-3 * OZ_BITS), (double)G[g]);
+                    // levels in pairs 8 bits apart, then J = H_0 2^16 + H_1: all exact in int64
+                    const long long H0 = (long long)acc[0][c] * 256 + acc[1][c];
+                    const long long H1 = (long long)acc[2][c] * 256 + acc[3][c];
+                    const long long H2 = (long long)acc[4][c] * 256 + acc[5][c];
+                    const long long J = H0 * 65536 + H1;
+                    double v = fma((double)J, pow2(2 * OZ_BITS), (double)H2);
                     v *= scale;
                     if (nan_out) v = __longlong_as_double(0x7ff8000000000000ll);
                     p.e.apply(b, mh, ml, nn, v);
@@ -473,9 +476,10 @@ cudaError_t oz_maps_create(OzMaps** out, int M, int n, int nbatch, int ld, void*
 
 void oz_maps_destroy(OzMaps* m) { delete m; }
 
-// P's slices below its scale 2^e_P > max |P| (returned), each value rounded once
-// to 49 bits below the scale and cut into 7-bit integers, as BF16 bit patterns
-// (exact: |a_i| <= 128).
+// P's slices below its scale 2^e_P > max |P| (returned): each value rounded once
+// to t = round(p 2^(47 - e_P)), |t| <= 2^47, and cut into six balanced base-256
+// digits (the last one |p_0| <= 128), as BF16 bit patterns (exact: integers of at
+// most 8 significant bits).
 int oz_slice_host(const double* P, int n, int ld, uint16_t* const planes[OZ_S]) {
     double pmax = 0.0;
     for (size_t i = 0; i < (size_t)n * n; ++i) pmax = fabs(P[i]) > pmax ? fabs(P[i]) : pmax;
@@ -483,14 +487,17 @@ int oz_slice_host(const double* P, int n, int ld, uint16_t* const planes[OZ_S]) 
     frexp(pmax, &ep);
     for (int r = 0; r < n; ++r)
         for (int k = 0; k < n; ++k) {
-            const double x = P[(size_t)r * n + k];
-            const long long t = llrint(ldexp(x, OZ_FRAC - ep));
-            const unsigned long long u = (unsigned long long)(t < 0 ? -t : t);
+            long long t = llrint(ldexp(P[(size_t)r * n + k], OZ_FRAC_P - ep));
+            float dig[OZ_S];
+            for (int i = OZ_S - 1; i > 0; --i) {
+                const long long d = ((t + 128) & 255) - 128;
+                dig[i] = (float)d;
+                t = (t - d) / 256;  // exact: t - d is a multiple of 256
+            }
+            dig[0] = (float)t;
             for (int i = 0; i < OZ_S; ++i) {
-                const unsigned long long d = u >> (OZ_BITS * (OZ_S - 1 - i));
-                const float v = (t < 0 ? -1.f : 1.f) * (float)(i == 0 ? d : (d & ((1ull << OZ_BITS) - 1)));
                 uint32_t bits;
-                memcpy(&bits, &v, 4);
+                memcpy(&bits, &dig[i], 4);
                 planes[i][(size_t)r * ld + k] = (uint16_t)(bits >> 16);  // exact: at most 8 significant bits
             }
         }

@@ -10,7 +10,7 @@ returned field is set by the transforms:
   fp32    4 sqrt(n) 2^-24       FP32 round-to-nearest sums of n terms in each output pass
   tf32    3e-3                  one TF32 product: 11-bit operands (2^-11 = 4.9e-4 per pass)
   bf16x6  1e-6                  three BF16 pieces (24 bits) in every pass
-  fp64split 1e-10               FP64 fields; products of six 7-bit slices, exact accumulation
+  fp64split 1e-10               FP64 fields; products of six balanced 8-bit slices, exact accumulation
   bf16x3  3e-6                  two BF16 pieces (16 bits, 2^-17 = 7.6e-6 per operand) in the
                                 per-step passes, reaching the state through tau f: over the
                                 N tau <= 0.2 of these runs <= 0.2 * 7.6e-6 on top of the 1e-6 bar
