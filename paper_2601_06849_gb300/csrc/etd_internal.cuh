@@ -656,16 +656,20 @@ const char* tc_last_driver_error();
 constexpr int OZ_S = 6;
 constexpr int OZ_MAX_N = 16384;  // K <= 16384 keeps the int32 level sums exact
 constexpr int OZ_PAIRS = OZ_S * (OZ_S + 1) / 2;  // slice products per MMA tile and k-step
-struct OzMaps;  // opaque holder of the slice planes' tensor maps (ozaki.cu)
-cudaError_t oz_maps_create(OzMaps** out, int M, int n, int nbatch, int ld, void* const slices[OZ_S],
-                           void* const pslices[OZ_S]);
-void oz_maps_destroy(OzMaps* m);
-// P's slices on the host (n x n, written into planes of pitch ld); returns P's
-// scale exponent e_P (max |P| < 2^e_P)
-int oz_slice_host(const double* P, int n, int ld, uint16_t* const planes[OZ_S]);
-// The pass: A's row scales into rexp (nbatch * M ints) and its slices into
-// `slices`, then the products and the epilogue.
-cudaError_t launch_ozaki_pass(const OzMaps* maps, int p_exp, const double* A, int M, int n, int nbatch, int ld,
+constexpr int OZ_TILE_ROWS_A = 128;  // rows of an operand slice tile (the MMA's M)
+constexpr int OZ_TILE_ROWS_P = 32;   // rows of a P slice tile (the output tile's width)
+// Bytes of one tiled slice plane of `rows` rows of n values: tiles of tile_rows
+// rows x 32 values, the rows and the last k-block padded (padding must be zero).
+size_t oz_plane_bytes(long long rows, int n, int tile_rows);
+// Once per process, before the first pass: the product kernel's shared-memory size.
+cudaError_t oz_prepare();
+// P's slices on the host (n x n, into tiled planes of OZ_TILE_ROWS_P-row tiles,
+// zeroed by the caller); returns P's scale exponent e_P (max |P| < 2^e_P)
+int oz_slice_host(const double* P, int n, uint16_t* const planes[OZ_S]);
+// The pass: A's row scales into rexp (nbatch * M ints) and its slices into the
+// tiled planes `slices` (OZ_TILE_ROWS_A-row tiles), then the products with P's
+// tiled slice planes `pslices` and the epilogue.
+cudaError_t launch_ozaki_pass(void* const pslices[OZ_S], int p_exp, const double* A, int M, int n, int nbatch, int ld,
                               void* const slices[OZ_S], int* rexp, const Epi<double>& e, unsigned* err,
                               cudaStream_t st);
 cudaError_t launch_wait_timeout_probe(unsigned* err, double limit_ms, cudaStream_t st);

@@ -66,7 +66,6 @@ struct etd_plan {
     void* oz_slices[OZ_S] = {nullptr};  // the operand's BF16 slices (one set, refilled before every pass)
     void* oz_P[OZ_S] = {nullptr};       // P's slices
     int* oz_rexp = nullptr;             // per operand row: the slices' scale exponent
-    OzMaps* oz_maps = nullptr;
     int oz_pexp = 0;                    // P's scale exponent
     bool bf16 = false;  // BF16 operand pieces (ETD_PREC_BF16X3 / X6)
     size_t op_elem = 4; // bytes per operand-plane value
@@ -242,7 +241,6 @@ void free_plan(etd_plan* p) {
         if (p->oz_P[i]) cudaFree(p->oz_P[i]);
     }
     if (p->oz_rexp) cudaFree(p->oz_rexp);
-    if (p->oz_maps) oz_maps_destroy(p->oz_maps);
     for (auto& tl : p->timed) {
         cudaEventDestroy(tl.a);
         cudaEventDestroy(tl.b);
@@ -323,7 +321,7 @@ etd_status run_pass(etd_plan* p, int cur, int slot, int mode, int out_split, voi
     TimerScope ts(p, slot == p->out_slot && p->out_slot != 0 ? 2 : 0);
     if constexpr (sizeof(T) == 8) {
         if (p->ozaki) {
-            cudaError_t ce = launch_ozaki_pass(p->oz_maps, p->oz_pexp, (const double*)p->op[cur][0], p->M, p->n,
+            cudaError_t ce = launch_ozaki_pass(p->oz_P, p->oz_pexp, (const double*)p->op[cur][0], p->M, p->n,
                                                p->ninst * p->ncomp, p->ld, p->oz_slices, p->oz_rexp, e, p->err,
                                                p->stream);
             if (ce != cudaSuccess) return fail(ETD_ERR_CUDA, "FP64-split pass launch: %s", cudaGetErrorString(ce));
@@ -927,8 +925,8 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     for (int j = 0; j < (p->dst || p->ozaki ? 0 : p->pieces) && s == ETD_OK; ++j) s = dalloc(p, &p->P[j], pbytes);
     // FP64-split: the operand's slice planes, P's slice planes, the scale words
     for (int i = 0; i < (p->ozaki ? OZ_S : 0) && s == ETD_OK; ++i) {
-        s = dalloc(p, &p->oz_slices[i], (size_t)nb * p->bs * 2);
-        if (s == ETD_OK) s = dalloc(p, &p->oz_P[i], (size_t)n * p->ld * 2);
+        s = dalloc(p, &p->oz_slices[i], oz_plane_bytes((long long)nb * p->M, n, OZ_TILE_ROWS_A));
+        if (s == ETD_OK) s = dalloc(p, &p->oz_P[i], oz_plane_bytes(n, n, OZ_TILE_ROWS_P));
     }
     if (s == ETD_OK && p->ozaki) s = dalloc(p, (void**)&p->oz_rexp, sizeof(int) * (size_t)nb * p->M);
     if (s == ETD_OK && p->dst) s = dalloc(p, (void**)&p->dst_tw, sizeof(float2) * (size_t)(2 * (n + 1) - 1));
@@ -961,14 +959,17 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
         ce = cudaMemcpy(p->dst_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
     }
     if (p->ozaki && ce == cudaSuccess) {
-        std::vector<uint16_t> planes((size_t)OZ_S * n * p->ld, 0);
+        // tiled planes: their padding (rows past the last, values past n) stays zero
+        const size_t pplane = oz_plane_bytes(n, n, OZ_TILE_ROWS_P) / 2;
+        std::vector<uint16_t> planes((size_t)OZ_S * pplane, 0);
         uint16_t* ptrs[OZ_S];
-        for (int i = 0; i < OZ_S; ++i) ptrs[i] = planes.data() + (size_t)i * n * p->ld;
-        p->oz_pexp = oz_slice_host(P.data(), n, p->ld, ptrs);
+        for (int i = 0; i < OZ_S; ++i) ptrs[i] = planes.data() + (size_t)i * pplane;
+        p->oz_pexp = oz_slice_host(P.data(), n, ptrs);
         for (int i = 0; i < OZ_S && ce == cudaSuccess; ++i)
-            ce = cudaMemcpy(p->oz_P[i], ptrs[i], (size_t)n * p->ld * 2, cudaMemcpyHostToDevice);
-        for (int i = 0; i < OZ_S && ce == cudaSuccess; ++i) ce = cudaMemset(p->oz_slices[i], 0, (size_t)nb * p->bs * 2);
-        if (ce == cudaSuccess) ce = oz_maps_create(&p->oz_maps, p->M, n, nb, p->ld, p->oz_slices, p->oz_P);
+            ce = cudaMemcpy(p->oz_P[i], ptrs[i], pplane * 2, cudaMemcpyHostToDevice);
+        for (int i = 0; i < OZ_S && ce == cudaSuccess; ++i)
+            ce = cudaMemset(p->oz_slices[i], 0, oz_plane_bytes((long long)nb * p->M, n, OZ_TILE_ROWS_A));
+        if (ce == cudaSuccess) ce = oz_prepare();
     }
     for (int j = 0; j < (p->dst || p->ozaki ? 0 : p->pieces) && ce == cudaSuccess; ++j) {
         std::vector<char> hostbuf(pbytes, 0);

@@ -41,8 +41,9 @@
 // k-block (unbalanced 8-bit slices, products up to 2^16).
 //
 // Per pass: a slicing kernel (one warp per operand row: the row's scale, then its
-// seven BF16 slice planes in the layout of the FP64 operand buffer) and the
-// product kernel, persistent (one CTA per SM walks the 128 x 32 tiles; the MMA
+// six BF16 slices, written into tiled planes: 128 rows x 32 values per tile,
+// contiguous and already in the swizzled order of the shared-memory stage) and
+// the product kernel, persistent (one CTA per SM walks the 128 x 32 tiles; the MMA
 // warp fills the two TMEM buffers with the next tile's first groups while the
 // drain warps run the previous tile's epilogue):
 //   warps 0-7  drain: per group of four k-blocks, tcgen05.ld of the seven level
@@ -50,7 +51,10 @@
 //              levels per load round trip), integer sums; at the end the FP64
 //              result and the fused epilogue (Epi<double>, the Hadamard stages
 //              and outputs of the FP64 path);
-//   warp 8     TMA producer (one lane) and TMEM allocator;
+//   warp 8     TMA producer (one lane: per k-block twelve untiled bulk copies,
+//              one contiguous tile of each slice plane of A (8 KB) and of P
+//              (2 KB); a 2D tensor map would fetch the same bytes as 64-byte
+//              rows, twice the requests) and TMEM allocator;
 //   warp 9     MMA issuer (one lane): per k-step of 16 values, one product per A
 //              slice i with all P slices j <= 5 - i at once. The six level
 //              accumulators of a buffer are consecutive 32-column TMEM blocks and
@@ -72,15 +76,11 @@
 
 namespace etd {
 
-struct OzMaps {
-    CUtensorMap a[OZ_S];  // the operand's slice planes (box 32 values x 128 rows)
-    CUtensorMap p[OZ_S];  // P's slice planes (box 32 values x 32 rows)
-};
-
 namespace {
 
-constexpr int OZ_BM = 128;
-constexpr int OZ_BN = 32;
+constexpr int OZ_BM = OZ_TILE_ROWS_A;
+constexpr int OZ_BN = OZ_TILE_ROWS_P;
+static_assert(OZ_BM == 1 << 7 && OZ_BN == 1 << 5, "the tile offsets below take 128-row A and 32-row P tiles");
 constexpr int OZ_KV = 32;   // BF16 values of K per pipeline stage (one k-block)
 constexpr int OZ_ROW = 64;  // bytes of K per operand row in a stage
 constexpr int OZ_A_BYTES = OZ_BM * OZ_ROW;
@@ -105,6 +105,9 @@ struct OzPlanes {
 };
 
 struct OzParams {
+    const uint8_t* a[OZ_S];  // the operand's slice planes, tiles of OZ_BM rows x 32 values
+    const uint8_t* b[OZ_S];  // P's slice planes, tiles of OZ_BN rows x 32 values
+    int nkb;                 // k-blocks of 32 values per row: ceil(n / 32)
     int M, n, nbatch, tiles_m, tiles_n;
     int p_exp;                       // P's scale exponent e_P
     const int* rexp;                 // per row of the stacked entries: its scale exponent or code
@@ -119,17 +122,33 @@ __device__ __forceinline__ double pow2(int k) { return __longlong_as_double((lon
 constexpr int OZ_EXP_ZERO = -4096;       // row of zeros: zero slices, zero result
 constexpr int OZ_EXP_NONFINITE = 4096;   // row with NaN or Inf: NaN result
 
+// Untiled bulk copy of `bytes` contiguous bytes from global to shared memory,
+// completing on the mbarrier at `bar` (both addresses 16-byte aligned, bytes a
+// multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
 }  // namespace
+
+// Element offset of value k of row r in a tiled slice plane. A plane is a
+// sequence of tiles of 2^rows_log2 rows x 32 values (64-byte rows), ordered by
+// (row block, k-block); inside a tile the 16-byte chunk c of row rr sits at chunk
+// c ^ ((rr >> 1) & 3): the 64-byte swizzle of the shared-memory operand layout
+// the MMA reads. One untiled bulk copy then brings a tile into a 1024-byte
+// aligned pipeline stage as it is. Values past n in the last k-block and rows
+// past the last one stay zero (the planes are cleared once when allocated).
+__host__ __device__ __forceinline__ long long oz_tile_off(long long r, int k, int nkb, int rows_log2) {
+    const long long rb = r >> rows_log2;
+    const int rr = (int)(r & ((1 << rows_log2) - 1));
+    const int kb = k >> 5, kc = (k >> 3) & 3, e = k & 7;
+    return ((rb * nkb + kb) << (rows_log2 + 5)) + rr * 32 + ((kc ^ ((rr >> 1) & 3)) << 3) + e;
+}
 
 namespace {
 
-// The seven BF16 slice planes of A and each row's scale exponent, one warp per
-// row of the stacked batch entries (row r at r * ld; only its n values are
-// written, TMA reads zeros beyond): the warp reduces max |x| over the row, then
-// cuts every value below 2^e_r > max |x| (the row is read again from L1/L2).
-// rexp[r] = e_r; OZ_EXP_ZERO for a row of zeros (or below 1e-250: its slices
-// are zero), OZ_EXP_NONFINITE for a row with NaN or Inf (its first slice
-// carries them, so the products and the result of the row are NaN).
 // Balanced base-256 digits of one value below the scale: t = round(x 2^(48 - e)),
 // |t| <= 2^48, split once as t = hi 2^24 + lo with lo in [-2^23, 2^23), then each
 // half cut in 32-bit arithmetic: d = ((v + 128) & 255) - 128, v = (v - d) / 256.
@@ -148,8 +167,16 @@ __device__ __forceinline__ void oz_cut(double x, double scale, float (&a)[OZ_S])
 }
 static_assert(OZ_S == 6 && OZ_BITS == 8, "oz_cut is written for six balanced 8-bit slices");
 
+// The six BF16 slice planes of A (tiled, 128-row tiles) and each row's scale
+// exponent, one warp per row of the stacked batch entries (row r at r * ld; its
+// n values are written, the tiles' padding stays zero): the warp reduces max |x|
+// over the row, then cuts every value below 2^e_r > max |x| (the row is read
+// again from L1/L2).
+// rexp[r] = e_r; OZ_EXP_ZERO for a row of zeros (or below 1e-250: its slices
+// are zero), OZ_EXP_NONFINITE for a row with NaN or Inf (its first slice
+// carries them, so the products and the result of the row are NaN).
 __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ A, long long rows, int n, int ld,
-                                                      int* __restrict__ rexp, OzPlanes out) {
+                                                      int nkb, int* __restrict__ rexp, OzPlanes out) {
     const int lane = threadIdx.x & 31;
     const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
     const int npair = n >> 1;  // value pairs per row (rows start on even elements: ld is a multiple of 8)
@@ -183,7 +210,6 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
         }
         if (lane == 0) rexp[r] = code;
         const double scale = pow2(OZ_FRAC - e);  // x * scale = t, |t| <= 2^48
-        const long long o0 = r * ld;
         auto cut = [&](double x, float (&a)[OZ_S]) {
             if (code == OZ_EXP_NONFINITE) {
 #pragma unroll
@@ -201,15 +227,17 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
             float a[OZ_S], b[OZ_S];
             cut(v.x, a);
             cut(v.y, b);
+            const long long o = oz_tile_off(r, 2 * k, nkb, 7);  // values 2k, 2k + 1: one 4-byte word
 #pragma unroll
-            for (int i = 0; i < OZ_S; ++i)  // exact: |a_i| <= 128
-                reinterpret_cast<__nv_bfloat162*>(out.s[i] + o0)[k] = __floats2bfloat162_rn(a[i], b[i]);
+            for (int i = 0; i < OZ_S; ++i)  // exact: integers of at most 8 significant bits
+                *reinterpret_cast<__nv_bfloat162*>(out.s[i] + o) = __floats2bfloat162_rn(a[i], b[i]);
         }
         if ((n & 1) && lane == 0) {
             float a[OZ_S];
             cut(row[n - 1], a);
+            const long long o = oz_tile_off(r, n - 1, nkb, 7);
 #pragma unroll
-            for (int i = 0; i < OZ_S; ++i) out.s[i][o0 + n - 1] = __float2bfloat16_rn(a[i]);
+            for (int i = 0; i < OZ_S; ++i) out.s[i][o] = __float2bfloat16_rn(a[i]);
         }
     }
 }
@@ -218,7 +246,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
 
 namespace {
 
-__global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_constant__ OzMaps maps, const OzParams p) {
+__global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_constant__ OzParams p) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ int s_skip;
     __shared__ uint32_t s_tmem;
@@ -279,7 +307,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
         for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
             int tm, tn;
             tile_coords(t, p.tiles_m, p.tiles_n, 8, tm, tn);
-            const int arow = tm * OZ_BM, prow = tn * OZ_BN;
             for (int q = 0; q < nk; ++q, ++gq) {
                 const int s = gq % OZ_STAGES;
                 if (!mbar_wait(bar_empty + 8 * s, (uint32_t)(((gq / OZ_STAGES) & 1) ^ 1), abort_flag, p.err)) {
@@ -289,12 +316,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
                 const uint32_t st = smem_u32(smem + (size_t)s * OZ_STAGE_BYTES);
                 const uint32_t fb = bar_full + 8 * s;
                 mbar_expect_tx(fb, (uint32_t)OZ_STAGE_BYTES);
-                const int k0 = q * OZ_KV;
+                const size_t ta = ((size_t)tm * p.nkb + q) * OZ_A_BYTES, tb = ((size_t)tn * p.nkb + q) * OZ_B_BYTES;
 #pragma unroll
-                for (int i = 0; i < OZ_S; ++i) tma_load_2d(st + (uint32_t)(i * OZ_A_BYTES), &maps.a[i], fb, k0, arow);
+                for (int i = 0; i < OZ_S; ++i) bulk_load(st + (uint32_t)(i * OZ_A_BYTES), p.a[i] + ta, OZ_A_BYTES, fb);
 #pragma unroll
                 for (int j = 0; j < OZ_S; ++j)
-                    tma_load_2d(st + (uint32_t)(OZ_S * OZ_A_BYTES + j * OZ_B_BYTES), &maps.p[j], fb, k0, prow);
+                    bulk_load(st + (uint32_t)(OZ_S * OZ_A_BYTES + j * OZ_B_BYTES), p.b[j] + tb, OZ_B_BYTES, fb);
                 s_issued = gq + 1;
             }
         }
@@ -431,60 +458,32 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
     }
 }
 
-// One 2D tensor map of a BF16 slice plane: inner dimension n (values), `rows`
-// rows of pitch ld values, box of 32 values (64 bytes, 64-byte swizzle) x box_rows.
-bool oz_map(CUtensorMap* map, const void* base, int n, long long rows, int ld, int box_rows) {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    cuuint32_t box[2] = {(cuuint32_t)OZ_KV, (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 }  // namespace
 
-cudaError_t oz_maps_create(OzMaps** out, int M, int n, int nbatch, int ld, void* const slices[OZ_S],
-                           void* const pslices[OZ_S]) {
-    *out = nullptr;
-    OzMaps* m = new OzMaps();
-    bool ok = true;
-    for (int i = 0; i < OZ_S && ok; ++i) {
-        ok = oz_map(&m->a[i], slices[i], n, (long long)nbatch * M, ld, OZ_BM);
-        ok = ok && oz_map(&m->p[i], pslices[i], n, n, ld, OZ_BN);
-    }
-    if (!ok) {
-        delete m;
-        return cudaErrorInvalidValue;
-    }
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute((const void*)ozaki_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             OZ_SMEM);
-        if (e != cudaSuccess) {
-            delete m;
-            return e;
-        }
-        attr_set = true;
-    }
-    *out = m;
-    return cudaSuccess;
+size_t oz_plane_bytes(long long rows, int n, int tile_rows) {
+    return (size_t)((rows + tile_rows - 1) / tile_rows) * (size_t)((n + OZ_KV - 1) / OZ_KV) * (size_t)tile_rows * OZ_ROW;
 }
 
-void oz_maps_destroy(OzMaps* m) { delete m; }
+cudaError_t oz_prepare() {
+    static bool attr_set = false;
+    if (attr_set) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute((const void*)ozaki_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    attr_set = e == cudaSuccess;
+    return e;
+}
 
 // P's slices below its scale 2^e_P > max |P| (returned): each value rounded once
 // to t = round(p 2^(47 - e_P)), |t| <= 2^47, and cut into six balanced base-256
 // digits (the last one |p_0| <= 128), as BF16 bit patterns (exact: integers of at
-// most 8 significant bits).
-int oz_slice_host(const double* P, int n, int ld, uint16_t* const planes[OZ_S]) {
+// most 8 significant bits), in tiled planes of 32-row tiles (oz_plane_bytes(n, n,
+// 32) bytes each, cleared by the caller).
+int oz_slice_host(const double* P, int n, uint16_t* const planes[OZ_S]) {
     double pmax = 0.0;
     for (size_t i = 0; i < (size_t)n * n; ++i) pmax = fabs(P[i]) > pmax ? fabs(P[i]) : pmax;
     int ep = 0;
     frexp(pmax, &ep);
+    const int nkb = (n + OZ_KV - 1) / OZ_KV;
     for (int r = 0; r < n; ++r)
         for (int k = 0; k < n; ++k) {
             long long t = llrint(ldexp(P[(size_t)r * n + k], OZ_FRAC_P - ep));
@@ -495,30 +494,37 @@ int oz_slice_host(const double* P, int n, int ld, uint16_t* const planes[OZ_S]) 
                 t = (t - d) / 256;  // exact: t - d is a multiple of 256
             }
             dig[0] = (float)t;
+            const long long o = oz_tile_off(r, k, nkb, 5);
             for (int i = 0; i < OZ_S; ++i) {
                 uint32_t bits;
                 memcpy(&bits, &dig[i], 4);
-                planes[i][(size_t)r * ld + k] = (uint16_t)(bits >> 16);  // exact: at most 8 significant bits
+                planes[i][o] = (uint16_t)(bits >> 16);  // exact: at most 8 significant bits
             }
         }
     return ep;
 }
 
-cudaError_t launch_ozaki_pass(const OzMaps* maps, int p_exp, const double* A, int M, int n, int nbatch, int ld,
+cudaError_t launch_ozaki_pass(void* const pslices[OZ_S], int p_exp, const double* A, int M, int n, int nbatch, int ld,
                               void* const slices[OZ_S], int* rexp, const Epi<double>& e, unsigned* err,
                               cudaStream_t st) {
     OzPlanes planes;
     for (int i = 0; i < OZ_S; ++i) planes.s[i] = static_cast<__nv_bfloat16*>(slices[i]);
     const long long rows = (long long)nbatch * M;
+    const int nkb = (n + OZ_KV - 1) / OZ_KV;
     long long blocks = (rows + 7) / 8;  // one warp per row
     if (blocks > 152 * 16) blocks = 152 * 16;
-    oz_slice_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, rows, n, ld, rexp, planes);
+    oz_slice_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, rows, n, ld, nkb, rexp, planes);
     OzParams p;
+    for (int i = 0; i < OZ_S; ++i) {
+        p.a[i] = static_cast<const uint8_t*>(slices[i]);
+        p.b[i] = static_cast<const uint8_t*>(pslices[i]);
+    }
+    p.nkb = nkb;
     p.M = M;
     p.n = n;
     p.nbatch = nbatch;
     p.p_exp = p_exp;
-    p.tiles_m = (int)(((long long)nbatch * M + OZ_BM - 1) / OZ_BM);
+    p.tiles_m = (int)((rows + OZ_BM - 1) / OZ_BM);
     p.tiles_n = (n + OZ_BN - 1) / OZ_BN;
     p.rexp = rexp;
     p.err = err;
@@ -531,7 +537,7 @@ cudaError_t launch_ozaki_pass(const OzMaps* maps, int p_exp, const double* A, in
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
     }
     const long long ntiles = (long long)p.tiles_m * p.tiles_n;
-    ozaki_pass_kernel<<<(unsigned)(ntiles < sms ? ntiles : sms), OZ_THREADS, OZ_SMEM, st>>>(*maps, p);
+    ozaki_pass_kernel<<<(unsigned)(ntiles < sms ? ntiles : sms), OZ_THREADS, OZ_SMEM, st>>>(p);
     return cudaGetLastError();
 }
 
