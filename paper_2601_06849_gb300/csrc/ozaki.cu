@@ -120,6 +120,11 @@ __device__ __forceinline__ double pow2(int k) { return __longlong_as_double((lon
 
 // Row exponent codes besides a finite scale exponent (|e| < 1100).
 constexpr int OZ_EXP_ZERO = -4096;       // row of zeros: zero slices, zero result
+constexpr int OZ_BEXP_MIN = 193;         // rows with max |x| < 2^-830 count as zero rows
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
 constexpr int OZ_EXP_NONFINITE = 4096;   // row with NaN or Inf: NaN result
 
 // Untiled bulk copy of `bytes` contiguous bytes from global to shared memory,
@@ -149,12 +154,34 @@ __host__ __device__ __forceinline__ long long oz_tile_off(long long r, int k, in
 
 namespace {
 
-// Balanced base-256 digits of one value below the scale: t = round(x 2^(48 - e)),
-// |t| <= 2^48, split once as t = hi 2^24 + lo with lo in [-2^23, 2^23), then each
-// half cut in 32-bit arithmetic: d = ((v + 128) & 255) - 128, v = (v - d) / 256.
-// The last digit of each half takes the rest: |a_3| <= 128, |a_0| <= 256.
-__device__ __forceinline__ void oz_cut(double x, double scale, float (&a)[OZ_S]) {
-    const long long t = __double2ll_rn(x * scale);  // exact power-of-two scaling, one rounding
+// FP64 arithmetic runs at about two operations per clock and SM on this GPU, 64
+// times slower than FP32; the slicing is integer arithmetic on the bit patterns
+// instead (an integer-only forming of the result in the product kernel's
+// epilogue measured slower than its four FP64 operations, and was dropped).
+//
+// t = round(x 2^(48 - e)) to nearest, ties to even, for |x| < 2^e, from the bits of
+// x: x = m 2^(b - 1075) (m with its implicit bit, b the biased exponent, 1 for a
+// subnormal), so t = m 2^-sh with sh = 1027 + e - b >= 5.
+__device__ __forceinline__ long long oz_round_scaled(unsigned long long bits, int e) {
+    const int b = (int)((bits >> 52) & 0x7FF);
+    unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+    const int bb = b == 0 ? 1 : b;
+    if (b != 0) m |= 1ull << 52;
+    const int sh = 1027 + e - bb;
+    unsigned long long q = 0;
+    if (sh < 64) {
+        q = m >> sh;
+        const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        q += (rem > half || (rem == half && (q & 1))) ? 1 : 0;
+    }
+    return (bits >> 63) ? -(long long)q : (long long)q;
+}
+
+// Balanced base-256 digits of t (|t| <= 2^48), split once as t = hi 2^24 + lo
+// with lo in [-2^23, 2^23), then each half cut in 32-bit arithmetic:
+// d = ((v + 128) & 255) - 128, v = (v - d) / 256. The last digit of each half
+// takes the rest: |a_3| <= 128, |a_0| <= 256.
+__device__ __forceinline__ void oz_cut(long long t, float (&a)[OZ_S]) {
     int lo = (int)(((t + (1ll << 23)) & ((1ll << 24) - 1)) - (1ll << 23));
     int hi = (int)((t - lo) >> 24);
     int d;
@@ -172,7 +199,7 @@ static_assert(OZ_S == 6 && OZ_BITS == 8, "oz_cut is written for six balanced 8-b
 // n values are written, the tiles' padding stays zero): the warp reduces max |x|
 // over the row, then cuts every value below 2^e_r > max |x| (the row is read
 // again from L1/L2).
-// rexp[r] = e_r; OZ_EXP_ZERO for a row of zeros (or below 1e-250: its slices
+// rexp[r] = e_r; OZ_EXP_ZERO for a row of zeros (or max below 2^-830: its slices
 // are zero), OZ_EXP_NONFINITE for a row with NaN or Inf (its first slice
 // carries them, so the products and the result of the row are NaN).
 __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ A, long long rows, int n, int ld,
@@ -183,43 +210,44 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
     for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += wstride) {
         const double* row = A + r * ld;
         const double2* row2 = reinterpret_cast<const double2*>(row);
-        double m = 0.0;
-        bool bad = false;
+        // max |x| over the row on the bit patterns (their order is that of |x|)
+        unsigned long long mb = 0;
         for (int k = lane; k < npair; k += 32) {
             const double2 v = row2[k];
-            const double a = fabs(v.x), b = fabs(v.y);
-            bad |= !(a <= 1.7976931348623157e308) || !(b <= 1.7976931348623157e308);
-            m = fmax(m, fmax(a, b));
+            const unsigned long long a = abs_bits(v.x), b = abs_bits(v.y);
+            mb = a > mb ? a : mb;
+            mb = b > mb ? b : mb;
         }
         if ((n & 1) && lane == 0) {
-            const double a = fabs(row[n - 1]);
-            bad |= !(a <= 1.7976931348623157e308);
-            m = fmax(m, a);
+            const unsigned long long a = abs_bits(row[n - 1]);
+            mb = a > mb ? a : mb;
         }
-        for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-        bad = __any_sync(0xffffffffu, bad);
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, mb, off);
+            mb = o > mb ? o : mb;
+        }
+        const int bmax = (int)(mb >> 52);  // biased exponent of the row's max
         int e = 0;
         int code;
-        if (bad) {
-            code = OZ_EXP_NONFINITE;
-        } else if (m < 1e-250) {
+        if (bmax == 0x7FF) {
+            code = OZ_EXP_NONFINITE;  // NaN or Inf in the row
+        } else if (bmax < OZ_BEXP_MIN) {
             code = OZ_EXP_ZERO;
         } else {
-            frexp(m, &e);
+            e = bmax - 1022;  // max |x| < 2^e (frexp's exponent of the max)
             code = e;
         }
         if (lane == 0) rexp[r] = code;
-        const double scale = pow2(OZ_FRAC - e);  // x * scale = t, |t| <= 2^48
         auto cut = [&](double x, float (&a)[OZ_S]) {
             if (code == OZ_EXP_NONFINITE) {
 #pragma unroll
                 for (int i = 0; i < OZ_S; ++i) a[i] = 0.f;
-                if (!(fabs(x) <= 1.7976931348623157e308)) a[0] = (float)x;  // NaN / Inf into the products
+                if ((abs_bits(x) >> 52) == 0x7FF) a[0] = (float)x;  // NaN / Inf into the products
             } else if (code == OZ_EXP_ZERO) {
 #pragma unroll
                 for (int i = 0; i < OZ_S; ++i) a[i] = 0.f;
             } else {
-                oz_cut(x, scale, a);
+                oz_cut(oz_round_scaled((unsigned long long)__double_as_longlong(x), e), a);
             }
         };
         for (int k = lane; k < npair; k += 32) {
