@@ -106,3 +106,15 @@ def test_options_defaults_and_diag_validation(lib):
         etd.etd_plan_create(2, 64, 0.1, 0.0, 1e-3, 2, o)
     assert ei.value.status == etd.ETD_ERR_INVALID_ARG
 
+
+
+def test_fp64split_size_limit_rejected_before_device_work(lib):
+    """FP64-split keeps its level sums exact in int32 up to K = 16384 values
+    (128 groups of 128 products below 7 * 2^21 each), which is also the largest 2D
+    grid a plan takes: a larger one is refused before anything touches the device."""
+    o = etd.etd_options_default()
+    o.precision = etd.PRECISION["fp64split"]
+    with pytest.raises(etd.EtdError) as ei:
+        etd.etd_plan_create(2, 16385, 0.1, 0.0, 1e-3, 2, o)
+    assert ei.value.status in (etd.ETD_ERR_INVALID_ARG, etd.ETD_ERR_UNSUPPORTED)
+    assert "16384" in str(ei.value)
