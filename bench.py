@@ -63,7 +63,7 @@ WORKLOADS = {
 RUN_STEPS = {"fhn2d_4096": 1000, "fhn2d_2048": 1000, "fhn2d_4095": 1000, "ac3d_256": 200, "ac3d_384": 200,
              "ac3d_255": 200, "ac2d_64": 100, "ensemble512": 500, "adjoint3d_128": 400}
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates
-F64_PRECISIONS = ("fp64", "fp64split")  # precisions with FP64 fields
+F64_PRECISIONS = ("fp64", "fp64split", "fp64split40", "fp64split32")  # precisions with FP64 fields
 # the arithmetic each precision computes in
 DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32 (f32 fields)",
          "tf32x3": "tf32x3 (f32 fields, double-float spectral state)",
@@ -71,6 +71,8 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32 (f32 fields)",
          "bf16x3": "bf16x3 (f32 fields, double-float spectral state)",
          "bf16x6": "bf16x6 (f32 fields, double-float spectral state)",
          "fp64split": "f64 (f64 fields and state; products as 21 exact bf16 slice products)",
+         "fp64split40": "f64 (f64 fields and state; products as 15 exact bf16 slice products, 40-bit operands)",
+         "fp64split32": "f64 (f64 fields and state; products as 10 exact bf16 slice products, 32-bit operands)",
          "dst32": "f32 (fast sine transforms)"}
 # DRAM traffic records (ncu, per launch of the per-step pass) of the default
 # workload, with the kernel sources they are valid for
@@ -148,7 +150,7 @@ def run_adjoint(args, world, rank, local):
     # forward and the adjoint's 9 transforms (d passes each) per step, 2 n^(d+1) per
     # pass and component, times the split products
     products = {"fp64": 1, "fp32": 1, "tf32": 1, "tf32x3": 3, "bf16x3": 3, "bf16x6": 6, "tf32x6": 6,
-                "fp64split": 21}.get(
+                "fp64split": 21, "fp64split40": 15, "fp64split32": 10}.get(
         args.precision, 1)
     passes = window * (4 * d + 4 * d + 9 * d)
     flops = passes * 2.0 * n ** (d + 1) * 2 * products * iters
@@ -483,7 +485,7 @@ def tensor_peak(peaks, src, precision, timed_s):
     the sustained rate for longer ones; TF32 products at the nominal TF32/BF16
     ratio of it."""
     key = "bf16_tflops" if timed_s < 2.0 else "bf16_tflops_sustained"
-    bf16_mode = precision.startswith("bf16") or precision == "fp64split"  # the slices are BF16
+    bf16_mode = precision.startswith("bf16") or precision.startswith("fp64split")  # the slices are BF16
     peak = peaks[key] * (1.0 if bf16_mode else TF32_OVER_BF16)
     return peak, f"{src}: {key}" + ("" if bf16_mode else " x 1.1/2.25 (TF32/BF16 nominal)")
 
@@ -794,7 +796,7 @@ def main():
                 "frac": top["frac"], "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "kernel": ("FP64-split transform pass (oz_slice_kernel + ozaki_pass_kernel, tcgen05 BF16 slice "
-                           "products), per-step passes, mean over the step" if args.precision == "fp64split" else
+                           "products), per-step passes, mean over the step" if args.precision.startswith("fp64split") else
                            "tcgen05 transform pass (per-step passes, mean over the step)"),
                 "peak_source": top["peak_source"], "avg_launch_ms": avg_gemm_ms,
                 "tensor": tens, "hbm": hbm}

@@ -15,7 +15,7 @@
  * Conventions shared by every call:
  *   - Field layout: [comp][z][y][x], x fastest, contiguous, no boundary values
  *     (the Dirichlet zeros are implicit; Section 2.1 vectorisation order).
- *     Element type: double for ETD_PREC_FP64 and ETD_PREC_FP64_SPLIT, float for every
+ *     Element type: double for ETD_PREC_FP64 and the FP64-split precisions, float for every
  *     other precision.
  *   - Device pointers must be 16-byte aligned device memory of at least
  *     n_comp * n^d elements; host pointers any host memory of that size.
@@ -62,10 +62,14 @@ enum {
                             in FP32 on CUDA cores) instead of the dense product with P: a
                             comparison path, not the paper's dense-eigenbasis method; needs
                             m + 1 a power of two, 16 <= m + 1 <= 8192 */
-    ETD_PREC_FP64_SPLIT = 8 /* double fields and state; every product with P in FP64 accuracy on the
+    ETD_PREC_FP64_SPLIT = 8, /* double fields and state; every product with P in FP64 accuracy on the
                             BF16 tensor cores: each operand row cut into six balanced 8-bit integer
                             slices below a power-of-two scale (P likewise), the 21 slice products of
                             weight >= 2^-40 accumulated exactly, the result formed in FP64 */
+    ETD_PREC_FP64_SPLIT40 = 9, /* as ETD_PREC_FP64_SPLIT with five slices (40 bits below each row's
+                            scale, 15 slice products): about 2^-40 relative error per product
+                            instead of 2^-48, for results held to 1e-6 rather than 1e-10 */
+    ETD_PREC_FP64_SPLIT32 = 10 /* four slices (32 bits, 10 slice products): about 2^-32 per product */
 };
 /* In every split mode (X3, X6) the two transforms whose error stays in the
  * result, U -> U^ when the carried spectral state is (re)built and the
@@ -138,8 +142,8 @@ typedef struct {
 /* Performance-relevant facts of a plan (for benchmarks and roofline figures). */
 typedef struct {
     int d, n, n_comp, precision;
-    int products;                /* tensor-core products per MMA tile (1, 3, 6, or 21 slice products for
-                                    ETD_PREC_FP64_SPLIT; 0 for CUDA cores) */
+    int products;                /* tensor-core products per MMA tile (1, 3, 6, or 21 / 15 / 10 slice products for
+                                    ETD_PREC_FP64_SPLIT / _SPLIT40 / _SPLIT32; 0 for CUDA cores) */
     int gemms_per_step;          /* transform passes per time step (8 in 2D, 12 in 3D) */
     long long unknowns;          /* n_comp * n^d */
     double gemm_flops;           /* algorithmic flops of one pass, all components: 2 n^(d+1) n_comp */

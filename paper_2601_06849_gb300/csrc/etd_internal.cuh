@@ -650,12 +650,13 @@ cudaError_t launch_gemm_tc(const TcConfig& cfg, int slot, const TcMaps* maps, in
                            const Epi<float>& e, unsigned* err, cudaStream_t st);
 const char* tc_last_driver_error();
 
-// ETD_PREC_FP64_SPLIT transform pass (ozaki.cu): FP64 operands cut into OZ_S
-// balanced 8-bit digits (BF16 slices) below a per-row power-of-two scale, exact
-// slice products on the tensor cores, FP64 result through the Epi<double> epilogue.
-constexpr int OZ_S = 6;
+// ETD_PREC_FP64_SPLIT (6 slices), _SPLIT40 (5) and _SPLIT32 (4) transform pass
+// (ozaki.cu): FP64 operands cut into balanced 8-bit digits (BF16 slices) below a
+// per-row power-of-two scale, exact slice products on the tensor cores, FP64 result
+// through the Epi<double> epilogue.
+constexpr int OZ_S = 6;          // the most slices a precision uses (planes allocated per plan: its own count)
 constexpr int OZ_MAX_N = 16384;  // K <= 16384 keeps the int32 level sums exact
-constexpr int OZ_PAIRS = OZ_S * (OZ_S + 1) / 2;  // slice products per MMA tile and k-step
+int oz_pairs(int s);             // slice products per MMA tile and k-step: s (s + 1) / 2
 constexpr int OZ_TILE_ROWS_A = 128;  // rows of an operand slice tile (the MMA's M)
 constexpr int OZ_TILE_ROWS_P = 32;   // rows of a P slice tile (the output tile's width)
 // Bytes of one tiled slice plane of `rows` rows of n values: tiles of tile_rows
@@ -665,13 +666,13 @@ size_t oz_plane_bytes(long long rows, int n, int tile_rows);
 cudaError_t oz_prepare();
 // P's slices on the host (n x n, into tiled planes of OZ_TILE_ROWS_P-row tiles,
 // zeroed by the caller); returns P's scale exponent e_P (max |P| < 2^e_P)
-int oz_slice_host(const double* P, int n, uint16_t* const planes[OZ_S]);
+int oz_slice_host(const double* P, int n, int s, uint16_t* const planes[OZ_S]);
 // The pass: A's row scales into rexp (nbatch * M ints) and its slices into the
 // tiled planes `slices` (OZ_TILE_ROWS_A-row tiles), then the products with P's
 // tiled slice planes `pslices` and the epilogue.
-cudaError_t launch_ozaki_pass(void* const pslices[OZ_S], int p_exp, const double* A, int M, int n, int nbatch, int ld,
-                              void* const slices[OZ_S], int* rexp, const Epi<double>& e, unsigned* err,
-                              cudaStream_t st);
+cudaError_t launch_ozaki_pass(int s, void* const pslices[OZ_S], int p_exp, const double* A, int M, int n,
+                              int nbatch, int ld, void* const slices[OZ_S], int* rexp, const Epi<double>& e,
+                              unsigned* err, cudaStream_t st);
 cudaError_t launch_wait_timeout_probe(unsigned* err, double limit_ms, cudaStream_t st);
 
 }  // namespace etd

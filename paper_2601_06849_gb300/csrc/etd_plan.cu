@@ -62,7 +62,8 @@ struct etd_plan {
     bool dst = false;         // ETD_PREC_DST32: FFT-based sine transforms instead of products with P
     float2* dst_tw = nullptr; // its FFT twiddles by stage (N - 1 of them, N = 2(n+1))
     void* dst_tmp = nullptr;  // its natural-order scratch rows
-    bool ozaki = false;       // ETD_PREC_FP64_SPLIT: FP64 products as exact BF16 slice products
+    bool ozaki = false;       // ETD_PREC_FP64_SPLIT*: FP64 products as exact BF16 slice products
+    int oz_s = 0;             // its slice count (6, 5 or 4)
     void* oz_slices[OZ_S] = {nullptr};  // the operand's BF16 slices (one set, refilled before every pass)
     void* oz_P[OZ_S] = {nullptr};       // P's slices
     int* oz_rexp = nullptr;             // per operand row: the slices' scale exponent
@@ -321,7 +322,7 @@ etd_status run_pass(etd_plan* p, int cur, int slot, int mode, int out_split, voi
     TimerScope ts(p, slot == p->out_slot && p->out_slot != 0 ? 2 : 0);
     if constexpr (sizeof(T) == 8) {
         if (p->ozaki) {
-            cudaError_t ce = launch_ozaki_pass(p->oz_P, p->oz_pexp, (const double*)p->op[cur][0], p->M, p->n,
+            cudaError_t ce = launch_ozaki_pass(p->oz_s, p->oz_P, p->oz_pexp, (const double*)p->op[cur][0], p->M, p->n,
                                                p->ninst * p->ncomp, p->ld, p->oz_slices, p->oz_rexp, e, p->err,
                                                p->stream);
             if (ce != cudaSuccess) return fail(ETD_ERR_CUDA, "FP64-split pass launch: %s", cudaGetErrorString(ce));
@@ -735,9 +736,12 @@ etd_status validate_options(int d, int m, int pade_order, const etd_options& opt
         if (N < 16 || N > 8192 || (N & (N - 1)))
             return fail(ETD_ERR_UNSUPPORTED, "ETD_PREC_DST32 needs m + 1 a power of two in [16, 8192] (m = %d)", m);
     }
-    if (opt.precision == ETD_PREC_FP64_SPLIT && m > OZ_MAX_N)  // the 2D limit; exact int32 level sums up to it
-        return fail(ETD_ERR_UNSUPPORTED, "ETD_PREC_FP64_SPLIT needs m <= %d (exact level sums; m = %d)", OZ_MAX_N, m);
-    if (opt.precision < ETD_PREC_FP64 || opt.precision > ETD_PREC_FP64_SPLIT)
+    if ((opt.precision == ETD_PREC_FP64_SPLIT || opt.precision == ETD_PREC_FP64_SPLIT40 ||
+         opt.precision == ETD_PREC_FP64_SPLIT32) &&
+        m > OZ_MAX_N)  // the 2D limit; exact int32 level sums up to it
+        return fail(ETD_ERR_UNSUPPORTED, "the FP64-split precisions need m <= %d (exact level sums; m = %d)", OZ_MAX_N,
+                    m);
+    if (opt.precision < ETD_PREC_FP64 || opt.precision > ETD_PREC_FP64_SPLIT32)
         return fail(ETD_ERR_INVALID_ARG, "unknown precision");
     return ETD_OK;
 }
@@ -852,8 +856,12 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     p->stream = (cudaStream_t)opt.stream;
     p->diag_every = opt.diag_every;
     p->diag_max = opt.diag_max_abs;
-    p->elem = (opt.precision == ETD_PREC_FP64 || opt.precision == ETD_PREC_FP64_SPLIT) ? 8 : 4;
-    p->ozaki = opt.precision == ETD_PREC_FP64_SPLIT;
+    p->oz_s = opt.precision == ETD_PREC_FP64_SPLIT     ? 6
+              : opt.precision == ETD_PREC_FP64_SPLIT40 ? 5
+              : opt.precision == ETD_PREC_FP64_SPLIT32 ? 4
+                                                       : 0;
+    p->ozaki = p->oz_s > 0;
+    p->elem = (opt.precision == ETD_PREC_FP64 || p->ozaki) ? 8 : 4;
     p->bf16 = (opt.precision == ETD_PREC_BF16X3 || opt.precision == ETD_PREC_BF16X6);
     p->use_tc = p->bf16 || opt.precision == ETD_PREC_TF32 || opt.precision == ETD_PREC_TF32X3 ||
                 opt.precision == ETD_PREC_TF32X6;
@@ -924,7 +932,7 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     // the sine-transform path needs no P: its twiddles and a scratch field instead
     for (int j = 0; j < (p->dst || p->ozaki ? 0 : p->pieces) && s == ETD_OK; ++j) s = dalloc(p, &p->P[j], pbytes);
     // FP64-split: the operand's slice planes, P's slice planes, the scale words
-    for (int i = 0; i < (p->ozaki ? OZ_S : 0) && s == ETD_OK; ++i) {
+    for (int i = 0; i < (p->ozaki ? p->oz_s : 0) && s == ETD_OK; ++i) {
         s = dalloc(p, &p->oz_slices[i], oz_plane_bytes((long long)nb * p->M, n, OZ_TILE_ROWS_A));
         if (s == ETD_OK) s = dalloc(p, &p->oz_P[i], oz_plane_bytes(n, n, OZ_TILE_ROWS_P));
     }
@@ -961,13 +969,13 @@ etd_status build_plan(etd_plan** out, int d, int m, int ninst, const double* kap
     if (p->ozaki && ce == cudaSuccess) {
         // tiled planes: their padding (rows past the last, values past n) stays zero
         const size_t pplane = oz_plane_bytes(n, n, OZ_TILE_ROWS_P) / 2;
-        std::vector<uint16_t> planes((size_t)OZ_S * pplane, 0);
-        uint16_t* ptrs[OZ_S];
-        for (int i = 0; i < OZ_S; ++i) ptrs[i] = planes.data() + (size_t)i * pplane;
-        p->oz_pexp = oz_slice_host(P.data(), n, ptrs);
-        for (int i = 0; i < OZ_S && ce == cudaSuccess; ++i)
+        std::vector<uint16_t> planes((size_t)p->oz_s * pplane, 0);
+        uint16_t* ptrs[OZ_S] = {nullptr};
+        for (int i = 0; i < p->oz_s; ++i) ptrs[i] = planes.data() + (size_t)i * pplane;
+        p->oz_pexp = oz_slice_host(P.data(), n, p->oz_s, ptrs);
+        for (int i = 0; i < p->oz_s && ce == cudaSuccess; ++i)
             ce = cudaMemcpy(p->oz_P[i], ptrs[i], pplane * 2, cudaMemcpyHostToDevice);
-        for (int i = 0; i < OZ_S && ce == cudaSuccess; ++i)
+        for (int i = 0; i < p->oz_s && ce == cudaSuccess; ++i)
             ce = cudaMemset(p->oz_slices[i], 0, oz_plane_bytes((long long)nb * p->M, n, OZ_TILE_ROWS_A));
         if (ce == cudaSuccess) ce = oz_prepare();
     }
@@ -1085,7 +1093,10 @@ etd_status etd_batch_create(etd_plan** out, int count, const int* d, const int* 
     B->count = count;
     B->ncomp = opt.n_comp;
     B->precision = opt.precision;
-    B->elem = (opt.precision == ETD_PREC_FP64 || opt.precision == ETD_PREC_FP64_SPLIT) ? 8 : 4;
+    B->elem = (opt.precision == ETD_PREC_FP64 || opt.precision == ETD_PREC_FP64_SPLIT ||
+               opt.precision == ETD_PREC_FP64_SPLIT40 || opt.precision == ETD_PREC_FP64_SPLIT32)
+                  ? 8
+                  : 4;
     B->stream = (cudaStream_t)opt.stream;
     // group the instances by grid (d, n), in order of first appearance
     std::vector<std::pair<int, int>> keys;
@@ -1464,7 +1475,7 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
     info->n = p->n;
     info->n_comp = p->ncomp;
     info->precision = p->precision;
-    info->products = p->use_tc ? p->tc[0].products : (p->ozaki ? OZ_PAIRS : 0);
+    info->products = p->use_tc ? p->tc[0].products : (p->ozaki ? oz_pairs(p->oz_s) : 0);
     info->kernels_per_pass = (p->ozaki || p->dst) ? 2 : 1;
     info->gemms_per_step = 4 * p->d;
     info->unknowns = (long long)p->ninst * p->ncomp * p->npts;
@@ -1487,8 +1498,8 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
     if (p->ozaki) {
         // FP64-split: P's slices, and per pass the operand read once more (the
         // row's max before its slices), its slices written and read (2 bytes each)
-        basis = (double)p->n * p->n * 2.0 * OZ_S;
-        slicing = vals * (8.0 + 2.0 * 2.0 * OZ_S);
+        basis = (double)p->n * p->n * 2.0 * p->oz_s;
+        slicing = vals * (8.0 + 2.0 * 2.0 * p->oz_s);
     }
     const double st = 8.0, fe = (double)p->elem;
     const double pass_in = pin * opb + basis + slicing;

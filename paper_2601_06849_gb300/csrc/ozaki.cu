@@ -40,6 +40,12 @@
 // drain (TMEM loads, int32 sums) bounded the kernel when it ran after every
 // k-block (unbalanced 8-bit slices, products up to 2^16).
 //
+// Fewer slices (ETD_PREC_FP64_SPLIT40: S = 5, ETD_PREC_FP64_SPLIT32: S = 4): the
+// same scheme with t rounded to 8S bits (P: 8S - 1), S digits, levels l <= S - 1
+// (S (S + 1) / 2 pairs), out = 2^(e_r + e_P - 8S - 7) sum_l S_l 2^(8 (S - 1 - l)),
+// and smaller pipeline stages (more of them in flight); the kernels below are
+// templates on S.
+//
 // Per pass: a slicing kernel (one warp per operand row: the row's scale, then its
 // six BF16 slices, written into tiled planes: 128 rows x 32 values per tile,
 // contiguous and already in the swizzled order of the shared-memory stage) and
@@ -85,20 +91,24 @@ constexpr int OZ_KV = 32;   // BF16 values of K per pipeline stage (one k-block)
 constexpr int OZ_ROW = 64;  // bytes of K per operand row in a stage
 constexpr int OZ_A_BYTES = OZ_BM * OZ_ROW;
 constexpr int OZ_B_BYTES = OZ_BN * OZ_ROW;
-constexpr int OZ_STAGE_BYTES = OZ_S * (OZ_A_BYTES + OZ_B_BYTES);
-constexpr int OZ_STAGES = 3;
-constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024;  // + alignment slack
+// Per slice count S (6: ETD_PREC_FP64_SPLIT, 5: _SPLIT40, 4: _SPLIT32): bytes of one
+// pipeline stage, stages that fit (3 x 60 KB, 4 x 50 KB, 5 x 40 KB), dynamic shared memory.
+__host__ __device__ constexpr int oz_stage_bytes(int S) { return S * (OZ_A_BYTES + OZ_B_BYTES); }
+__host__ __device__ constexpr int oz_stages(int S) { return S == 6 ? 3 : (S == 5 ? 4 : 5); }
+__host__ __device__ constexpr int oz_smem(int S) { return oz_stages(S) * oz_stage_bytes(S) + 1024; }  // + alignment
 constexpr int OZ_DRAIN_WARPS = 8;
 constexpr int OZ_WARP_TMA = 8;
 constexpr int OZ_WARP_MMA = 9;
 constexpr int OZ_THREADS = 320;
-constexpr uint32_t OZ_TMEM_COLS = 512;  // 2 buffers x 6 levels x 32 columns = 384, allocated as 512
+constexpr uint32_t OZ_TMEM_COLS = 512;  // 2 buffers x S levels x 32 columns (at most 384), allocated as 512
 constexpr int OZ_BITS = 8;
-constexpr int OZ_FRAC = OZ_S * OZ_BITS;  // 48 bits below an operand row's scale
-constexpr int OZ_FRAC_P = OZ_FRAC - 1;   // 47 below P's (its top slice then stays within 128)
+// bits below an operand row's scale (8 S: 48, 40 or 32); P takes one bit less, so that
+// its top slice stays within 128
+__host__ __device__ constexpr int oz_frac(int S) { return S * OZ_BITS; }
 constexpr int OZ_GROUP = 4;              // k-blocks (32 values each) a TMEM buffer accumulates before a drain
 static_assert(2 * OZ_S * OZ_BN <= (int)OZ_TMEM_COLS, "level accumulators exceed the TMEM allocation");
-static_assert(OZ_SMEM <= 227 * 1024, "pipeline stages exceed the shared memory of a CTA");
+static_assert(oz_smem(6) <= 227 * 1024 && oz_smem(5) <= 227 * 1024 && oz_smem(4) <= 227 * 1024,
+              "pipeline stages exceed the shared memory of a CTA");
 
 struct OzPlanes {
     __nv_bfloat16* s[OZ_S];
@@ -159,15 +169,16 @@ namespace {
 // instead (an integer-only forming of the result in the product kernel's
 // epilogue measured slower than its four FP64 operations, and was dropped).
 //
-// t = round(x 2^(48 - e)) to nearest, ties to even, for |x| < 2^e, from the bits of
-// x: x = m 2^(b - 1075) (m with its implicit bit, b the biased exponent, 1 for a
-// subnormal), so t = m 2^-sh with sh = 1027 + e - b >= 5.
+// t = round(x 2^(F - e)) to nearest, ties to even, for |x| < 2^e (F = 48, 40 or 32),
+// from the bits of x: x = m 2^(b - 1075) (m with its implicit bit, b the biased
+// exponent, 1 for a subnormal), so t = m 2^-sh with sh = 1075 - F + e - b >= 5.
+template <int F>
 __device__ __forceinline__ long long oz_round_scaled(unsigned long long bits, int e) {
     const int b = (int)((bits >> 52) & 0x7FF);
     unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
     const int bb = b == 0 ? 1 : b;
     if (b != 0) m |= 1ull << 52;
-    const int sh = 1027 + e - bb;
+    const int sh = 1075 - F + e - bb;
     unsigned long long q = 0;
     if (sh < 64) {
         q = m >> sh;
@@ -177,22 +188,27 @@ __device__ __forceinline__ long long oz_round_scaled(unsigned long long bits, in
     return (bits >> 63) ? -(long long)q : (long long)q;
 }
 
-// Balanced base-256 digits of t (|t| <= 2^48), split once as t = hi 2^24 + lo
+// S balanced base-256 digits of t (|t| <= 2^(8 S)), split once as t = hi 2^24 + lo
 // with lo in [-2^23, 2^23), then each half cut in 32-bit arithmetic:
 // d = ((v + 128) & 255) - 128, v = (v - d) / 256. The last digit of each half
-// takes the rest: |a_3| <= 128, |a_0| <= 256.
+// takes the rest: |a_(S-3)| <= 128, |a_0| <= 256 (hi has S - 3 digits).
+template <int S>
 __device__ __forceinline__ void oz_cut(long long t, float (&a)[OZ_S]) {
+    static_assert(S >= 4 && S <= 6 && OZ_BITS == 8, "oz_cut is written for four to six balanced 8-bit slices");
     int lo = (int)(((t + (1ll << 23)) & ((1ll << 24) - 1)) - (1ll << 23));
     int hi = (int)((t - lo) >> 24);
     int d;
-    d = ((lo + 128) & 255) - 128, a[5] = (float)d, lo = (lo - d) >> 8;
-    d = ((lo + 128) & 255) - 128, a[4] = (float)d, lo = (lo - d) >> 8;
-    a[3] = (float)lo;
-    d = ((hi + 128) & 255) - 128, a[2] = (float)d, hi = (hi - d) >> 8;
-    d = ((hi + 128) & 255) - 128, a[1] = (float)d, hi = (hi - d) >> 8;
+    d = ((lo + 128) & 255) - 128, a[S - 1] = (float)d, lo = (lo - d) >> 8;
+    d = ((lo + 128) & 255) - 128, a[S - 2] = (float)d, lo = (lo - d) >> 8;
+    a[S - 3] = (float)lo;
+    if constexpr (S == 6) {
+        d = ((hi + 128) & 255) - 128, a[2] = (float)d, hi = (hi - d) >> 8;
+    }
+    if constexpr (S >= 5) {
+        d = ((hi + 128) & 255) - 128, a[1] = (float)d, hi = (hi - d) >> 8;
+    }
     a[0] = (float)hi;
 }
-static_assert(OZ_S == 6 && OZ_BITS == 8, "oz_cut is written for six balanced 8-bit slices");
 
 // The six BF16 slice planes of A (tiled, 128-row tiles) and each row's scale
 // exponent, one warp per row of the stacked batch entries (row r at r * ld; its
@@ -202,6 +218,7 @@ static_assert(OZ_S == 6 && OZ_BITS == 8, "oz_cut is written for six balanced 8-b
 // rexp[r] = e_r; OZ_EXP_ZERO for a row of zeros (or max below 2^-830: its slices
 // are zero), OZ_EXP_NONFINITE for a row with NaN or Inf (its first slice
 // carries them, so the products and the result of the row are NaN).
+template <int S>
 __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ A, long long rows, int n, int ld,
                                                       int nkb, int* __restrict__ rexp, OzPlanes out) {
     const int lane = threadIdx.x & 31;
@@ -241,13 +258,13 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
         auto cut = [&](double x, float (&a)[OZ_S]) {
             if (code == OZ_EXP_NONFINITE) {
 #pragma unroll
-                for (int i = 0; i < OZ_S; ++i) a[i] = 0.f;
+                for (int i = 0; i < S; ++i) a[i] = 0.f;
                 if ((abs_bits(x) >> 52) == 0x7FF) a[0] = (float)x;  // NaN / Inf into the products
             } else if (code == OZ_EXP_ZERO) {
 #pragma unroll
-                for (int i = 0; i < OZ_S; ++i) a[i] = 0.f;
+                for (int i = 0; i < S; ++i) a[i] = 0.f;
             } else {
-                oz_cut(oz_round_scaled((unsigned long long)__double_as_longlong(x), e), a);
+                oz_cut<S>(oz_round_scaled<oz_frac(S)>((unsigned long long)__double_as_longlong(x), e), a);
             }
         };
         for (int k = lane; k < npair; k += 32) {
@@ -257,7 +274,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
             cut(v.y, b);
             const long long o = oz_tile_off(r, 2 * k, nkb, 7);  // values 2k, 2k + 1: one 4-byte word
 #pragma unroll
-            for (int i = 0; i < OZ_S; ++i)  // exact: integers of at most 8 significant bits
+            for (int i = 0; i < S; ++i)  // exact: integers of at most 8 significant bits
                 *reinterpret_cast<__nv_bfloat162*>(out.s[i] + o) = __floats2bfloat162_rn(a[i], b[i]);
         }
         if ((n & 1) && lane == 0) {
@@ -265,7 +282,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
             cut(row[n - 1], a);
             const long long o = oz_tile_off(r, n - 1, nkb, 7);
 #pragma unroll
-            for (int i = 0; i < OZ_S; ++i) out.s[i][o] = __float2bfloat16_rn(a[i]);
+            for (int i = 0; i < S; ++i) out.s[i][o] = __float2bfloat16_rn(a[i]);
         }
     }
 }
@@ -274,7 +291,9 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
 
 namespace {
 
+template <int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_constant__ OzParams p) {
+    constexpr int STAGES = oz_stages(S), STAGE_BYTES = oz_stage_bytes(S);
     extern __shared__ uint8_t smem_raw[];
     __shared__ int s_skip;
     __shared__ uint32_t s_tmem;
@@ -282,7 +301,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
     __shared__ int s_consumed;
     __shared__ int s_issued;
     // full[3], empty[3] (shared-memory ring), acc_full[2], acc_empty[2] (TMEM ring), done
-    __shared__ __align__(8) uint64_t s_bar[2 * OZ_STAGES + 5];
+    __shared__ __align__(8) uint64_t s_bar[2 * STAGES + 5];
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     if (threadIdx.x == 0) s_skip = (*(volatile unsigned*)p.err != 0u);
@@ -292,17 +311,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     volatile int* abort_flag = &s_abort;
     const uint32_t bar_full = smem_u32(&s_bar[0]);
-    const uint32_t bar_empty = smem_u32(&s_bar[OZ_STAGES]);
-    const uint32_t bar_acc_full = smem_u32(&s_bar[2 * OZ_STAGES]);
-    const uint32_t bar_acc_empty = smem_u32(&s_bar[2 * OZ_STAGES + 2]);
-    const uint32_t bar_done = smem_u32(&s_bar[2 * OZ_STAGES + 4]);
+    const uint32_t bar_empty = smem_u32(&s_bar[STAGES]);
+    const uint32_t bar_acc_full = smem_u32(&s_bar[2 * STAGES]);
+    const uint32_t bar_acc_empty = smem_u32(&s_bar[2 * STAGES + 2]);
+    const uint32_t bar_done = smem_u32(&s_bar[2 * STAGES + 4]);
 
     const int nk = (p.n + OZ_KV - 1) / OZ_KV;  // k-blocks of a tile (one pipeline stage each)
     const int ng = (nk + OZ_GROUP - 1) / OZ_GROUP;  // k-block groups of a tile (one TMEM buffer each)
     const int ntiles = p.tiles_m * p.tiles_n;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < OZ_STAGES; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             mbar_init(bar_full + 8 * s, 1);
             mbar_init(bar_empty + 8 * s, 1);
         }
@@ -336,20 +355,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
             int tm, tn;
             tile_coords(t, p.tiles_m, p.tiles_n, 8, tm, tn);
             for (int q = 0; q < nk; ++q, ++gq) {
-                const int s = gq % OZ_STAGES;
-                if (!mbar_wait(bar_empty + 8 * s, (uint32_t)(((gq / OZ_STAGES) & 1) ^ 1), abort_flag, p.err)) {
+                const int s = gq % STAGES;
+                if (!mbar_wait(bar_empty + 8 * s, (uint32_t)(((gq / STAGES) & 1) ^ 1), abort_flag, p.err)) {
                     stop = true;
                     break;
                 }
-                const uint32_t st = smem_u32(smem + (size_t)s * OZ_STAGE_BYTES);
+                const uint32_t st = smem_u32(smem + (size_t)s * STAGE_BYTES);
                 const uint32_t fb = bar_full + 8 * s;
-                mbar_expect_tx(fb, (uint32_t)OZ_STAGE_BYTES);
+                mbar_expect_tx(fb, (uint32_t)STAGE_BYTES);
                 const size_t ta = ((size_t)tm * p.nkb + q) * OZ_A_BYTES, tb = ((size_t)tn * p.nkb + q) * OZ_B_BYTES;
 #pragma unroll
-                for (int i = 0; i < OZ_S; ++i) bulk_load(st + (uint32_t)(i * OZ_A_BYTES), p.a[i] + ta, OZ_A_BYTES, fb);
+                for (int i = 0; i < S; ++i) bulk_load(st + (uint32_t)(i * OZ_A_BYTES), p.a[i] + ta, OZ_A_BYTES, fb);
 #pragma unroll
-                for (int j = 0; j < OZ_S; ++j)
-                    bulk_load(st + (uint32_t)(OZ_S * OZ_A_BYTES + j * OZ_B_BYTES), p.b[j] + tb, OZ_B_BYTES, fb);
+                for (int j = 0; j < S; ++j)
+                    bulk_load(st + (uint32_t)(S * OZ_A_BYTES + j * OZ_B_BYTES), p.b[j] + tb, OZ_B_BYTES, fb);
                 s_issued = gq + 1;
             }
         }
@@ -360,27 +379,27 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
         bool stop = false;
         for (int t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
         for (int q = 0; q < nk; ++q, ++gq) {
-            const int s = gq % OZ_STAGES;
+            const int s = gq % STAGES;
             const int g = gg + q / OZ_GROUP, a = g & 1;  // TMEM buffer a holds k-block group g
             const bool first = q % OZ_GROUP == 0, last = q % OZ_GROUP == OZ_GROUP - 1 || q == nk - 1;
-            if (!mbar_wait(bar_full + 8 * s, (uint32_t)((gq / OZ_STAGES) & 1), abort_flag, p.err) ||
+            if (!mbar_wait(bar_full + 8 * s, (uint32_t)((gq / STAGES) & 1), abort_flag, p.err) ||
                 (first && g >= 2 &&
                  !mbar_wait(bar_acc_empty + 8 * a, (uint32_t)(((g >> 1) - 1) & 1), abort_flag, p.err))) {
                 stop = true;
                 break;
             }
             tc_fence_after();
-            const uint64_t dA = desc0 + (uint64_t)(s * (OZ_STAGE_BYTES >> 4));
-            const uint64_t dB = dA + (uint64_t)(OZ_S * (OZ_A_BYTES >> 4));
-            const uint32_t d = tmem + (uint32_t)(a * OZ_S * OZ_BN);
+            const uint64_t dA = desc0 + (uint64_t)(s * (STAGE_BYTES >> 4));
+            const uint64_t dB = dA + (uint64_t)(S * (OZ_A_BYTES >> 4));
+            const uint32_t d = tmem + (uint32_t)(a * S * OZ_BN);
 #pragma unroll
             for (int kk = 0; kk < OZ_ROW / 32; ++kk) {  // 16 BF16 values (32 bytes) of K per product
 #pragma unroll
-                for (int i = 0; i < OZ_S; ++i) {
-                    // A slice i times P slices 0 .. OZ_S-1-i into level blocks i .. OZ_S-1; the
+                for (int i = 0; i < S; ++i) {
+                    // A slice i times P slices 0 .. S-1-i into level blocks i .. S-1; the
                     // first product of a group (i = 0, all level blocks) overwrites them
                     mma_bf16(d + (uint32_t)(i * OZ_BN), dA + (uint64_t)(i * (OZ_A_BYTES >> 4) + 2 * kk),
-                             dB + (uint64_t)(2 * kk), idesc_bf16(OZ_BM, OZ_BN * (OZ_S - i)),
+                             dB + (uint64_t)(2 * kk), idesc_bf16(OZ_BM, OZ_BN * (S - i)),
                              (i > 0 || kk > 0 || !first) ? 1u : 0u);
                 }
             }
@@ -400,9 +419,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             int tm, tn;
             tile_coords(t, p.tiles_m, p.tiles_n, 8, tm, tn);
-            int acc[OZ_S][16];
+            int acc[S][16];
 #pragma unroll
-            for (int l = 0; l < OZ_S; ++l)
+            for (int l = 0; l < S; ++l)
 #pragma unroll
                 for (int c = 0; c < 16; ++c) acc[l][c] = 0;
             for (int q = 0; q < ng; ++q, ++gg) {
@@ -414,16 +433,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
                 tc_fence_after();
                 // two levels per TMEM load round trip
 #pragma unroll
-                for (int l = 0; l < OZ_S; l += 2) {
+                for (int l = 0; l < S; l += 2) {
                     uint32_t r[32];
-                    tmem_ld16(lane_base + (uint32_t)((a * OZ_S + l) * OZ_BN), *reinterpret_cast<uint32_t(*)[16]>(r));
-                    if (l + 1 < OZ_S)
-                        tmem_ld16(lane_base + (uint32_t)((a * OZ_S + l + 1) * OZ_BN),
+                    tmem_ld16(lane_base + (uint32_t)((a * S + l) * OZ_BN), *reinterpret_cast<uint32_t(*)[16]>(r));
+                    if (l + 1 < S)
+                        tmem_ld16(lane_base + (uint32_t)((a * S + l + 1) * OZ_BN),
                                   *reinterpret_cast<uint32_t(*)[16]>(r + 16));
                     tmem_wait32(r);
 #pragma unroll
                     for (int h = 0; h < 2; ++h)
-                        if (l + h < OZ_S)
+                        if (l + h < S)
 #pragma unroll
                             for (int c = 0; c < 16; ++c)
                                 acc[l + h][c] += __float2int_rn(__uint_as_float(r[16 * h + c]));  // exact integers
@@ -440,19 +459,33 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
                 const int mh = mm / p.n, ml = mm - mh * p.n;
                 const int code = p.rexp[grow];
                 const bool nan_out = code == OZ_EXP_NONFINITE;
-                // 2^(e_r - 48) 2^(e_P - 47) 2^40 (sum_l S_l 2^(8 (5 - l)))
-                const double scale =
-                    pow2((code == OZ_EXP_ZERO || nan_out ? 0 : code) + p.p_exp - OZ_FRAC - OZ_FRAC_P + 5 * OZ_BITS);
+                // 2^(e_r - 8S) 2^(e_P - 8S + 1) 2^(8 (S - 1)) (sum_l S_l 2^(8 (S - 1 - l)))
+                const double scale = pow2((code == OZ_EXP_ZERO || nan_out ? 0 : code) + p.p_exp -
+                                          (2 * oz_frac(S) - 1) + (S - 1) * OZ_BITS);
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
                     const int nn = tn * OZ_BN + half * 16 + c;
                     if (nn >= p.n) continue;
-                    // levels in pairs 8 bits apart, then J = H_0 2^16 + H_1: all exact in int64
-                    const long long H0 = (long long)acc[0][c] * 256 + acc[1][c];
-                    const long long H1 = (long long)acc[2][c] * 256 + acc[3][c];
-                    const long long H2 = (long long)acc[4][c] * 256 + acc[5][c];
-                    const long long J = H0 * 65536 + H1;
-                    double v = fma((double)J, pow2(2 * OZ_BITS), (double)H2);
+                    double v;
+                    if constexpr (S == 6) {
+                        // levels in pairs 8 bits apart, then J = H_0 2^16 + H_1: all exact in int64
+                        const long long H0 = (long long)acc[0][c] * 256 + acc[1][c];
+                        const long long H1 = (long long)acc[2][c] * 256 + acc[3][c];
+                        const long long H2 = (long long)acc[4][c] * 256 + acc[5][c];
+                        const long long J = H0 * 65536 + H1;
+                        v = fma((double)J, pow2(2 * OZ_BITS), (double)H2);
+                    } else if constexpr (S == 5) {
+                        // J = (S_0 2^8 + S_1) 2^16 + S_2 2^8 + S_3 (exact in int64), then + S_4
+                        const long long H0 = (long long)acc[0][c] * 256 + acc[1][c];
+                        const long long H1 = (long long)acc[2][c] * 256 + acc[3][c];
+                        const long long J = H0 * 65536 + H1;
+                        v = fma((double)J, pow2(OZ_BITS), (double)acc[4][c]);
+                    } else {
+                        // T = (S_0 2^8 + S_1) 2^16 + S_2 2^8 + S_3: exact in int64 (< 2^56), one rounding
+                        const long long H0 = (long long)acc[0][c] * 256 + acc[1][c];
+                        const long long H1 = (long long)acc[2][c] * 256 + acc[3][c];
+                        v = (double)(H0 * 65536 + H1);
+                    }
                     v *= scale;
                     if (nan_out) v = __longlong_as_double(0x7ff8000000000000ll);
                     p.e.apply(b, mh, ml, nn, v);
@@ -467,9 +500,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
         if (*abort_flag) {
             // copies still in flight after an abort: wait for them (bounded) before exit
             for (int q = s_consumed; q < s_issued; ++q) {
-                const int s = q % OZ_STAGES;
+                const int s = q % STAGES;
                 const unsigned long long t0 = globaltimer();
-                while (!mbar_try(bar_full + 8 * s, (uint32_t)((q / OZ_STAGES) & 1)) &&
+                while (!mbar_try(bar_full + 8 * s, (uint32_t)((q / STAGES) & 1)) &&
                        globaltimer() - t0 < 100000000ull) {
                 }
             }
@@ -495,18 +528,26 @@ size_t oz_plane_bytes(long long rows, int n, int tile_rows) {
 cudaError_t oz_prepare() {
     static bool attr_set = false;
     if (attr_set) return cudaSuccess;
-    const cudaError_t e =
-        cudaFuncSetAttribute((const void*)ozaki_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    cudaError_t e = cudaFuncSetAttribute((const void*)ozaki_pass_kernel<6>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, oz_smem(6));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void*)ozaki_pass_kernel<5>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 oz_smem(5));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void*)ozaki_pass_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 oz_smem(4));
     attr_set = e == cudaSuccess;
     return e;
 }
 
-// P's slices below its scale 2^e_P > max |P| (returned): each value rounded once
-// to t = round(p 2^(47 - e_P)), |t| <= 2^47, and cut into six balanced base-256
-// digits (the last one |p_0| <= 128), as BF16 bit patterns (exact: integers of at
-// most 8 significant bits), in tiled planes of 32-row tiles (oz_plane_bytes(n, n,
-// 32) bytes each, cleared by the caller).
-int oz_slice_host(const double* P, int n, uint16_t* const planes[OZ_S]) {
+int oz_pairs(int s) { return s * (s + 1) / 2; }
+
+// P's S slices below its scale 2^e_P > max |P| (returned): each value rounded once
+// to t = round(p 2^(8S - 1 - e_P)), |t| <= 2^(8S - 1), and cut into S balanced
+// base-256 digits (the last one |p_0| <= 128), as BF16 bit patterns (exact:
+// integers of at most 8 significant bits), in tiled planes of 32-row tiles
+// (oz_plane_bytes(n, n, 32) bytes each, cleared by the caller).
+int oz_slice_host(const double* P, int n, int S, uint16_t* const planes[OZ_S]) {
     double pmax = 0.0;
     for (size_t i = 0; i < (size_t)n * n; ++i) pmax = fabs(P[i]) > pmax ? fabs(P[i]) : pmax;
     int ep = 0;
@@ -514,16 +555,16 @@ int oz_slice_host(const double* P, int n, uint16_t* const planes[OZ_S]) {
     const int nkb = (n + OZ_KV - 1) / OZ_KV;
     for (int r = 0; r < n; ++r)
         for (int k = 0; k < n; ++k) {
-            long long t = llrint(ldexp(P[(size_t)r * n + k], OZ_FRAC_P - ep));
+            long long t = llrint(ldexp(P[(size_t)r * n + k], oz_frac(S) - 1 - ep));
             float dig[OZ_S];
-            for (int i = OZ_S - 1; i > 0; --i) {
+            for (int i = S - 1; i > 0; --i) {
                 const long long d = ((t + 128) & 255) - 128;
                 dig[i] = (float)d;
                 t = (t - d) / 256;  // exact: t - d is a multiple of 256
             }
             dig[0] = (float)t;
             const long long o = oz_tile_off(r, k, nkb, 5);
-            for (int i = 0; i < OZ_S; ++i) {
+            for (int i = 0; i < S; ++i) {
                 uint32_t bits;
                 memcpy(&bits, &dig[i], 4);
                 planes[i][o] = (uint16_t)(bits >> 16);  // exact: at most 8 significant bits
@@ -532,16 +573,19 @@ int oz_slice_host(const double* P, int n, uint16_t* const planes[OZ_S]) {
     return ep;
 }
 
-cudaError_t launch_ozaki_pass(void* const pslices[OZ_S], int p_exp, const double* A, int M, int n, int nbatch, int ld,
-                              void* const slices[OZ_S], int* rexp, const Epi<double>& e, unsigned* err,
-                              cudaStream_t st) {
+namespace {
+
+template <int S>
+cudaError_t launch_ozaki_pass_s(void* const pslices[OZ_S], int p_exp, const double* A, int M, int n, int nbatch,
+                                int ld, void* const slices[OZ_S], int* rexp, const Epi<double>& e, unsigned* err,
+                                cudaStream_t st) {
     OzPlanes planes;
     for (int i = 0; i < OZ_S; ++i) planes.s[i] = static_cast<__nv_bfloat16*>(slices[i]);
     const long long rows = (long long)nbatch * M;
     const int nkb = (n + OZ_KV - 1) / OZ_KV;
     long long blocks = (rows + 7) / 8;  // one warp per row
     if (blocks > 152 * 16) blocks = 152 * 16;
-    oz_slice_kernel<<<(unsigned)blocks, 256, 0, st>>>(A, rows, n, ld, nkb, rexp, planes);
+    oz_slice_kernel<S><<<(unsigned)blocks, 256, 0, st>>>(A, rows, n, ld, nkb, rexp, planes);
     OzParams p;
     for (int i = 0; i < OZ_S; ++i) {
         p.a[i] = static_cast<const uint8_t*>(slices[i]);
@@ -565,8 +609,19 @@ cudaError_t launch_ozaki_pass(void* const pslices[OZ_S], int p_exp, const double
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
     }
     const long long ntiles = (long long)p.tiles_m * p.tiles_n;
-    ozaki_pass_kernel<<<(unsigned)(ntiles < sms ? ntiles : sms), OZ_THREADS, OZ_SMEM, st>>>(p);
+    ozaki_pass_kernel<S><<<(unsigned)(ntiles < sms ? ntiles : sms), OZ_THREADS, oz_smem(S), st>>>(p);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_ozaki_pass(int S, void* const pslices[OZ_S], int p_exp, const double* A, int M, int n,
+                              int nbatch, int ld, void* const slices[OZ_S], int* rexp, const Epi<double>& e,
+                              unsigned* err, cudaStream_t st) {
+    if (S == 6) return launch_ozaki_pass_s<6>(pslices, p_exp, A, M, n, nbatch, ld, slices, rexp, e, err, st);
+    if (S == 5) return launch_ozaki_pass_s<5>(pslices, p_exp, A, M, n, nbatch, ld, slices, rexp, e, err, st);
+    if (S == 4) return launch_ozaki_pass_s<4>(pslices, p_exp, A, M, n, nbatch, ld, slices, rexp, e, err, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace etd

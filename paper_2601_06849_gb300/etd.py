@@ -19,7 +19,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libetd.so")
 
 ETD_OK, ETD_ERR_INVALID_ARG, ETD_ERR_OOM, ETD_ERR_CUDA, ETD_ERR_UNSUPPORTED, ETD_ERR_DIVERGED, ETD_ERR_TIMEOUT = range(7)
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16x3": 4, "bf16x6": 5, "tf32x6": 6, "dst32": 7,
-             "fp64split": 8}
+             "fp64split": 8, "fp64split40": 9, "fp64split32": 10}
+# precisions whose fields and state are FP64
+F64_PRECISIONS = ("fp64", "fp64split", "fp64split40", "fp64split32")
 REACTION = {"none": 0, "linear": 1, "allen_cahn": 2, "fhn": 3, "singular": 4, "ac_forced": 5}
 FAMILY = {"exact": 0, 2: 2, 4: 4, 0: 0}
 
@@ -237,7 +239,7 @@ class Batch:
         count = len(n)
         d = [d] * count if isinstance(d, int) else list(d)
         self.n, self.d, self.n_comp = list(n), d, n_comp
-        self.dtype = torch.float64 if precision in ("fp64", "fp64split") else torch.float32
+        self.dtype = torch.float64 if precision in F64_PRECISIONS else torch.float32
         opt = etd_options_default()
         opt.precision = PRECISION[precision]
         opt.reaction = REACTION[reaction]
@@ -296,7 +298,7 @@ class Plan:
     """One ETD2RK-DS problem on (0,1)^d with n interior points per axis.
 
     ``pade``: 2 (P_{0,2}), 4 (P_{0,4}) or "exact" (eq. (9)-(10)).
-    ``precision``: one of PRECISION; fields are float64 for "fp64" and "fp64split", else float32.
+    ``precision``: one of PRECISION; fields are float64 for the F64_PRECISIONS, else float32.
     ``diag_every``, ``diag_max_abs``: the in-step field check of etd_options
     (0 = off); a failed check makes the next ``sync()`` raise ETD_ERR_DIVERGED.
     """
@@ -309,7 +311,7 @@ class Plan:
 
         self.d, self.n, self.dt, self.n_comp = d, n, dt, n_comp
         self.precision = precision
-        self.dtype = torch.float64 if precision in ("fp64", "fp64split") else torch.float32
+        self.dtype = torch.float64 if precision in F64_PRECISIONS else torch.float32
         opt = etd_options_default()
         opt.precision = PRECISION[precision]
         opt.reaction = REACTION[reaction]

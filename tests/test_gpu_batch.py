@@ -20,7 +20,7 @@ def oracle_instance(d, n, ku, dt, u0, steps):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["tf32x3", "fp64", "fp64split"])
+@pytest.mark.parametrize("precision", ["tf32x3", "fp64", "fp64split", "fp64split40", "fp64split32"])
 def test_mixed_grid_ensemble_matches_oracle(precision):
     torch = need_gpu()
     ns = [64, 96, 64, 130, 96, 37, 64]
@@ -33,7 +33,7 @@ def test_mixed_grid_ensemble_matches_oracle(precision):
     fields = [torch.tensor(u, dtype=batch.dtype, device="cuda") for u in u0]
     batch.step(fields, 12)
     batch.sync()
-    bar = 1e-10 if precision in ("fp64", "fp64split") else 1e-6
+    bar = {"fp64": 1e-10, "fp64split": 1e-10, "fp64split40": 3e-8, "fp64split32": 1e-6}.get(precision, 1e-6)
     for i, n in enumerate(ns):
         ref = oracle_instance(2, n, ku[i], dts[i], u0[i], 12)
         got = fields[i].double().cpu().numpy()

@@ -11,6 +11,11 @@ returned field is set by the transforms:
   tf32    3e-3                  one TF32 product: 11-bit operands (2^-11 = 4.9e-4 per pass)
   bf16x6  1e-6                  three BF16 pieces (24 bits) in every pass
   fp64split 1e-10               FP64 fields; products of six balanced 8-bit slices, exact accumulation
+  fp64split40 3e-8              the same with five slices: operands rounded 2^8 more coarsely
+                                (40 instead of 48 bits below the row's scale), so fp64split's
+                                bar scaled by 2^8
+  fp64split32 1e-6              four slices (32 bits): fp64split's bar scaled by 2^16 would be
+                                6.6e-6; the mode is meant for the split-precision bar, 1e-6
   bf16x3  3e-6                  two BF16 pieces (16 bits, 2^-17 = 7.6e-6 per operand) in the
                                 per-step passes, reaching the state through tau f: over the
                                 N tau <= 0.2 of these runs <= 0.2 * 7.6e-6 on top of the 1e-6 bar
@@ -24,7 +29,7 @@ from oracle import oracle as O
 from oracle import spectral as S
 from paper_2601_06849_gb300 import etd, inputs
 
-TOL = {"fp64": 1e-10, "fp64split": 1e-10, "tf32x3": 1e-6, "tf32x6": 1e-6, "tf32": 3e-3, "bf16x6": 1e-6,
+TOL = {"fp64": 1e-10, "fp64split": 1e-10, "fp64split40": 3e-8, "fp64split32": 1e-6, "tf32x3": 1e-6, "tf32x6": 1e-6, "tf32": 3e-3, "bf16x6": 1e-6,
        "bf16x3": 3e-6}
 
 
@@ -53,7 +58,8 @@ def oracle_ref(d, n, kappa, q, tau, u0, steps, reaction, rp=(), pade=2):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "fp64split", "tf32x3", "tf32x6", "fp32", "tf32", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64split", "fp64split40", "fp64split32", "tf32x3", "tf32x6", "fp32", "tf32", "bf16x3",
+                                       "bf16x6"])
 def test_allen_cahn_2d_n64_100_steps(precision):
     """2D Allen-Cahn, n = 64, kappa = 0.01, q = 0, tau = 1e-3, 100 steps."""
     torch = need_gpu()
@@ -65,7 +71,8 @@ def test_allen_cahn_2d_n64_100_steps(precision):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "fp64split", "tf32x3", "tf32x6", "fp32", "tf32", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64split", "fp64split40", "fp64split32", "tf32x3", "tf32x6", "fp32", "tf32", "bf16x3",
+                                       "bf16x6"])
 @pytest.mark.parametrize("n", [300, 129])
 def test_fhn_2d_ragged(precision, n):
     """2D FitzHugh-Nagumo with the workload's parameters on grids with ragged tiles."""
@@ -78,7 +85,7 @@ def test_fhn_2d_ragged(precision, n):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "fp64split", "tf32x3", "fp32", "bf16x3", "bf16x6"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64split", "fp64split40", "fp64split32", "tf32x3", "fp32", "bf16x3", "bf16x6"])
 @pytest.mark.parametrize("n", [48, 33])
 def test_allen_cahn_3d(precision, n):
     """3D Allen-Cahn, kappa = 1e-3, q = 0.1, tau = 5e-3, Gaussian bump."""
@@ -90,7 +97,7 @@ def test_allen_cahn_3d(precision, n):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "fp64split", "tf32x3", "tf32x6", "bf16x6"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64split", "fp64split40", "fp64split32", "tf32x3", "tf32x6", "bf16x6"])
 def test_fhn_3d_two_components(precision):
     torch = need_gpu()
     n = 40
@@ -130,7 +137,7 @@ def test_exact_exponential(precision, d, n):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision", ["fp64", "fp64split", "tf32x3"])
+@pytest.mark.parametrize("precision", ["fp64", "fp64split", "fp64split40", "fp64split32", "tf32x3"])
 @pytest.mark.parametrize("d", [2, 3])
 def test_smallest_grid(precision, d):
     torch = need_gpu()
@@ -268,13 +275,14 @@ def test_fused_reaction_across_calls_and_interleaved_transforms(precision, d, n)
 
 
 @pytest.mark.gpu
-def test_fp64split_2d_n1024_fhn():
-    """The FP64-split tensor-core path on a 2D FitzHugh-Nagumo grid of n = 1024
-    (K = 1024: 32 k-blocks of exact level sums per tile) within the FP64 bar."""
+@pytest.mark.parametrize("precision", ["fp64split", "fp64split40", "fp64split32"])
+def test_fp64split_2d_n1024_fhn(precision):
+    """The FP64-split tensor-core paths on a 2D FitzHugh-Nagumo grid of n = 1024
+    (K = 1024: 32 k-blocks of exact level sums per tile) within their bars."""
     torch = need_gpu()
     n, steps = 1024, 10
     u0 = inputs.fhn_uniform(n, 2, workload=15)
     ref = oracle_ref(2, n, (1e-3, 5e-3), 0.0, 1e-2, u0, steps, "fhn", FHN)
-    got = run_gpu(torch, 2, n, 1e-3, 0.0, 1e-2, u0, steps, "fp64split", "fhn", FHN, kappa_comp=(1e-3, 5e-3))
+    got = run_gpu(torch, 2, n, 1e-3, 0.0, 1e-2, u0, steps, precision, "fhn", FHN, kappa_comp=(1e-3, 5e-3))
     for c in range(2):
-        assert rel_err(got[c], ref[c]) < 1e-10
+        assert rel_err(got[c], ref[c]) < TOL[precision]
