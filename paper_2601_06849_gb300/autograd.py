@@ -53,7 +53,7 @@ class _Solve(torch.autograd.Function):
         return lam, g_kappa, g_rx, None
 
 
-def solve(u0, kappa, rx_params, *, d, n, q, dt, n_steps, pade=2, precision="bf16x6", reaction="fhn",
+def solve(u0, kappa, rx_params, *, d, n, q, dt, n_steps, pade=2, precision="fp64split", reaction="fhn",
           checkpoint_every=20):
     """u(n_steps * dt) from u0 (CUDA tensor, shape (n_comp, n, ..)); kappa a CPU
     tensor of per-component diffusivities, rx_params a CPU tensor of reaction

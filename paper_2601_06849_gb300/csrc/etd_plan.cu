@@ -704,7 +704,7 @@ extern "C" {
 etd_status etd_options_default(etd_options* opt) {
     if (!opt) return fail(ETD_ERR_INVALID_ARG, "opt is NULL");
     std::memset(opt, 0, sizeof(*opt));
-    opt->precision = ETD_PREC_BF16X6;
+    opt->precision = ETD_PREC_FP64_SPLIT;
     opt->reaction = ETD_RX_ALLEN_CAHN;
     opt->n_comp = 1;
     return ETD_OK;

@@ -232,7 +232,7 @@ class Batch:
     ``n``, ``kappa``, ``q``, ``dt`` are per-instance sequences; the reaction,
     precision, Pade order and component count are shared."""
 
-    def __init__(self, d, n, kappa, q, dt, pade=2, precision="bf16x6", reaction="fhn", rx_params=(), n_comp=2,
+    def __init__(self, d, n, kappa, q, dt, pade=2, precision="fp64split", reaction="fhn", rx_params=(), n_comp=2,
                  kappa_v=None, stream=None, autotune=False, diag_every=0, diag_max_abs=0.0):
         import torch
 
@@ -303,7 +303,7 @@ class Plan:
     (0 = off); a failed check makes the next ``sync()`` raise ETD_ERR_DIVERGED.
     """
 
-    def __init__(self, d: int, n: int, kappa: float, q: float, dt: float, pade=2, precision: str = "bf16x6",
+    def __init__(self, d: int, n: int, kappa: float, q: float, dt: float, pade=2, precision: str = "fp64split",
                  reaction: str = "allen_cahn", rx_params: Sequence[float] = (), n_comp: int = 1,
                  kappa_comp: Optional[Sequence[float]] = None, stream=None, autotune: bool = False,
                  diag_every: int = 0, diag_max_abs: float = 0.0):

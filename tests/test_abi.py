@@ -96,10 +96,11 @@ def test_plan_info_layout_matches_header():
 
 
 def test_options_defaults_and_diag_validation(lib):
-    """Defaults: split BF16 x6 (the mode held to the 1e-6 bar), in-step check off;
-    a negative check interval is rejected before any device work."""
+    """Defaults: FP64-split (the precision held to 1e-6, indeed 1e-10, of FP64 over
+    every configuration's whole run), in-step check off; a negative check interval
+    is rejected before any device work."""
     o = etd.etd_options_default()
-    assert o.precision == etd.PRECISION["bf16x6"]
+    assert o.precision == etd.PRECISION["fp64split"]
     assert o.diag_every == 0 and o.diag_max_abs == 0.0
     o.diag_every = -1
     with pytest.raises(etd.EtdError) as ei:

@@ -80,7 +80,8 @@ def test_ensemble_with_2d_and_3d_instances_resumes():
     ku = [2e-3, 1e-3, 5e-4, 3e-3]
     dts = [5e-3, 1e-2, 2e-3, 4e-3]
     u0 = [inputs.fhn_uniform(n, dd, workload=80 + i) for i, (dd, n) in enumerate(zip(d, ns))]
-    batch = etd.Batch(d, ns, ku, [0.1] * 4, dts, reaction="fhn", rx_params=FHN, n_comp=2, kappa_v=KV)
+    batch = etd.Batch(d, ns, ku, [0.1] * 4, dts, precision="bf16x6", reaction="fhn", rx_params=FHN, n_comp=2,
+                      kappa_v=KV)
     fields = [torch.tensor(u, dtype=torch.float32, device="cuda") for u in u0]
     batch.step(fields, 4)
     batch.step(fields, 4)  # same pointers: carried states resume
@@ -98,12 +99,14 @@ def test_ensemble_agrees_with_single_plans():
     ku = [1e-3, 2e-3, 4e-3]
     dts = [1e-2, 5e-3, 2e-3]
     u0 = [inputs.fhn_uniform(128, 2, workload=90 + i) for i in range(3)]
-    batch = etd.Batch(2, ns, ku, [0.0] * 3, dts, reaction="fhn", rx_params=FHN, n_comp=2, kappa_v=KV)
+    batch = etd.Batch(2, ns, ku, [0.0] * 3, dts, precision="bf16x6", reaction="fhn", rx_params=FHN, n_comp=2,
+                      kappa_v=KV)
     fields = [torch.tensor(u, dtype=torch.float32, device="cuda") for u in u0]
     batch.step(fields, 10)
     batch.sync()
     for i in range(3):
-        plan = etd.Plan(2, 128, ku[i], 0.0, dts[i], reaction="fhn", rx_params=FHN, n_comp=2, kappa_comp=(ku[i], KV))
+        plan = etd.Plan(2, 128, ku[i], 0.0, dts[i], precision="bf16x6", reaction="fhn", rx_params=FHN, n_comp=2,
+                        kappa_comp=(ku[i], KV))
         u = torch.tensor(u0[i], dtype=torch.float32, device="cuda")
         plan.step(u, 10)
         plan.sync()
@@ -115,7 +118,8 @@ def test_ensemble_agrees_with_single_plans():
 @pytest.mark.gpu
 def test_batch_rejects_wrong_calls():
     torch = need_gpu()
-    batch = etd.Batch(2, [32, 48], [1e-3, 1e-3], [0.0, 0.0], [1e-2, 1e-2], reaction="fhn", rx_params=FHN, n_comp=2)
+    batch = etd.Batch(2, [32, 48], [1e-3, 1e-3], [0.0, 0.0], [1e-2, 1e-2], precision="bf16x6", reaction="fhn",
+                      rx_params=FHN, n_comp=2)
     u = torch.zeros((2, 32, 32), device="cuda")
     with pytest.raises(etd.EtdError):
         etd.etd_step(batch.handle, u.data_ptr(), 1)  # a batch is not a single plan

@@ -90,7 +90,7 @@ def test_host_entry_point_reports_diverged():
 def test_ensemble_checks_every_group():
     torch = need_gpu()
     ns = [64, 96, 64]
-    b = etd.Batch(2, ns, [1e-3] * 3, [0.0] * 3, [1e-2] * 3, reaction="fhn", rx_params=FHN, n_comp=2,
+    b = etd.Batch(2, ns, [1e-3] * 3, [0.0] * 3, [1e-2] * 3, precision="bf16x6", reaction="fhn", rx_params=FHN, n_comp=2,
                   kappa_v=5e-3, diag_every=1)
     fields = [torch.tensor(inputs.fhn_uniform(n, 2, workload=23 + i), dtype=torch.float32, device="cuda")
               for i, n in enumerate(ns)]

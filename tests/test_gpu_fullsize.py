@@ -81,8 +81,8 @@ def test_maximum_sizes_sine_mode(d, n, modes):
 @pytest.mark.gpu
 def test_zero_steps_is_identity():
     torch = need_gpu()
-    plan = etd.Plan(2, 70, 0.01, 0.0, 1e-3)
-    u = torch.rand((1, 70, 70), device="cuda")
+    plan = etd.Plan(2, 70, 0.01, 0.0, 1e-3)  # the default precision (FP64-split: double fields)
+    u = torch.rand((1, 70, 70), device="cuda", dtype=plan.dtype)
     before = u.clone()
     plan.step(u, 0)
     plan.sync()
