@@ -126,3 +126,28 @@ def test_batch_rejects_wrong_calls():
     with pytest.raises(etd.EtdError):
         batch.step([u, torch.zeros((2, 32, 32), device="cuda")], 1)  # wrong shape for instance 1
     batch.close()
+
+
+@pytest.mark.gpu
+def test_fp64split_ensemble_many_small_grids():
+    """18 distinct small grids (n = 6 .. 40) in FP64-split, stepped in two calls on
+    the same fields (carried states resume, the captured step replays); every
+    member against the oracle at the FP64 bar."""
+    torch = need_gpu()
+    ns = list(range(6, 42, 2))  # 18 grid sizes
+    g = inputs.rng(95)
+    ku = np.exp(g.uniform(np.log(1e-3), np.log(1e-2), len(ns)))
+    dts = g.uniform(1e-3, 1e-2, len(ns))
+    u0 = [inputs.fhn_uniform(n, 2, workload=96 + i) for i, n in enumerate(ns)]
+    batch = etd.Batch(2, ns, ku, [0.0] * len(ns), dts, precision="fp64split", reaction="fhn", rx_params=FHN,
+                      n_comp=2, kappa_v=KV)
+    fields = [torch.tensor(u, dtype=batch.dtype, device="cuda") for u in u0]
+    batch.step(fields, 3)
+    batch.step(fields, 4)  # the same fields: carried states resume, the captured step replays
+    batch.sync()
+    for i, n in enumerate(ns):
+        ref = oracle_instance(2, n, ku[i], dts[i], u0[i], 7)
+        got = fields[i].double().cpu().numpy()
+        for c in range(2):
+            assert rel_err(got[c], ref[c]) < 1e-10, (i, n, c)
+    batch.close()
