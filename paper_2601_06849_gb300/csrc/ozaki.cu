@@ -52,16 +52,16 @@
 // the product kernel, persistent (one CTA per SM walks the 128 x 32 tiles; the MMA
 // warp fills the two TMEM buffers with the next tile's first groups while the
 // drain warps run the previous tile's epilogue):
-//   warps 0-7  drain: per group of four k-blocks, tcgen05.ld of the seven level
-//              accumulators of their TMEM lane quarter and 16-column half (two
+//   warps 0-15 drain: per group of four k-blocks, tcgen05.ld of the S level
+//              accumulators of their TMEM lane quarter and 8-column quarter (two
 //              levels per load round trip), integer sums; at the end the FP64
 //              result and the fused epilogue (Epi<double>, the Hadamard stages
 //              and outputs of the FP64 path);
-//   warp 8     TMA producer (one lane: per k-block twelve untiled bulk copies,
+//   warp 16    TMA producer (one lane: per k-block twelve untiled bulk copies,
 //              one contiguous tile of each slice plane of A (8 KB) and of P
 //              (2 KB); a 2D tensor map would fetch the same bytes as 64-byte
 //              rows, twice the requests) and TMEM allocator;
-//   warp 9     MMA issuer (one lane): per k-step of 16 values, one product per A
+//   warp 17    MMA issuer (one lane): per k-step of 16 values, one product per A
 //              slice i with all P slices j <= 5 - i at once. The six level
 //              accumulators of a buffer are consecutive 32-column TMEM blocks and
 //              the P slices consecutive 32-row blocks of shared memory, so the
@@ -96,10 +96,12 @@ constexpr int OZ_B_BYTES = OZ_BN * OZ_ROW;
 __host__ __device__ constexpr int oz_stage_bytes(int S) { return S * (OZ_A_BYTES + OZ_B_BYTES); }
 __host__ __device__ constexpr int oz_stages(int S) { return S == 6 ? 3 : (S == 5 ? 4 : 5); }
 __host__ __device__ constexpr int oz_smem(int S) { return oz_stages(S) * oz_stage_bytes(S) + 1024; }  // + alignment
-constexpr int OZ_DRAIN_WARPS = 8;
-constexpr int OZ_WARP_TMA = 8;
-constexpr int OZ_WARP_MMA = 9;
-constexpr int OZ_THREADS = 320;
+constexpr int OZ_DRAIN_WARPS = 16;                   // four per TMEM lane quarter
+constexpr int OZ_DC = OZ_BN * 4 / OZ_DRAIN_WARPS;   // columns of a tile per drain warp (8)
+constexpr int OZ_WARP_TMA = OZ_DRAIN_WARPS;
+constexpr int OZ_WARP_MMA = OZ_DRAIN_WARPS + 1;
+constexpr int OZ_THREADS = (OZ_DRAIN_WARPS + 2) * 32;
+static_assert(OZ_DC == 8, "the drain loads eight columns per level (tcgen05.ld 32x32b.x8)");
 constexpr uint32_t OZ_TMEM_COLS = 512;  // 2 buffers x S levels x 32 columns (at most 384), allocated as 512
 constexpr int OZ_BITS = 8;
 // bits below an operand row's scale (8 S: 48, 40 or 32); P takes one bit less, so that
@@ -291,6 +293,23 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
 
 namespace {
 
+// The six-slice result (J 2^16 + H_2) 2^E: while |J| < 2^46 the sum is exact in
+// int64 and takes one conversion, the scale going into the exponent field; the
+// rest (large sums, results outside the normal range) takes the general form in
+// a function of its own, so that the common path is not predicated with it.
+__device__ __noinline__ double oz_form6_general(long long J, long long H2, double scale) {
+    return fma((double)J, pow2(2 * OZ_BITS), (double)H2) * scale;
+}
+__device__ __forceinline__ double oz_form6(long long J, long long H2, int E, double scale) {
+    if (J < (1ll << 46) && J > -(1ll << 46)) {
+        const double v = (double)(J * 65536 + H2);
+        const long long bits = __double_as_longlong(v);
+        const int be = (int)((bits >> 52) & 0x7FF);
+        if (be != 0 && be + E >= 1 && be + E <= 2046) return __longlong_as_double(bits + ((long long)E << 52));
+    }
+    return oz_form6_general(J, H2, scale);
+}
+
 template <int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_constant__ OzParams p) {
     constexpr int STAGES = oz_stages(S), STAGE_BYTES = oz_stage_bytes(S);
@@ -412,18 +431,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
         mma_commit(bar_done);
     } else if (warp < OZ_DRAIN_WARPS) {
         // ---------------- drain: exact integer level sums, then the FP64 epilogue ----------------
-        const int quarter = warp & 3, half = warp >> 2;  // TMEM lanes 32 quarter.., columns 16 half..
-        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 16);
+        const int quarter = warp & 3, cq = warp >> 2;  // TMEM lanes 32 quarter.., columns OZ_DC cq..
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cq * OZ_DC);
         int gg = 0;  // k-block groups drained by this CTA so far
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
             int tm, tn;
             tile_coords(t, p.tiles_m, p.tiles_n, 8, tm, tn);
-            int acc[S][16];
+            int acc[S][OZ_DC];
 #pragma unroll
             for (int l = 0; l < S; ++l)
 #pragma unroll
-                for (int c = 0; c < 16; ++c) acc[l][c] = 0;
+                for (int c = 0; c < OZ_DC; ++c) acc[l][c] = 0;
             for (int q = 0; q < ng; ++q, ++gg) {
                 const int a = gg & 1;
                 if (!mbar_wait(bar_acc_full + 8 * a, (uint32_t)((gg >> 1) & 1), abort_flag, p.err)) {
@@ -434,18 +453,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
                 // two levels per TMEM load round trip
 #pragma unroll
                 for (int l = 0; l < S; l += 2) {
-                    uint32_t r[32];
-                    tmem_ld16(lane_base + (uint32_t)((a * S + l) * OZ_BN), *reinterpret_cast<uint32_t(*)[16]>(r));
+                    uint32_t r[16];
+                    tmem_ld8(lane_base + (uint32_t)((a * S + l) * OZ_BN), *reinterpret_cast<uint32_t(*)[8]>(r));
                     if (l + 1 < S)
-                        tmem_ld16(lane_base + (uint32_t)((a * S + l + 1) * OZ_BN),
-                                  *reinterpret_cast<uint32_t(*)[16]>(r + 16));
-                    tmem_wait32(r);
+                        tmem_ld8(lane_base + (uint32_t)((a * S + l + 1) * OZ_BN),
+                                 *reinterpret_cast<uint32_t(*)[8]>(r + 8));
+                    tmem_wait16(r);
 #pragma unroll
                     for (int h = 0; h < 2; ++h)
                         if (l + h < S)
 #pragma unroll
-                            for (int c = 0; c < 16; ++c)
-                                acc[l + h][c] += __float2int_rn(__uint_as_float(r[16 * h + c]));  // exact integers
+                            for (int c = 0; c < OZ_DC; ++c)
+                                acc[l + h][c] += __float2int_rn(__uint_as_float(r[8 * h + c]));  // exact integers
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -460,11 +479,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
                 const int code = p.rexp[grow];
                 const bool nan_out = code == OZ_EXP_NONFINITE;
                 // 2^(e_r - 8S) 2^(e_P - 8S + 1) 2^(8 (S - 1)) (sum_l S_l 2^(8 (S - 1 - l)))
-                const double scale = pow2((code == OZ_EXP_ZERO || nan_out ? 0 : code) + p.p_exp -
-                                          (2 * oz_frac(S) - 1) + (S - 1) * OZ_BITS);
+                const int E = (code == OZ_EXP_ZERO || nan_out ? 0 : code) + p.p_exp - (2 * oz_frac(S) - 1) +
+                              (S - 1) * OZ_BITS;
+                const double scale = pow2(E);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    const int nn = tn * OZ_BN + half * 16 + c;
+                for (int c = 0; c < OZ_DC; ++c) {
+                    const int nn = tn * OZ_BN + cq * OZ_DC + c;
                     if (nn >= p.n) continue;
                     double v;
                     if constexpr (S == 6) {
@@ -472,21 +492,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
                         const long long H0 = (long long)acc[0][c] * 256 + acc[1][c];
                         const long long H1 = (long long)acc[2][c] * 256 + acc[3][c];
                         const long long H2 = (long long)acc[4][c] * 256 + acc[5][c];
-                        const long long J = H0 * 65536 + H1;
-                        v = fma((double)J, pow2(2 * OZ_BITS), (double)H2);
+                        v = oz_form6(H0 * 65536 + H1, H2, E, scale);
                     } else if constexpr (S == 5) {
                         // J = (S_0 2^8 + S_1) 2^16 + S_2 2^8 + S_3 (exact in int64), then + S_4
                         const long long H0 = (long long)acc[0][c] * 256 + acc[1][c];
                         const long long H1 = (long long)acc[2][c] * 256 + acc[3][c];
                         const long long J = H0 * 65536 + H1;
-                        v = fma((double)J, pow2(OZ_BITS), (double)acc[4][c]);
+                        v = fma((double)J, pow2(OZ_BITS), (double)acc[4][c]) * scale;
                     } else {
                         // T = (S_0 2^8 + S_1) 2^16 + S_2 2^8 + S_3: exact in int64 (< 2^56), one rounding
                         const long long H0 = (long long)acc[0][c] * 256 + acc[1][c];
                         const long long H1 = (long long)acc[2][c] * 256 + acc[3][c];
-                        v = (double)(H0 * 65536 + H1);
+                        v = (double)(H0 * 65536 + H1) * scale;
                     }
-                    v *= scale;
                     if (nan_out) v = __longlong_as_double(0x7ff8000000000000ll);
                     p.e.apply(b, mh, ml, nn, v);
                 }
