@@ -47,7 +47,7 @@
 // templates on S.
 //
 // Per pass: a slicing kernel (one warp per operand row: the row's scale, then its
-// six BF16 slices, written into tiled planes: 128 rows x 32 values per tile,
+// S BF16 slices, written into tiled planes: 128 rows x 32 values per tile,
 // contiguous and already in the swizzled order of the shared-memory stage) and
 // the product kernel, persistent (one CTA per SM walks the 128 x 32 tiles; the MMA
 // warp fills the two TMEM buffers with the next tile's first groups while the
@@ -69,9 +69,10 @@
 //              (N = 32 (6 - i)), written from level block i on, adds a_i p_j to
 //              level block i + j: 6 products per k-step instead of 21, each A
 //              chunk read from shared memory once per k-step.
-// Shared memory holds three pipeline stages of 32 K-values (64-byte rows,
-// 64-byte swizzle) of the six A slices and the six P slices (60 KB per stage).
-// TMEM holds two buffers of six 32-column level accumulators.
+// (Products, levels and stages as written for S = 6.) Shared memory holds three
+// pipeline stages of 32 K-values (64-byte rows, 64-byte swizzle) of the six A
+// slices and the six P slices (60 KB per stage; S = 5, 4: four stages of 50 KB,
+// five of 40 KB). TMEM holds two buffers of S 32-column level accumulators.
 // Every wait is bounded (tc_ptx.cuh); on expiry the CTA raises ERR_TIMEOUT and
 // returns after its copies and products have completed (bounded as well).
 #include <cuda.h>
@@ -212,7 +213,7 @@ __device__ __forceinline__ void oz_cut(long long t, float (&a)[OZ_S]) {
     a[0] = (float)hi;
 }
 
-// The six BF16 slice planes of A (tiled, 128-row tiles) and each row's scale
+// The S BF16 slice planes of A (tiled, 128-row tiles) and each row's scale
 // exponent, one warp per row of the stacked batch entries (row r at r * ld; its
 // n values are written, the tiles' padding stays zero): the warp reduces max |x|
 // over the row, then cuts every value below 2^e_r > max |x| (the row is read
@@ -392,7 +393,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) ozaki_pass_kernel(const __grid_
             }
         }
     } else if (warp == OZ_WARP_MMA && lane == 0) {
-        // ---------------- MMA issuer: the 28 slice pairs of levels 0-6 as 7 products ----------------
+        // ---------------- MMA issuer: the S (S + 1) / 2 slice pairs of levels 0 .. S-1 as S products ----------------
         const uint64_t desc0 = sdesc_kmajor(smem_u32(smem), OZ_ROW);
         int gq = 0, gg = 0;  // k-blocks and k-block groups of this CTA so far
         bool stop = false;
