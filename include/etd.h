@@ -197,7 +197,10 @@ etd_status etd_step(etd_plan* p, void* u_dev, int n_steps);
  * When u_host holds exactly (bit for bit) the field the previous call returned,
  * as in a host-side time-stepping loop, the carried spectral state is kept (a
  * device-side comparison of the copied field decides); any other content
- * rebuilds it, as etd_step does for a new field.
+ * rebuilds it, as etd_step does for a new field. The step starts from the field
+ * the previous call returned while the copy and the comparison run beside it; a
+ * changed field discards that step and is stepped from a rebuilt state (same
+ * result, the time of two steps).
  */
 etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps);
 

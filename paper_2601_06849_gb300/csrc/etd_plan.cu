@@ -88,6 +88,9 @@ struct etd_plan {
     void* host_field = nullptr;  // etd_step_host: the field being stepped (the last one returned)
     void* host_in = nullptr;     // etd_step_host: the incoming field
     bool host_valid = false;     // host_field holds the field the last etd_step_host returned
+    void* host_snap = nullptr;   // etd_step_host: a device copy of the field the last call returned
+    cudaStream_t copy_stream = nullptr;  // etd_step_host: the input's copy and comparison beside the step
+    cudaEvent_t ev_host = nullptr;
     long long workspace = 0;
     // carried spectral state
     bool uhat_valid = false;
@@ -228,12 +231,14 @@ void free_plan(etd_plan* p) {
     if (p->adj_dgrid2) cudaFree(p->adj_dgrid2);
     if (p->adj_acc) cudaFree(p->adj_acc);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    if (p->ev_host) cudaEventDestroy(p->ev_host);
     for (auto ev : p->ev_done)
         if (ev) cudaEventDestroy(ev);
     void* bufs[] = {p->P[0],     p->P[1],     p->P[2],     p->grid,     p->grid2,    p->uhat,     p->zhat,
                     p->wphys,    p->op[0][0], p->op[0][1], p->op[0][2], p->op[1][0],
                     p->op[1][1], p->op[1][2], p->err,      p->stats,    p->host_field, p->host_in,
-                    p->dst_tw,   p->dst_tmp};
+                    p->dst_tw,   p->dst_tmp,  p->host_snap};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (p->maps) tc_maps_destroy(p->maps);
@@ -1360,31 +1365,62 @@ etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps) {
     if (!p->host_field) {
         etd_status s = dalloc(p, &p->host_field, bytes);
         if (s == ETD_OK) s = dalloc(p, &p->host_in, bytes);
+        if (s == ETD_OK) s = dalloc(p, &p->host_snap, bytes);
         if (s != ETD_OK) return s;
+        ETD_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+        ETD_CUDA(cudaEventCreateWithFlags(&p->ev_host, cudaEventDisableTiming));
     }
-    ETD_CUDA(cudaMemcpyAsync(p->host_in, u_host, bytes, cudaMemcpyHostToDevice, p->stream));
+    unsigned* const flag = reinterpret_cast<unsigned*>(p->stats + 3);
     // A caller that steps in a loop hands back the field this call returned last
     // time; then the carried spectral state still belongs to it and needs no
-    // rebuild. Anything else (a different or modified field) is compared bitwise
-    // on the device and rebuilds the state.
-    bool same = false;
-    if (p->host_valid && p->uhat_valid && p->uhat_src == p->host_field) {
-        ETD_CUDA(cudaMemsetAsync(p->stats + 3, 0, sizeof(unsigned), p->stream));
-        launch_differ(p->host_in, p->host_field, bytes, reinterpret_cast<unsigned*>(p->stats + 3), p->stream);
+    // rebuild. That is taken as the likely case: the step starts at once from the
+    // device copy of that field, while the incoming field is copied in and
+    // compared bitwise with a snapshot of it on a second stream. If they differ
+    // (the caller changed the field), the speculative step is discarded and the
+    // incoming field is stepped from a rebuilt state.
+    if (p->host_valid && p->uhat_valid && p->uhat_src == p->host_field && n_steps > 0) {
+        ETD_CUDA(cudaEventRecord(p->ev_host, p->stream));
+        ETD_CUDA(cudaStreamWaitEvent(p->copy_stream, p->ev_host, 0));
+        ETD_CUDA(cudaMemcpyAsync(p->host_in, u_host, bytes, cudaMemcpyHostToDevice, p->copy_stream));
+        ETD_CUDA(cudaMemsetAsync(flag, 0, sizeof(unsigned), p->copy_stream));
+        launch_differ(p->host_in, p->host_snap, bytes, flag, p->copy_stream);
         ETD_CUDA(cudaGetLastError());
+        const double t0 = p->t;
+        const long long done0 = p->steps_done;
+        p->host_valid = false;
+        etd_status s = (p->elem == 8) ? step_impl<double>(p, p->host_field, n_steps)
+                                      : step_impl<float>(p, p->host_field, n_steps);
+        // read back only now: a copy into pageable host memory returns when it is
+        // done, which would hold the step back if issued before it
         unsigned differ = 1;
-        ETD_CUDA(cudaMemcpyAsync(&differ, p->stats + 3, sizeof differ, cudaMemcpyDeviceToHost, p->stream));
+        ETD_CUDA(cudaMemcpyAsync(&differ, flag, sizeof differ, cudaMemcpyDeviceToHost, p->copy_stream));
+        ETD_CUDA(cudaStreamSynchronize(p->copy_stream));
+        if (s != ETD_OK) return s;
+        if (differ == 0) {
+            ETD_CUDA(cudaMemcpyAsync(p->host_snap, p->host_field, bytes, cudaMemcpyDeviceToDevice, p->stream));
+            ETD_CUDA(cudaMemcpyAsync(u_host, p->host_field, bytes, cudaMemcpyDeviceToHost, p->stream));
+            s = etd_sync(p);
+            p->host_valid = s == ETD_OK;
+            return s;
+        }
+        // the field was changed: undo the speculative step's effects on the plan
         ETD_CUDA(cudaStreamSynchronize(p->stream));
-        same = differ == 0;
-    }
-    if (!same) {
-        std::swap(p->host_in, p->host_field);  // step the incoming field; its state is rebuilt
+        ETD_CUDA(cudaMemset(p->err, 0, sizeof(unsigned) * 2));
+        p->t = t0;
+        p->steps_done = done0;
+        p->rx_ready = false;
+        std::swap(p->host_in, p->host_field);
+        p->uhat_valid = false;
+    } else {
+        ETD_CUDA(cudaMemcpyAsync(p->host_in, u_host, bytes, cudaMemcpyHostToDevice, p->stream));
+        std::swap(p->host_in, p->host_field);  // step the incoming field; its state is (re)built
         p->uhat_valid = false;
     }
     p->host_valid = false;
     etd_status s = (p->elem == 8) ? step_impl<double>(p, p->host_field, n_steps)
                                   : step_impl<float>(p, p->host_field, n_steps);
     if (s != ETD_OK) return s;
+    ETD_CUDA(cudaMemcpyAsync(p->host_snap, p->host_field, bytes, cudaMemcpyDeviceToDevice, p->stream));
     ETD_CUDA(cudaMemcpyAsync(u_host, p->host_field, bytes, cudaMemcpyDeviceToHost, p->stream));
     s = etd_sync(p);
     p->host_valid = s == ETD_OK;
