@@ -1404,6 +1404,8 @@ etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps) {
             return s;
         }
         // the field was changed: undo the speculative step's effects on the plan
+        // (its time, step count and error flags: it stepped a field the caller no
+        // longer holds)
         ETD_CUDA(cudaStreamSynchronize(p->stream));
         ETD_CUDA(cudaMemset(p->err, 0, sizeof(unsigned) * 2));
         p->t = t0;
