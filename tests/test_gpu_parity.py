@@ -246,6 +246,14 @@ def test_bad_field_arguments():
     with pytest.raises(etd.EtdError) as ei:
         etd.etd_step(plan.handle, host.data_ptr(), 1)
     assert ei.value.status == etd.ETD_ERR_INVALID_ARG
+    # alignment: device fields must start on a 16-byte boundary (4-byte offset
+    # refused, 16-byte offset taken)
+    buf = torch.zeros(64 * 64 + 8, device="cuda")
+    with pytest.raises(etd.EtdError) as ei:
+        etd.etd_step(plan.handle, buf[1:].data_ptr(), 1)
+    assert ei.value.status == etd.ETD_ERR_INVALID_ARG
+    etd.etd_step(plan.handle, buf[4:].data_ptr(), 1)
+    plan.sync()
     plan.close()
 
 
