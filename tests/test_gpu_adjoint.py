@@ -21,7 +21,8 @@ def setup(d, n, kind, precision, pade=2):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision,bar", [("fp64", 1e-9), ("fp64split", 1e-9), ("tf32x3", 1e-5), ("bf16x6", 1e-5)])
+@pytest.mark.parametrize("precision,bar", [("fp64", 1e-9), ("fp64split", 1e-9), ("fp64split32", 1e-5), ("tf32x3", 1e-5),
+                                           ("bf16x6", 1e-5)])
 @pytest.mark.parametrize("d,n,kind,pade", [(2, 20, "fhn", 2), (3, 10, "allen_cahn", 2), (2, 33, "linear", 4),
                                            (3, 12, "fhn", 4)])
 def test_adjoint_matches_fp64_oracle(precision, bar, d, n, kind, pade):
@@ -89,7 +90,7 @@ def fhn_window_grads(torch, n, steps, precision, u0, target, every=20):
     bench's adjoint workload parameters) through autograd.solve."""
     from paper_2601_06849_gb300 import autograd as AG
 
-    dt = torch.float64 if precision in ("fp64", "fp64split") else torch.float32
+    dt = torch.float64 if precision in etd.F64_PRECISIONS else torch.float32
     u0r = torch.tensor(u0, dtype=dt, device="cuda").requires_grad_(True)
     kr = torch.tensor([1e-3, 5e-3], dtype=torch.float64, requires_grad=True)
     rr = torch.tensor([1.0, 0.01, 0.5, 0.1], dtype=torch.float64, requires_grad=True)
@@ -101,7 +102,8 @@ def fhn_window_grads(torch, n, steps, precision, u0, target, every=20):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision,bar", [("fp64split", 1e-8), ("bf16x6", 3e-4), ("tf32x3", 3e-3)])
+@pytest.mark.parametrize("precision,bar", [("fp64split", 1e-8), ("fp64split32", 1e-5), ("bf16x6", 3e-4),
+                                           ("tf32x3", 3e-3)])
 def test_adjoint_long_window_against_fp64(precision, bar):
     """200 steps (10 checkpoint segments) of 3D FitzHugh-Nagumo, n = 24: each
     gradient (dL/dkappa, dL/d eps, dL/du0) against the FP64 path, relative to its
@@ -109,7 +111,8 @@ def test_adjoint_long_window_against_fp64(precision, bar):
     the adjoint, so their bounds here are stated errors, not the 1e-5 bar; for
     scale, rounding u0 to FP32 alone moves dL/du0 of the FP64 path by 5e-6 to
     1.4e-5 on this problem, so no FP32-field path can reach 1e-5 on u0 over such
-    a window. The FP64-split path (FP64 fields) is held to 1e-8."""
+    a window. The FP64-split path (FP64 fields) is held to 1e-8, its four-slice
+    variant (32-bit products, FP64 fields) to the adjoint bar of 1e-5."""
     torch = need_gpu()
     n, steps = 24, 200
     u0 = inputs.fhn_uniform(n, 3, workload=115)
