@@ -42,7 +42,7 @@ typedef enum {
     ETD_ERR_INVALID_ARG = 1, /* bad size, pointer, alignment or option */
     ETD_ERR_OOM = 2,         /* a device allocation failed */
     ETD_ERR_CUDA = 3,        /* a CUDA runtime or driver call failed */
-    ETD_ERR_UNSUPPORTED = 4, /* valid request this build or GPU cannot run */
+    ETD_ERR_UNSUPPORTED = 4, /* valid request the library or the GPU cannot run */
     ETD_ERR_DIVERGED = 5,    /* non-finite values or |u| beyond diag_max_abs (in-step check, etd_field_stats) */
     ETD_ERR_TIMEOUT = 6      /* a device-side wait exceeded its time limit */
 } etd_status;
