@@ -178,16 +178,11 @@ namespace {
 template <int F>
 __device__ __forceinline__ long long oz_round_scaled(unsigned long long bits, int e) {
     const int b = (int)((bits >> 52) & 0x7FF);
-    unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
-    const int bb = b == 0 ? 1 : b;
-    if (b != 0) m |= 1ull << 52;
-    const int sh = 1075 - F + e - bb;
-    unsigned long long q = 0;
-    if (sh < 64) {
-        q = m >> sh;
-        const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-        q += (rem > half || (rem == half && (q & 1))) ? 1 : 0;
-    }
+    const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(b != 0) << 52);
+    const int sh = 1075 - F + e - (b == 0 ? 1 : b);
+    // floor((m + 2^(sh-1) - 1 + lsb) / 2^sh), lsb the last bit of floor(m / 2^sh):
+    // ties go to the even quotient (m + 2^(sh-1) < 2^54: no overflow)
+    const unsigned long long q = sh < 64 ? (m + ((1ull << (sh - 1)) - 1) + ((m >> sh) & 1)) >> sh : 0;
     return (bits >> 63) ? -(long long)q : (long long)q;
 }
 
@@ -230,23 +225,17 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
     for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += wstride) {
         const double* row = A + r * ld;
         const double2* row2 = reinterpret_cast<const double2*>(row);
-        // max |x| over the row on the bit patterns (their order is that of |x|)
-        unsigned long long mb = 0;
+        // the biased exponent of max |x| over the row: the largest exponent field
+        // (0x7FF when the row holds a NaN or an Inf)
+        unsigned bx = 0;
         for (int k = lane; k < npair; k += 32) {
             const double2 v = row2[k];
-            const unsigned long long a = abs_bits(v.x), b = abs_bits(v.y);
-            mb = a > mb ? a : mb;
-            mb = b > mb ? b : mb;
+            const unsigned a = ((unsigned)__double2hiint(v.x) >> 20) & 0x7FFu;
+            const unsigned b = ((unsigned)__double2hiint(v.y) >> 20) & 0x7FFu;
+            bx = max(bx, max(a, b));
         }
-        if ((n & 1) && lane == 0) {
-            const unsigned long long a = abs_bits(row[n - 1]);
-            mb = a > mb ? a : mb;
-        }
-        for (int off = 16; off > 0; off >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, mb, off);
-            mb = o > mb ? o : mb;
-        }
-        const int bmax = (int)(mb >> 52);  // biased exponent of the row's max
+        if ((n & 1) && lane == 0) bx = max(bx, ((unsigned)__double2hiint(row[n - 1]) >> 20) & 0x7FFu);
+        const int bmax = (int)__reduce_max_sync(0xffffffffu, bx);
         int e = 0;
         int code;
         if (bmax == 0x7FF) {
@@ -270,12 +259,14 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
                 oz_cut<S>(oz_round_scaled<oz_frac(S)>((unsigned long long)__double_as_longlong(x), e), a);
             }
         };
-        for (int k = lane; k < npair; k += 32) {
+        // values 2k, 2k + 1 share a 4-byte word; k + 32 lies two k-blocks (two tiles
+        // of 128 x 32 values) further on, at the same place in its tile
+        long long o = oz_tile_off(r, 2 * lane, nkb, 7);
+        for (int k = lane; k < npair; k += 32, o += 2 * OZ_BM * OZ_KV) {
             const double2 v = row2[k];
             float a[OZ_S], b[OZ_S];
             cut(v.x, a);
             cut(v.y, b);
-            const long long o = oz_tile_off(r, 2 * k, nkb, 7);  // values 2k, 2k + 1: one 4-byte word
 #pragma unroll
             for (int i = 0; i < S; ++i)  // exact: integers of at most 8 significant bits
                 *reinterpret_cast<__nv_bfloat162*>(out.s[i] + o) = __floats2bfloat162_rn(a[i], b[i]);
