@@ -1534,10 +1534,12 @@ etd_status etd_get_plan_info(const etd_plan* p, etd_plan_info* info) {
     double basis = p->dst ? 0.0 : (double)p->n * p->n * (double)p->op_elem * pin;  // DST32 reads no P
     double slicing = 0.0;
     if (p->ozaki) {
-        // FP64-split: P's slices, and per pass the operand read once more (the
-        // row's max before its slices), its slices written and read (2 bytes each)
+        // FP64-split: P's slices, and per pass the operand's slices written and
+        // read (2 bytes each); the operand itself counts once (pin * opb), like
+        // every other value, although a slicer may read a row twice (its max,
+        // then its slices)
         basis = (double)p->n * p->n * 2.0 * p->oz_s;
-        slicing = vals * (8.0 + 2.0 * 2.0 * p->oz_s);
+        slicing = vals * (2.0 * 2.0 * p->oz_s);
     }
     const double st = 8.0, fe = (double)p->elem;
     const double pass_in = pin * opb + basis + slicing;

@@ -169,53 +169,121 @@ namespace {
 
 // FP64 arithmetic runs at about two operations per clock and SM on this GPU, 64
 // times slower than FP32; the slicing is integer arithmetic on the bit patterns
-// instead (an integer-only forming of the result in the product kernel's
-// epilogue measured slower than its four FP64 operations, and was dropped).
+// for the rounding and exact FP32 arithmetic for the digits instead (an
+// integer-only forming of the result in the product kernel's epilogue measured
+// slower than its four FP64 operations, and was dropped).
 //
-// t = round(x 2^(F - e)) to nearest, ties to even, for |x| < 2^e (F = 48, 40 or 32),
-// from the bits of x: x = m 2^(b - 1075) (m with its implicit bit, b the biased
-// exponent, 1 for a subnormal), so t = m 2^-sh with sh = 1075 - F + e - b >= 5.
+// q = round(|x| 2^(F - e)) to nearest, ties to even, for |x| < 2^e (F = 48, 40 or 32),
+// from the bits of x: |x| = m 2^(b - 1075) (m with its implicit bit, b the biased
+// exponent, 1 for a subnormal), so q = m 2^-sh with sh = 1075 - F + e - b >= 5.
 template <int F>
-__device__ __forceinline__ long long oz_round_scaled(unsigned long long bits, int e) {
+__device__ __forceinline__ unsigned long long oz_round_mag(unsigned long long bits, int e) {
     const int b = (int)((bits >> 52) & 0x7FF);
     const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | ((unsigned long long)(b != 0) << 52);
     const int sh = 1075 - F + e - (b == 0 ? 1 : b);
     // floor((m + 2^(sh-1) - 1 + lsb) / 2^sh), lsb the last bit of floor(m / 2^sh):
     // ties go to the even quotient (m + 2^(sh-1) < 2^54: no overflow)
-    const unsigned long long q = sh < 64 ? (m + ((1ull << (sh - 1)) - 1) + ((m >> sh) & 1)) >> sh : 0;
-    return (bits >> 63) ? -(long long)q : (long long)q;
+    return sh < 64 ? (m + ((1ull << (sh - 1)) - 1) + ((m >> sh) & 1)) >> sh : 0;
 }
 
-// S balanced base-256 digits of t (|t| <= 2^(8 S)), split once as t = hi 2^24 + lo
-// with lo in [-2^23, 2^23), then each half cut in 32-bit arithmetic:
-// d = ((v + 128) & 255) - 128, v = (v - d) / 256. The last digit of each half
-// takes the rest: |a_(S-3)| <= 128, |a_0| <= 256 (hi has S - 3 digits).
+// rne(v / 256) for |v| < 2^30: adding 1.5 2^23 to |y| < 2^22 leaves a sum whose last
+// place is 1, so the sum is y rounded to an integer (ties to even), and taking
+// 1.5 2^23 off again is exact. Both operations are written with explicit rounding,
+// so the compiler neither contracts nor cancels them.
+constexpr float OZ_RND = 12582912.0f;
+__device__ __forceinline__ float oz_rne_div256(float v) {
+    return __fadd_rn(__fmaf_rn(v, 0.00390625f, OZ_RND), -OZ_RND);
+}
+
+// S balanced base-256 digits of t = sign(x) q (q <= 2^(8 S)). q is split once as
+// q = hi 2^24 + lo with lo in [-2^23, 2^23) (two integer operations each), both
+// converted exactly to FP32 with x's sign; each half is then cut in FP32 by
+// u = rne(v / 256), digit v - 256 u (an exact fma: an integer of at most 8 bits),
+// v <- u; the last quotient of each half is its top digit: |a_i| <= 128 below the
+// top, |a_(S-3)| <= 128, |a_0| <= 256 (hi <= 2^24 has S - 3 digits). All values
+// are integers below 2^25, so every operation is exact.
 template <int S>
-__device__ __forceinline__ void oz_cut(long long t, float (&a)[OZ_S]) {
-    static_assert(S >= 4 && S <= 6 && OZ_BITS == 8, "oz_cut is written for four to six balanced 8-bit slices");
-    int lo = (int)(((t + (1ll << 23)) & ((1ll << 24) - 1)) - (1ll << 23));
-    int hi = (int)((t - lo) >> 24);
-    int d;
-    d = ((lo + 128) & 255) - 128, a[S - 1] = (float)d, lo = (lo - d) >> 8;
-    d = ((lo + 128) & 255) - 128, a[S - 2] = (float)d, lo = (lo - d) >> 8;
-    a[S - 3] = (float)lo;
+__device__ __forceinline__ void oz_digits(unsigned long long q, unsigned x_hi, float (&a)[OZ_S]) {
+    static_assert(S >= 4 && S <= 6 && OZ_BITS == 8, "oz_digits is written for four to six balanced 8-bit slices");
+    const unsigned q0 = (unsigned)q, q1 = (unsigned)(q >> 32);
+    const int lo = (int)(q0 << 8) >> 8;                                  // low 24 bits of q, balanced
+    const unsigned hi = __funnelshift_r(q0, q1, 24) + ((q0 >> 23) & 1u);  // (q - lo) / 2^24
+    const float sg = __int_as_float((int)((x_hi & 0x80000000u) | 0x3F800000u));  // sign(x) as +-1
+    const float lf = __fmul_rn((float)lo, sg), hf = __fmul_rn((float)hi, sg);
+    const float u = oz_rne_div256(lf);
+    a[S - 1] = __fmaf_rn(u, -256.f, lf);
+    const float u2 = oz_rne_div256(u);
+    a[S - 2] = __fmaf_rn(u2, -256.f, u);
+    a[S - 3] = u2;
     if constexpr (S == 6) {
-        d = ((hi + 128) & 255) - 128, a[2] = (float)d, hi = (hi - d) >> 8;
+        const float v = oz_rne_div256(hf);
+        a[2] = __fmaf_rn(v, -256.f, hf);
+        const float v2 = oz_rne_div256(v);
+        a[1] = __fmaf_rn(v2, -256.f, v);
+        a[0] = v2;
+    } else if constexpr (S == 5) {
+        const float v = oz_rne_div256(hf);
+        a[1] = __fmaf_rn(v, -256.f, hf);
+        a[0] = v;
+    } else {
+        a[0] = hf;
     }
-    if constexpr (S >= 5) {
-        d = ((hi + 128) & 255) - 128, a[1] = (float)d, hi = (hi - d) >> 8;
-    }
-    a[0] = (float)hi;
 }
 
-// The S BF16 slice planes of A (tiled, 128-row tiles) and each row's scale
-// exponent, one warp per row of the stacked batch entries (row r at r * ld; its
-// n values are written, the tiles' padding stays zero): the warp reduces max |x|
-// over the row, then cuts every value below 2^e_r > max |x| (the row is read
-// again from L1/L2).
-// rexp[r] = e_r; OZ_EXP_ZERO for a row of zeros (or max below 2^-830: its slices
-// are zero), OZ_EXP_NONFINITE for a row with NaN or Inf (its first slice
-// carries them, so the products and the result of the row are NaN).
+// Biased exponent field of x (0x7FF for NaN and Inf): the largest one over a row
+// is the biased exponent of the row's max |x|.
+__device__ __forceinline__ unsigned oz_bexp(double x) { return ((unsigned)__double2hiint(x) >> 20) & 0x7FFu; }
+
+// A row's scale code from the biased exponent of its max |x|: e_r with
+// max |x| < 2^e_r (frexp's exponent of the max); OZ_EXP_ZERO for a row of zeros (or
+// max below 2^-830: its slices are zero), OZ_EXP_NONFINITE for a row with NaN or
+// Inf (its first slice carries them, so the products and the result of the row are NaN).
+__device__ __forceinline__ int oz_row_code(int bmax) {
+    return bmax == 0x7FF ? OZ_EXP_NONFINITE : (bmax < OZ_BEXP_MIN ? OZ_EXP_ZERO : bmax - 1022);
+}
+
+// The S slices of one value x of a row with scale code `code`.
+template <int S>
+__device__ __forceinline__ void oz_cut_value(double x, int code, float (&a)[OZ_S]) {
+    if (code == OZ_EXP_NONFINITE) {
+#pragma unroll
+        for (int i = 0; i < S; ++i) a[i] = 0.f;
+        if ((abs_bits(x) >> 52) == 0x7FF) a[0] = (float)x;  // NaN / Inf into the products
+    } else if (code == OZ_EXP_ZERO) {
+#pragma unroll
+        for (int i = 0; i < S; ++i) a[i] = 0.f;
+    } else {
+        const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+        oz_digits<S>(oz_round_mag<oz_frac(S)>(bits, code), (unsigned)(bits >> 32), a);
+    }
+}
+
+// Values 2k, 2k + 1 of a row (one 4-byte word of each plane, at element offset o).
+template <int S>
+__device__ __forceinline__ void oz_store_pair(const OzPlanes& out, long long o, double x0, double x1, int code) {
+    float a[OZ_S], b[OZ_S];
+    oz_cut_value<S>(x0, code, a);
+    oz_cut_value<S>(x1, code, b);
+#pragma unroll
+    for (int i = 0; i < S; ++i)  // exact: integers of at most 8 significant bits
+        *reinterpret_cast<__nv_bfloat162*>(out.s[i] + o) = __floats2bfloat162_rn(a[i], b[i]);
+}
+
+// The last value of a row of odd length n.
+template <int S>
+__device__ __forceinline__ void oz_store_last(const OzPlanes& out, long long r, int n, int nkb, double x, int code) {
+    float a[OZ_S];
+    oz_cut_value<S>(x, code, a);
+    const long long o = oz_tile_off(r, n - 1, nkb, 7);
+#pragma unroll
+    for (int i = 0; i < S; ++i) out.s[i][o] = __float2bfloat16_rn(a[i]);
+}
+
+// The S BF16 slice planes of A (tiled, 128-row tiles) and each row's scale code
+// rexp[r] (oz_row_code), one warp per row of the stacked batch entries (row r at
+// r * ld; its n values are written, the tiles' padding stays zero): the warp
+// reduces max |x| over the row, then cuts every value below 2^e_r > max |x| (the
+// row is read again, from L1/L2 for rows of up to 1024 values).
 template <int S>
 __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict__ A, long long rows, int n, int ld,
                                                       int nkb, int* __restrict__ rexp, OzPlanes out) {
@@ -225,60 +293,69 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const double* __restrict_
     for (long long r = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); r < rows; r += wstride) {
         const double* row = A + r * ld;
         const double2* row2 = reinterpret_cast<const double2*>(row);
-        // the biased exponent of max |x| over the row: the largest exponent field
-        // (0x7FF when the row holds a NaN or an Inf)
         unsigned bx = 0;
         for (int k = lane; k < npair; k += 32) {
             const double2 v = row2[k];
-            const unsigned a = ((unsigned)__double2hiint(v.x) >> 20) & 0x7FFu;
-            const unsigned b = ((unsigned)__double2hiint(v.y) >> 20) & 0x7FFu;
-            bx = max(bx, max(a, b));
+            bx = max(bx, max(oz_bexp(v.x), oz_bexp(v.y)));
         }
-        if ((n & 1) && lane == 0) bx = max(bx, ((unsigned)__double2hiint(row[n - 1]) >> 20) & 0x7FFu);
-        const int bmax = (int)__reduce_max_sync(0xffffffffu, bx);
-        int e = 0;
-        int code;
-        if (bmax == 0x7FF) {
-            code = OZ_EXP_NONFINITE;  // NaN or Inf in the row
-        } else if (bmax < OZ_BEXP_MIN) {
-            code = OZ_EXP_ZERO;
-        } else {
-            e = bmax - 1022;  // max |x| < 2^e (frexp's exponent of the max)
-            code = e;
-        }
+        if ((n & 1) && lane == 0) bx = max(bx, oz_bexp(row[n - 1]));
+        const int code = oz_row_code((int)__reduce_max_sync(0xffffffffu, bx));
         if (lane == 0) rexp[r] = code;
-        auto cut = [&](double x, float (&a)[OZ_S]) {
-            if (code == OZ_EXP_NONFINITE) {
-#pragma unroll
-                for (int i = 0; i < S; ++i) a[i] = 0.f;
-                if ((abs_bits(x) >> 52) == 0x7FF) a[0] = (float)x;  // NaN / Inf into the products
-            } else if (code == OZ_EXP_ZERO) {
-#pragma unroll
-                for (int i = 0; i < S; ++i) a[i] = 0.f;
-            } else {
-                oz_cut<S>(oz_round_scaled<oz_frac(S)>((unsigned long long)__double_as_longlong(x), e), a);
-            }
-        };
-        // values 2k, 2k + 1 share a 4-byte word; k + 32 lies two k-blocks (two tiles
-        // of 128 x 32 values) further on, at the same place in its tile
+        // k + 32 lies two k-blocks (two tiles of 128 x 32 values) further on, at
+        // the same place in its tile
         long long o = oz_tile_off(r, 2 * lane, nkb, 7);
         for (int k = lane; k < npair; k += 32, o += 2 * OZ_BM * OZ_KV) {
             const double2 v = row2[k];
-            float a[OZ_S], b[OZ_S];
-            cut(v.x, a);
-            cut(v.y, b);
-#pragma unroll
-            for (int i = 0; i < S; ++i)  // exact: integers of at most 8 significant bits
-                *reinterpret_cast<__nv_bfloat162*>(out.s[i] + o) = __floats2bfloat162_rn(a[i], b[i]);
+            oz_store_pair<S>(out, o, v.x, v.y, code);
         }
-        if ((n & 1) && lane == 0) {
-            float a[OZ_S];
-            cut(row[n - 1], a);
-            const long long o = oz_tile_off(r, n - 1, nkb, 7);
-#pragma unroll
-            for (int i = 0; i < S; ++i) out.s[i][o] = __float2bfloat16_rn(a[i]);
-        }
+        if ((n & 1) && lane == 0) oz_store_last<S>(out, r, n, nkb, row[n - 1], code);
     }
+}
+
+// The same slicing for rows of more than 1024 values: one block per row, each
+// thread holding up to OZ_PT value pairs in registers from the max to the cut, so
+// the row is read once. (With one warp per row of 4096 values, the rows in flight,
+// 54 of 32 KB per SM, exceed the L2 and the second read came from DRAM.)
+constexpr int OZ_PT = 8;
+constexpr int OZ_SLICE_ROW_MIN = 1025;  // rows of at least this many values take the block-per-row kernel
+
+__host__ __device__ constexpr int oz_slice_row_threads(int n) {  // a multiple of 32, at most 1024 for n <= 16384
+    return 32 * (((n >> 1) + OZ_PT * 32 - 1) / (OZ_PT * 32));
+}
+
+template <int S>
+__global__ void __launch_bounds__(1024) oz_slice_row_kernel(const double* __restrict__ A, int n, int ld, int nkb,
+                                                          int* __restrict__ rexp, OzPlanes out) {
+    __shared__ unsigned s_bx[32];
+    const long long r = blockIdx.x;
+    const double* row = A + r * ld;
+    const double2* row2 = reinterpret_cast<const double2*>(row);
+    const int npair = n >> 1, nt = blockDim.x, t = threadIdx.x;  // npair <= OZ_PT nt (launch rule)
+    double2 v[OZ_PT];
+    unsigned bx = 0;
+#pragma unroll
+    for (int j = 0; j < OZ_PT; ++j) {
+        const int k = t + j * nt;
+        v[j] = k < npair ? row2[k] : make_double2(0.0, 0.0);
+        bx = max(bx, max(oz_bexp(v[j].x), oz_bexp(v[j].y)));
+    }
+    const double last = (n & 1) ? row[n - 1] : 0.0;
+    bx = max(bx, oz_bexp(last));
+    bx = __reduce_max_sync(0xffffffffu, bx);
+    if ((t & 31) == 0) s_bx[t >> 5] = bx;
+    __syncthreads();
+    bx = 0;
+    for (int w = 0; w < (nt >> 5); ++w) bx = max(bx, s_bx[w]);
+    const int code = oz_row_code((int)bx);
+    if (t == 0) rexp[r] = code;
+    // pair k + nt lies 2 nt / 32 k-blocks further on, at the same place in its tile
+    // (nt is a multiple of 16)
+    long long o = oz_tile_off(r, 2 * t, nkb, 7);
+    const long long step = (long long)(2 * nt / OZ_KV) * (OZ_BM * OZ_KV);
+#pragma unroll
+    for (int j = 0; j < OZ_PT; ++j, o += step)
+        if (t + j * nt < npair) oz_store_pair<S>(out, o, v[j].x, v[j].y, code);
+    if ((n & 1) && t == 0) oz_store_last<S>(out, r, n, nkb, last, code);
 }
 
 }  // namespace
@@ -593,9 +670,14 @@ cudaError_t launch_ozaki_pass_s(void* const pslices[OZ_S], int p_exp, const doub
     for (int i = 0; i < OZ_S; ++i) planes.s[i] = static_cast<__nv_bfloat16*>(slices[i]);
     const long long rows = (long long)nbatch * M;
     const int nkb = (n + OZ_KV - 1) / OZ_KV;
-    long long blocks = (rows + 7) / 8;  // one warp per row
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    oz_slice_kernel<S><<<(unsigned)blocks, 256, 0, st>>>(A, rows, n, ld, nkb, rexp, planes);
+    if (n >= OZ_SLICE_ROW_MIN) {
+        if (n > OZ_MAX_N || rows > 0x7FFFFFFFll) return cudaErrorInvalidValue;  // one block per row, at most 1024 threads
+        oz_slice_row_kernel<S><<<(unsigned)rows, oz_slice_row_threads(n), 0, st>>>(A, n, ld, nkb, rexp, planes);
+    } else {
+        long long blocks = (rows + 7) / 8;  // one warp per row
+        if (blocks > 152 * 16) blocks = 152 * 16;
+        oz_slice_kernel<S><<<(unsigned)blocks, 256, 0, st>>>(A, rows, n, ld, nkb, rexp, planes);
+    }
     OzParams p;
     for (int i = 0; i < OZ_S; ++i) {
         p.a[i] = static_cast<const uint8_t*>(slices[i]);
