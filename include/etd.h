@@ -200,7 +200,9 @@ etd_status etd_step(etd_plan* p, void* u_dev, int n_steps);
  * rebuilds it, as etd_step does for a new field. The step starts from the field
  * the previous call returned while the copy and the comparison run beside it; a
  * changed field discards that step and is stepped from a rebuilt state (same
- * result, the time of two steps).
+ * result, the time of two steps). The result is copied back in four parts on
+ * the plan stream and three plan-owned streams (created on the first call, with
+ * the plan's other host-step buffers); all four have completed when the call returns.
  */
 etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps);
 

@@ -91,6 +91,8 @@ struct etd_plan {
     void* host_snap = nullptr;   // etd_step_host: a device copy of the field the last call returned
     cudaStream_t copy_stream = nullptr;  // etd_step_host: the input's copy and comparison beside the step
     cudaEvent_t ev_host = nullptr;
+    cudaStream_t out_stream[3] = {};     // etd_step_host: three of the four parts of the result's copy out
+    cudaEvent_t ev_out[4] = {};
     long long workspace = 0;
     // carried spectral state
     bool uhat_valid = false;
@@ -233,6 +235,10 @@ void free_plan(etd_plan* p) {
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     if (p->ev_host) cudaEventDestroy(p->ev_host);
+    for (cudaStream_t& st : p->out_stream)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t& ev : p->ev_out)
+        if (ev) cudaEventDestroy(ev);
     for (auto ev : p->ev_done)
         if (ev) cudaEventDestroy(ev);
     void* bufs[] = {p->P[0],     p->P[1],     p->P[2],     p->grid,     p->grid2,    p->uhat,     p->zhat,
@@ -1356,6 +1362,30 @@ etd_status etd_sync(etd_plan* p) {
     return ETD_OK;
 }
 
+// etd_step_host's result: the snapshot the next call compares against, and the
+// copy out to the caller's buffer in four parts, one on the plan's stream and
+// three on their own streams, so that several copy engines move it at once; the
+// plan's stream waits for all four (etd_sync then covers them).
+static etd_status host_copy_out(etd_plan* p, void* u_host, size_t bytes) {
+    ETD_CUDA(cudaEventRecord(p->ev_out[0], p->stream));
+    const size_t part = ((bytes + 3) / 4 + 4095) & ~(size_t)4095;
+    for (int i = 1; i < 4; ++i) {
+        const size_t off = (size_t)i * part;
+        if (off >= bytes) break;
+        const size_t len = bytes - off < part ? bytes - off : part;
+        cudaStream_t st = p->out_stream[i - 1];
+        ETD_CUDA(cudaStreamWaitEvent(st, p->ev_out[0], 0));
+        ETD_CUDA(cudaMemcpyAsync(static_cast<char*>(u_host) + off, static_cast<const char*>(p->host_field) + off, len,
+                                 cudaMemcpyDeviceToHost, st));
+        ETD_CUDA(cudaEventRecord(p->ev_out[i], st));
+    }
+    ETD_CUDA(cudaMemcpyAsync(u_host, p->host_field, bytes < part ? bytes : part, cudaMemcpyDeviceToHost, p->stream));
+    ETD_CUDA(cudaMemcpyAsync(p->host_snap, p->host_field, bytes, cudaMemcpyDeviceToDevice, p->stream));
+    for (int i = 1; i < 4; ++i)
+        if ((size_t)i * part < bytes) ETD_CUDA(cudaStreamWaitEvent(p->stream, p->ev_out[i], 0));
+    return ETD_OK;
+}
+
 etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps) {
     if (!p) return fail(ETD_ERR_INVALID_ARG, "plan is NULL");
     if (p->is_batch) return fail(ETD_ERR_INVALID_ARG, "a batch plan is stepped with etd_batch_step");
@@ -1369,6 +1399,8 @@ etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps) {
         if (s != ETD_OK) return s;
         ETD_CUDA(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
         ETD_CUDA(cudaEventCreateWithFlags(&p->ev_host, cudaEventDisableTiming));
+        for (cudaStream_t& st : p->out_stream) ETD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        for (cudaEvent_t& ev : p->ev_out) ETD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
     unsigned* const flag = reinterpret_cast<unsigned*>(p->stats + 3);
     // A caller that steps in a loop hands back the field this call returned last
@@ -1397,9 +1429,8 @@ etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps) {
         ETD_CUDA(cudaStreamSynchronize(p->copy_stream));
         if (s != ETD_OK) return s;
         if (differ == 0) {
-            ETD_CUDA(cudaMemcpyAsync(p->host_snap, p->host_field, bytes, cudaMemcpyDeviceToDevice, p->stream));
-            ETD_CUDA(cudaMemcpyAsync(u_host, p->host_field, bytes, cudaMemcpyDeviceToHost, p->stream));
-            s = etd_sync(p);
+            s = host_copy_out(p, u_host, bytes);
+            if (s == ETD_OK) s = etd_sync(p);
             p->host_valid = s == ETD_OK;
             return s;
         }
@@ -1422,9 +1453,8 @@ etd_status etd_step_host(etd_plan* p, void* u_host, int n_steps) {
     etd_status s = (p->elem == 8) ? step_impl<double>(p, p->host_field, n_steps)
                                   : step_impl<float>(p, p->host_field, n_steps);
     if (s != ETD_OK) return s;
-    ETD_CUDA(cudaMemcpyAsync(p->host_snap, p->host_field, bytes, cudaMemcpyDeviceToDevice, p->stream));
-    ETD_CUDA(cudaMemcpyAsync(u_host, p->host_field, bytes, cudaMemcpyDeviceToHost, p->stream));
-    s = etd_sync(p);
+    s = host_copy_out(p, u_host, bytes);
+    if (s == ETD_OK) s = etd_sync(p);
     p->host_valid = s == ETD_OK;
     return s;
 }
