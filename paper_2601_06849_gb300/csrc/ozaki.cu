@@ -27,7 +27,7 @@
 // K = 16384: 128 groups x 7 x 2^21 < 2^31), and at the end
 //     out = 2^(e_r + e_P - 55) (J 2^16 + H_2),   J = H_0 2^16 + H_1,
 //     H_g = S_2g 2^8 + S_2g+1                     (int64, exact)
-// is formed in FP64 (two roundings). What is left out: the rounding of each
+// is formed in FP64 (one rounding while |J| < 2^46, else two). What is left out: the rounding of each
 // operand to 48 bits below its row's scale (2^-49 relative to the row's max; P:
 // 2^-48) and the pairs with i + j >= 6 (each below 2^-49 of the scales' product
 // per term, of random sign): a few 2^-48 relative to the row's max |out|. The
@@ -46,9 +46,10 @@
 // and smaller pipeline stages (more of them in flight); the kernels below are
 // templates on S.
 //
-// Per pass: a slicing kernel (one warp per operand row: the row's scale, then its
-// S BF16 slices, written into tiled planes: 128 rows x 32 values per tile,
-// contiguous and already in the swizzled order of the shared-memory stage) and
+// Per pass: a slicing kernel (one warp per operand row, one block per row for rows
+// of more than 1024 values: the row's scale, then its S BF16 slices, written into
+// tiled planes: 128 rows x 32 values per tile, contiguous and already in the
+// swizzled order of the shared-memory stage) and
 // the product kernel, persistent (one CTA per SM walks the 128 x 32 tiles; the MMA
 // warp fills the two TMEM buffers with the next tile's first groups while the
 // drain warps run the previous tile's epilogue):
